@@ -1,0 +1,363 @@
+"""Throughput benchmark of the lane-detection path on GB300.
+
+One step = one pass of the whole path (all stages) over one batch of 64 synthetic 1242x375 frames
+(the KITTI-shaped throughput workload).  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the only other program of the method here) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s @1242x375 batch 64 (plain vs learned proposal @≥99% agree); p99 ms"
+UNIT = "frames/s"
+WORKLOAD = "batch64_1242x375"
+DTYPE = "u8/i32 (f32 decisions, f64 solves)"
+INT_OPS_PER_TAP = 4  # bilateral tap: Q15 weight product with rounding, shift, w*I accumulate, w accumulate
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------------------------------
+# oracle arm (host cores)
+# ----------------------------------------------------------------------------------------------------
+def _oracle_worker(args):
+    cfg_name, frame, pdict = args
+    import oracle
+    from paper_1807_02752_gb300 import scenes
+
+    cfg, _ = scenes.WORKLOADS[cfg_name]
+    d, im, _ = scenes.make_frame(cfg, frame)
+    p = oracle.default_params(**pdict)
+    t0 = time.perf_counter()
+    r = oracle.detect(d, im, p, dumps=False)
+    return time.perf_counter() - t0, r["n_lanes"]
+
+
+def oracle_pool(n_workers):
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(n_workers)
+
+
+def run_oracle_frames(pool, frames, pdict):
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_worker, [(WORKLOAD, f, pdict) for f in frames], chunksize=1)
+    wall = time.perf_counter() - t0
+    return wall, sum(r[0] for r in res)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        inside = [s for s in self.samples if t0 - 0.1 <= s[0] <= t1 + 0.1]
+        used = inside or [min(self.samples, key=lambda s: min(abs(s[0] - t0), abs(s[0] - t1)))]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(s[1][0]) for s in used if num(s[1][0]) is not None]
+        mx = [num(s[1][1]) for s in used if num(s[1][1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in used for i in range(4) if "Active" in s[1][3 + i] and "Not" not in s[1][3 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inside)}
+
+
+# ----------------------------------------------------------------------------------------------------
+def bilateral_pixels(det, disp, W, H, n):
+    """Pixels whose bilateral output the path needs: 3x3 dilation of the interior road pixels."""
+    from paper_1807_02752_gb300 import ld
+    from scipy import ndimage
+
+    total = 0
+    for f in range(n):
+        rows = det.debug(f, ld.STAGE_ROWS, W, H)
+        lanes = None
+        F = rows[0]
+        vt = int(np.argmax(F > 0)) if (F > 0).any() else H
+        d = disp[f]
+        road = np.zeros((H, W), bool)
+        with np.errstate(invalid="ignore"):
+            ok = np.isfinite(d) & (d > 0) & (np.abs(d - F[:, None]) <= np.float32(3.0))
+        road[vt:] = ok[vt:]
+        road[:, 0] = road[:, -1] = False
+        road[0, :] = road[-1, :] = False
+        total += int(ndimage.binary_dilation(road, np.ones((3, 3), bool)).sum())
+    return total
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1807_02752_gb300 import ld, scenes
+    from paper_1807_02752_gb300 import build as ldbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0 or local == 0:
+        ldbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    # the oracle pool starts before the first CUDA work so no process forks after it
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    pool = oracle_pool(min(16, host_cores())) if want_cpu else None
+
+    cfg, n = scenes.WORKLOADS[WORKLOAD]
+    W, H = cfg.width, cfg.height
+    # two input batches (frames of this rank), alternated so the inputs (2 x 149 MB) exceed the 129 MB L2
+    base = rank * 2 * n
+    d0, i0, _ = scenes.make_batch(cfg, n, first_frame=base)
+    d1, i1, _ = scenes.make_batch(cfg, n, first_frame=base + n)
+    disp = [torch.from_numpy(d0).cuda(), torch.from_numpy(d1).cuda()]
+    img = [torch.from_numpy(i0).cuda(), torch.from_numpy(i1).cuda()]
+    p = ld.default_params(n_disp=cfg.n_disp)
+    stream = torch.cuda.Stream()
+    det = ld.Detector(W, H, n, p, stream=stream)
+    outs = [det.alloc_lanes(n), det.alloc_lanes(n)]
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    with torch.cuda.stream(stream):
+        for s in range(max(args.warmup, 3)):
+            det.detect(disp[s & 1], img[s & 1], outs[s & 1])
+        stream.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall0 = time.time()
+        evs[0].record(stream)
+        for s in range(args.steps):
+            det.detect(disp[s & 1], img[s & 1], outs[s & 1])
+            evs[s + 1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        t_wall1 = time.time()
+        if world > 1:
+            dist.barrier()
+    total_ms = evs[0].elapsed_time(evs[-1])
+    step_ms = np.array([evs[s].elapsed_time(evs[s + 1]) for s in range(args.steps)])
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    clk = clocks.summary(t_wall0, t_wall1) if clocks else None
+
+    # per-kernel durations: eager launches with an event around every kernel, same stream
+    names = ld.launch_names()
+    kp_steps = max(5, min(args.steps, 40))
+    per = np.zeros(len(names))
+    with torch.cuda.stream(stream):
+        for s in range(kp_steps):
+            per += det.detect_timed(disp[s & 1], img[s & 1], outs[s & 1])
+    per /= kp_steps
+    if clocks:
+        clocks.stop()
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    hd = [torch.from_numpy(d0).pin_memory(), torch.from_numpy(d1).pin_memory()]
+    hi = [torch.from_numpy(i0).pin_memory(), torch.from_numpy(i1).pin_memory()]
+    res = np.zeros(n, ld.LANES_DTYPE)
+    e2e_steps = max(3, min(args.steps, 20))
+    det.detect_host_ptr(hd[0].data_ptr(), hi[0].data_ptr(), W, H, n, res)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        det.detect_host_ptr(hd[s & 1].data_ptr(), hi[s & 1].data_ptr(), W, H, n, res)
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+
+    # roofline of the dominant kernel
+    peaks, peak_src = load_peaks()
+    dom = int(np.argmax(per))
+    dom_name = names[dom]
+    dom_ms = float(per[dom])
+    roof = None
+    if dom_name == "k_grad":
+        npx = bilateral_pixels(det, d1 if (kp_steps - 1) & 1 else d0, W, H, n)
+        taps = (2 * p.bf_rho + 1) ** 2
+        ops = INT_OPS_PER_TAP * taps * npx
+        achieved = ops / (dom_ms * 1e-3) / 1e12
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # INT32 lanes x SMs x clock
+        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom_name,
+                "units_per_launch": {"bilateral_pixels": npx, "taps_per_pixel": taps, "int_ops_per_tap": INT_OPS_PER_TAP},
+                "peak_source": f"152 SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz ({peak_src} clock)"}
+    else:
+        in_bytes = n * H * W * 5
+        achieved = in_bytes / (dom_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom_name, "peak_source": peak_src}
+
+    cpu = None
+    if pool is not None:
+        frames = list(range(base, base + n))[: 4 * min(16, host_cores())]
+        run_oracle_frames(pool, frames[:2], p.as_dict())  # warm the workers
+        wall, cpu_s = run_oracle_frames(pool, frames, p.as_dict())
+        pool.close()
+        cpu = {"value": round(len(frames) / wall, 3), "unit": UNIT, "cores": min(16, host_cores()), "kind": "oracle",
+               "sample": f"{len(frames)} frames of the {WORKLOAD} workload, one frame per process "
+                         f"({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)"}
+
+    if rank == 0:
+        frames_total = world * n * args.steps
+        value = frames_total / (total_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+            "p50_ms": round(float(np.percentile(step_ms, 50)), 4), "p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
+            "data": "synthetic (seeded KITTI-shaped scenes; KITTI is not available)",
+            "config": {"workload": f"{WORKLOAD} plain form", "frames_per_step": n, "width": W, "height": H,
+                       "n_disp": cfg.n_disp, "outliers": cfg.outlier_frac, "invalid": cfg.invalid_frac,
+                       "l2": "inputs larger than L2 (two alternating 149 MB input batches)",
+                       "parallelism": f"replicas x{world}"},
+            "per_kernel_ms": {nm: round(float(x), 4) for nm, x in zip(names, per)},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(world * n * e2e_steps / e2e_s, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": int(n * H * W * 5), "d2h_bytes_per_step": int(n * ld.LANES_DTYPE.itemsize)},
+            "gpu_launches": int(ld.load().ld_launches_per_detect() * args.steps),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    det.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1807_02752_gb300 import scenes
+
+    import oracle
+    oracle.build()
+    cores = min(16, host_cores())
+    pool = oracle_pool(cores)
+    cfg, n = scenes.WORKLOADS[WORKLOAD]
+    pdict = oracle.default_params(n_disp=cfg.n_disp).as_dict()
+    per_step = cores  # one frame per process per step
+    for s in range(max(args.warmup, 1)):
+        run_oracle_frames(pool, [(s * per_step + k) % n for k in range(per_step)], pdict)
+    t0 = time.perf_counter()
+    cpu_total = 0.0
+    for s in range(args.steps):
+        wall, cpu_s = run_oracle_frames(pool, [(s * per_step + k) % n for k in range(per_step)], pdict)
+        cpu_total += cpu_s
+    wall = time.perf_counter() - t0
+    pool.close()
+    value = args.steps * per_step / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64/i64 (CPU)",
+        "data": "synthetic (seeded KITTI-shaped scenes; KITTI is not available)",
+        "config": {"workload": f"{WORKLOAD} plain form", "frames_per_step": per_step, "width": cfg.width,
+                   "height": cfg.height, "n_disp": cfg.n_disp, "parallelism": "host processes"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} frames of the {WORKLOAD} workload per step, one frame per process "
+                                   f"({cpu_total:.1f} s of CPU work)"},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * ld.h - C-ABI of the GB300 lane-detection library.
+ *
+ * The library runs the per-frame dense path of Fan & Dahnoun, "Real-Time Stereo Vision-Based Lane
+ * Detection System" (arXiv 1807.02752, Sec. 2.2-2.4) on an NVIDIA GB300 (sm_103a): from a disparity map
+ * and the left image of each frame to the validated lane positions (the lane vector Gamma of Alg. 7).
+ *
+ *   Sec. 2.2  v-disparity histogram, DP (Eq. 11-12), RANSAC road profile (Alg. 4, Eq. 13), V_py (Eq. 14)
+ *   Sec. 2.3  road mask, bilateral filter (Eq. 15-16), Sobel, sparse V_px votes (Eq. 17), dense
+ *             accumulator (Alg. 5), DP (Eq. 18), RANSAC quartic (Alg. 6, Eq. 19-21), V_px (Eq. 22)
+ *   Sec. 2.4  w_g (Eq. 23), M_0 / M_1 and lane energies (Alg. 7, Eq. 24-25), local-minimum selection
+ *
+ * Conventions for every entry point:
+ *   - images are row-major [n_frames][h][w], contiguous (pitch = w), row v = 0 at the top;
+ *   - disparity is float32 (0 or non-finite = invalid), the image is uint8 grey;
+ *   - return value LD_OK (0) or a negative LD_E_* code; ld_last_error() then describes it;
+ *   - per-frame algorithmic outcomes (no road, degenerate fit, no lanes) are flags in ld_lanes, not errors;
+ *   - nothing aborts, traps or waits without bound; a handle is not thread-safe (one handle per stream).
+ */
+#ifndef LD_H
+#define LD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LD_MAX_LANES 8
+#define LD_MAX_W 4096      /* widest frame */
+#define LD_MAX_H 1088      /* tallest frame: keeps the exact quartic normal-equation sums below 2^85 */
+#define LD_MAX_D 256       /* most disparity bins */
+
+/* return codes */
+#define LD_OK 0
+#define LD_E_ARG (-1)      /* bad argument (null pointer, size out of range, invalid parameter) */
+#define LD_E_CUDA (-2)     /* a CUDA runtime call failed; the message names it */
+#define LD_E_NOMEM (-3)    /* device or pinned-host allocation failed in ld_create */
+#define LD_E_STATE (-4)    /* call not valid in the handle's current state (e.g. no detect yet) */
+
+/* per-frame flags (ld_lanes.flags) */
+#define LD_F_NO_ROAD 1     /* no bottom run of rows with f(v) > 0 and f'(v) > 0 */
+#define LD_F_CAP_Y 2       /* road-profile RANSAC stopped at its round cap */
+#define LD_F_DEGEN_Y 4     /* road-profile fit impossible (too few points or singular system) */
+#define LD_F_CAP_X 8       /* V_px RANSAC stopped at its round cap */
+#define LD_F_DEGEN_X 16    /* V_px fit impossible */
+#define LD_F_NO_LANES 32   /* no lane passed validation */
+
+/*
+ * Parameters: every constant of the method, named after the paper's symbols.  ld_params_default() fills
+ * the paper's values (Sec. 2.2-2.4) and the readings of the points the paper leaves open.
+ */
+typedef struct ld_params {
+    int32_t n_disp;           /* D, bins of the v-disparity map (<= LD_MAX_D) */
+    int32_t tau_y;            /* Eq. 12: row step tau_y in [0, tau_y] (6) */
+    int32_t lambda_y;         /* Eq. 12 smoothness weight (not given in the paper; 1) */
+    float tr_y;               /* Sec. 2.2 squared-residual tolerance (4) */
+    int32_t eps_num, eps_den; /* Alg. 4 / Alg. 6 stop fraction eps = 99/100 */
+    float varpi;              /* Sec. 2.3.1 on-road tolerance |l - f(v)| <= varpi (3) */
+    int32_t bilateral;        /* 1: Eq. 15-16 pre-filter before Sobel; 0: Sobel on the raw image */
+    int32_t bf_rho;           /* bilateral window half-size rho, 1..5 (5 -> 11x11) */
+    double sigma_s, sigma_r;  /* Eq. 16 (300, 0.3 with intensities scaled to [0,1]) */
+    int32_t edge_thresh;      /* Sobel magnitude threshold (100) */
+    int32_t vote_rho;         /* Alg. 5 vote weight varrho (1) */
+    int32_t chi;              /* Alg. 5 band half-height chi (25) */
+    int32_t tau_x;            /* Eq. 18 column step tau_x in [-tau_x, tau_x] (5, at most 7) */
+    int32_t lambda_x;         /* Eq. 18 smoothness weight (not given; 1) */
+    float tr_x;               /* Sec. 2.3.3 squared-residual tolerance (16) */
+    double sigma_g;           /* Eq. 23 (3.5) */
+    int32_t box_nu, box_vs;   /* Alg. 7 box half-sizes nu = 1, varsigma = 3 */
+    int32_t lambda_g;         /* Eq. 24 recursion weight (1) */
+    int32_t xi_num, xi_den;   /* xi = 1/2: lane starts s in [-floor(xi W), W + floor(xi W)) */
+    int32_t thr_num, thr_den; /* lane threshold t = ceil(thr * min H) (not given; 1/32) */
+    int32_t near_px;          /* minima closer than this are "nearby" (not given; 30) */
+    int32_t max_lanes;        /* <= LD_MAX_LANES */
+    int32_t ransac_hyps;      /* hypotheses per RANSAC round (64, at most 256) */
+    int32_t ransac_rounds;    /* RANSAC round cap (64) */
+    uint64_t seed;            /* Philox4x32-10 key of the RANSAC draws */
+} ld_params;
+
+/* Result of one frame (caller-allocated; device memory for ld_detect, host memory for ld_detect_host). */
+typedef struct ld_lanes {
+    int32_t n_lanes, flags;
+    int32_t start_u[LD_MAX_LANES];  /* bottom-row start of each lane (u at v = h-1), ascending */
+    int64_t energy[LD_MAX_LANES];   /* its energy H(start) (Eq. 24), negative */
+    int32_t v_top;                  /* first road row, f^-1(0) on the row grid (h if no road) */
+    int32_t centre, scale_exp;      /* polynomial basis tau = (v - centre) / 2^scale_exp */
+    int32_t rounds_y, rounds_x;     /* RANSAC rounds run for beta and gamma */
+    int32_t reserved;
+    double beta[3];                 /* f(v) = sum beta_k tau^k, the road profile (Eq. 13) */
+    double gamma[5];                /* V_px(v) = sum gamma_k tau^k (Eq. 19, Eq. 22) */
+} ld_lanes;
+
+typedef struct ld_handle ld_handle;
+
+/* Fill p with the paper's constants and the library's readings of the unstated ones. */
+void ld_params_default(ld_params *p);
+
+/* Number of lane start positions per frame for width w: w + 2 floor(xi w) (Alg. 7, xi = 1/2). */
+int32_t ld_n_starts(const ld_params *p, int32_t w);
+
+/*
+ * Create a handle.  All device workspace for frames up to max_w x max_h and batches up to max_batch is
+ * allocated here once; ld_detect never allocates.  cuda_stream (a cudaStream_t, may be NULL for the
+ * default stream) is the stream every later call enqueues on.  *out receives the handle, or NULL on error.
+ * Errors: LD_E_ARG (sizes out of range, invalid params), LD_E_NOMEM, LD_E_CUDA.
+ */
+int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batch, void *cuda_stream,
+              ld_handle **out);
+
+/*
+ * Detect lanes in n_frames frames.  disp (float32) and img (uint8) are DEVICE pointers to
+ * [n_frames][h][w]; out_lanes is a DEVICE array of n_frames ld_lanes.  The call only enqueues work on the
+ * handle's stream (it returns before the GPU finishes); results are valid after the caller synchronises
+ * that stream.  The caller owns all three buffers and must keep them alive until then.
+ * Repeated calls with the same pointers and sizes replay a captured CUDA graph.
+ * Errors: LD_E_ARG (null pointer, w/h/n_frames out of the handle's range, w < 16, h < 16), LD_E_CUDA.
+ */
+int ld_detect(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t h_px, int32_t n_frames,
+              ld_lanes *out_lanes);
+
+/*
+ * Same as ld_detect with HOST buffers: copies the inputs to device staging owned by the handle, runs the
+ * path, copies the results to out_lanes (host, n_frames entries) and waits for the stream.  Page-locked
+ * (pinned) inputs give the fastest copies.  Errors as ld_detect.
+ */
+int ld_detect_host(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t h_px,
+                   int32_t n_frames, ld_lanes *out_lanes);
+
+/* Intermediate results of the last ld_detect / ld_detect_host call, for checking against a reference. */
+enum ld_stage {
+    LD_STAGE_VDISP = 1,    /* int32 [h][D]  v-disparity histogram m_y(d, v) */
+    LD_STAGE_PATH_Y = 2,   /* int16 [D]     DP row v_d at each d (entry 0 unused) */
+    LD_STAGE_INL_Y = 3,    /* uint8 [D]     final RANSAC membership of path point d */
+    LD_STAGE_ROWS = 4,     /* float [3][h]  f(v), V_py(v), V_px(v) on rows >= v_top, 0 above */
+    LD_STAGE_EDGES = 5,    /* int32 [h] counts, then int16 [h][w][4] entries (u, vote column or -1, G_x, G_y) */
+    LD_STAGE_PATH_X = 6,   /* int16 [h]     DP column u_v at each row v >= v_top */
+    LD_STAGE_INL_X = 7,    /* uint8 [h]     final RANSAC membership of the path point at row v */
+    LD_STAGE_M1 = 8,       /* int32 [h][w]  M_1 on rows >= v_top (0 above) */
+    LD_STAGE_HE = 9,       /* int64 [n_starts] energy histogram H */
+};
+/*
+ * Copy stage `stage` of frame `frame` (host buffer host_dst of `bytes` bytes, which must equal the
+ * stage's size) after synchronising the handle's stream.  Errors: LD_E_ARG, LD_E_STATE (no detect yet),
+ * LD_E_CUDA.
+ */
+int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, size_t bytes);
+
+/* Size in bytes of stage `stage` for the last call's frame size (0 if unknown). */
+size_t ld_debug_size(ld_handle *h, int32_t stage);
+
+/*
+ * Host-only: the lookup tables the kernels use, built from p exactly as ld_create builds them.
+ * ws_q[(2 rho + 1)^2] and wr_q[256] are Eq. 16 weights in Q15; wg_q[16385] is Eq. 23 in Q12 indexed by
+ * floor(sin(dtheta) 2^15).  Any pointer may be NULL.  Errors: LD_E_ARG.
+ */
+int ld_tables(const ld_params *p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_q);
+
+/* Number of kernel launches one ld_detect call enqueues, and the name of launch k (0-based). */
+int32_t ld_launches_per_detect(void);
+const char *ld_launch_name(int32_t k);
+
+/*
+ * Profiling form of ld_detect (DEVICE buffers as ld_detect): enqueues the same kernels without graph
+ * capture, with a CUDA event recorded on the handle's stream before the first kernel and after each one,
+ * waits for the stream, and writes the duration of launch k in milliseconds to ms_out[k]
+ * (ld_launches_per_detect() entries).  Errors as ld_detect.
+ */
+int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t h_px,
+                    int32_t n_frames, ld_lanes *out_lanes, float *ms_out);
+
+/* Message of the last error on h (or of the last failed ld_create when h is NULL). */
+const char *ld_last_error(const ld_handle *h);
+
+/* Release the handle and its workspace (synchronises its stream first).  NULL is ignored. */
+void ld_destroy(ld_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LD_H */

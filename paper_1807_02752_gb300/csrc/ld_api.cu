@@ -1,0 +1,609 @@
+// Host runtime behind include/ld.h: parameter checks, lookup tables, workspace, the launch sequence of
+// one ld_detect call (replayed from a captured CUDA graph when the same buffers come back), the
+// host-buffer path and the debug getters.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ld_internal.cuh"
+
+namespace {
+
+constexpr int kLaunches = 7;
+const char *const kLaunchNames[kLaunches] = {"k_vdisp", "k_road", "k_grad", "k_vpx", "k_m1", "k_energy", "k_select"};
+constexpr int kGraphSlots = 4;
+constexpr int kVoteCap = 12288;
+
+std::string g_create_error;
+
+struct GraphSlot {
+    const void *disp = nullptr, *img = nullptr;
+    void *out = nullptr;
+    int w = 0, h = 0, n = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct ld_handle {
+    ld_params p{};
+    int max_w = 0, max_h = 0, max_batch = 0;
+    cudaStream_t stream = nullptr;
+    int smem_optin = 0;
+    void *ws = nullptr;          // device workspace
+    ld::Work w{};
+    int32_t *d_tables = nullptr; // wr, wg
+    int32_t ws_q[121]{};
+    // host-buffer path
+    float *d_disp = nullptr;
+    uint8_t *d_img = nullptr;
+    ld_lanes *d_lanes = nullptr;
+    // last call
+    int last_w = 0, last_h = 0, last_n = 0;
+    bool have_last = false;
+    GraphSlot graphs[kGraphSlots];
+    int next_slot = 0;
+    cudaEvent_t ev[kLaunches + 1] = {};
+    std::string err;
+};
+
+namespace {
+
+int fail(ld_handle *h, int code, const std::string &msg)
+{
+    if (h)
+        h->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(ld_handle *h, cudaError_t e, const char *what)
+{
+    return fail(h, LD_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Eq. 16 in Q15 and Eq. 23 in Q12, built in double from the definitions.
+void build_tables(const ld_params &p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_q)
+{
+    const int rho = p.bf_rho, n = 2 * rho + 1;
+    if (ws_q)
+        for (int dy = -rho; dy <= rho; ++dy)
+            for (int dx = -rho; dx <= rho; ++dx) {
+                const double d2 = (double)(dx * dx + dy * dy);
+                ws_q[(dy + rho) * n + dx + rho] = (int32_t)std::floor(std::exp(-d2 / (p.sigma_s * p.sigma_s)) * 32768.0 + 0.5);
+            }
+    if (wr_q)
+        for (int k = 0; k < 256; ++k) {
+            const double x = (double)k / 255.0;
+            wr_q[k] = (int32_t)std::floor(std::exp(-(x * x) / (p.sigma_r * p.sigma_r)) * 32768.0 + 0.5);
+        }
+    if (wg_q)
+        for (int i = 0; i < ld::kWgEntries; ++i) {
+            const double dth = std::asin((double)i / 32768.0);
+            wg_q[i] = (int32_t)std::floor(std::exp(-(dth / (p.sigma_g * p.sigma_g)) * (36.0 / M_PI)) * 4096.0 + 0.5);
+        }
+}
+
+const char *check_params(const ld_params *p)
+{
+    if (!p)
+        return "params is NULL";
+    if (p->n_disp < 4 || p->n_disp > LD_MAX_D)
+        return "n_disp must be in [4, 256]";
+    if (p->tau_y < 0 || p->tau_y > 15)
+        return "tau_y must be in [0, 15]";
+    if (p->tau_x < 0 || p->tau_x > 7)
+        return "tau_x must be in [0, 7]";
+    if (p->lambda_y < 0 || p->lambda_x < 0 || p->lambda_y > 1000 || p->lambda_x > 1000)
+        return "lambda_y / lambda_x must be in [0, 1000]";
+    if (!(p->tr_y > 0.0f) || !(p->tr_x > 0.0f))
+        return "tr_y / tr_x must be > 0";
+    if (p->eps_den <= 0 || p->eps_num < 0 || p->eps_num > p->eps_den)
+        return "eps must be a fraction in [0, 1]";
+    if (!(p->varpi >= 0.0f))
+        return "varpi must be >= 0";
+    if (p->bf_rho < 1 || p->bf_rho > 5)
+        return "bf_rho must be in [1, 5]";
+    if (!(p->sigma_s > 0.0) || !(p->sigma_r > 0.0) || !(p->sigma_g > 0.0))
+        return "sigma_s, sigma_r, sigma_g must be > 0";
+    if (p->edge_thresh < 0 || p->edge_thresh > 4 * 255 * 2)
+        return "edge_thresh must be in [0, 2040]";
+    if (p->vote_rho < 1 || p->vote_rho > 16)
+        return "vote_rho must be in [1, 16]";
+    if (p->chi < 0 || p->chi > 256)
+        return "chi must be in [0, 256]";
+    if (p->box_nu < 0 || p->box_nu > 8 || p->box_vs < 0 || p->box_vs > 8)
+        return "box_nu / box_vs must be in [0, 8]";
+    if (p->lambda_g < 0 || p->lambda_g > 1)
+        return "lambda_g must be 0 or 1";
+    if (p->xi_den <= 0 || p->xi_num < 0 || p->xi_num > p->xi_den)
+        return "xi must be a fraction in [0, 1]";
+    if (p->thr_den <= 0 || p->thr_num < 0 || p->thr_num > p->thr_den)
+        return "thr must be a fraction in [0, 1]";
+    if (p->near_px < 0 || p->max_lanes < 1 || p->max_lanes > LD_MAX_LANES)
+        return "near_px must be >= 0 and max_lanes in [1, 8]";
+    if (p->ransac_hyps < 1 || p->ransac_hyps > ld::kMaxHyps || p->ransac_rounds < 1 || p->ransac_rounds > 1 << 20)
+        return "ransac_hyps must be in [1, 256] and ransac_rounds >= 1";
+    return nullptr;
+}
+
+ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
+{
+    const ld_params &p = h->p;
+    ld::KParams k{};
+    k.W = W;
+    k.H = H;
+    k.D = p.n_disp;
+    k.n_frames = n;
+    k.tau_y = p.tau_y;
+    k.lambda_y = p.lambda_y;
+    k.tr_y = p.tr_y;
+    k.eps_num = p.eps_num;
+    k.eps_den = p.eps_den;
+    k.varpi = p.varpi;
+    k.bilateral = p.bilateral;
+    k.rho = p.bf_rho;
+    k.edge_thresh2 = p.edge_thresh * p.edge_thresh;
+    k.vote_rho = p.vote_rho;
+    k.chi = p.chi;
+    k.tau_x = p.tau_x;
+    k.lambda_x = p.lambda_x;
+    k.tr_x = p.tr_x;
+    k.box_nu = p.box_nu;
+    k.box_vs = p.box_vs;
+    k.lambda_g = p.lambda_g;
+    k.S0 = (int32_t)((int64_t)W * p.xi_num / p.xi_den);
+    k.n_starts = W + 2 * k.S0;
+    k.thr_num = p.thr_num;
+    k.thr_den = p.thr_den;
+    k.near_px = p.near_px;
+    k.max_lanes = p.max_lanes;
+    k.hyps = p.ransac_hyps;
+    k.rounds = p.ransac_rounds;
+    k.key0 = (uint32_t)p.seed;
+    k.key1 = (uint32_t)(p.seed >> 32);
+    k.centre = (H - 1) / 2;
+    int e = 0;
+    const int half = (H - 1 - k.centre) > k.centre ? (H - 1 - k.centre) : k.centre;
+    while ((1 << e) < half)
+        ++e;
+    k.e = e;
+    k.vote_cap = kVoteCap;
+    const int n_ws = (2 * p.bf_rho + 1) * (2 * p.bf_rho + 1);
+    for (int i = 0; i < n_ws; ++i)
+        k.ws[i] = (int16_t)h->ws_q[i];
+    k.seg_rows = ld::vpx_seg_rows(k, (size_t)h->smem_optin);
+    return k;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// The launch sequence of one call; with `timed`, an event is recorded before and after every kernel.
+int enqueue(ld_handle *h, const ld::KParams &kp, const float *disp, const uint8_t *img, ld_lanes *out,
+            bool timed = false)
+{
+    cudaStream_t s = h->stream;
+    cudaError_t e = cudaSuccess;
+    if (timed && (e = cudaEventRecord(h->ev[0], s)) != cudaSuccess)
+        return cuda_fail(h, e, "event record");
+    for (int k = 0; k < kLaunches; ++k) {
+        switch (k) {
+        case 0: e = ld::launch_vdisp(kp, h->w, disp, s); break;
+        case 1: e = ld::launch_road(kp, h->w, s); break;
+        case 2: e = ld::launch_grad(kp, h->w, disp, img, s); break;
+        case 3: e = ld::launch_vpx(kp, h->w, s); break;
+        case 4: e = ld::launch_m1(kp, h->w, s); break;
+        case 5: e = ld::launch_energy(kp, h->w, s); break;
+        default: e = ld::launch_select(kp, h->w, out, s); break;
+        }
+        if (e != cudaSuccess)
+            return cuda_fail(h, e, kLaunchNames[k]);
+        if (timed && (e = cudaEventRecord(h->ev[k + 1], s)) != cudaSuccess)
+            return cuda_fail(h, e, "event record");
+    }
+    return LD_OK;
+}
+
+int check_call(ld_handle *h, const void *disp, const void *img, int w, int hh, int n, const void *out)
+{
+    if (!h)
+        return LD_E_ARG;
+    if (!disp || !img || !out)
+        return fail(h, LD_E_ARG, "null buffer");
+    if (w < 16 || hh < 16 || w > h->max_w || hh > h->max_h)
+        return fail(h, LD_E_ARG, "frame size outside [16, max_w] x [16, max_h]");
+    if (n < 1 || n > h->max_batch)
+        return fail(h, LD_E_ARG, "n_frames outside [1, max_batch]");
+    return LD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ld_params_default(ld_params *p)
+{
+    if (!p)
+        return;
+    std::memset(p, 0, sizeof(*p));
+    p->n_disp = 128;
+    p->tau_y = 6;
+    p->lambda_y = 1;
+    p->tr_y = 4.0f;
+    p->eps_num = 99;
+    p->eps_den = 100;
+    p->varpi = 3.0f;
+    p->bilateral = 1;
+    p->bf_rho = 5;
+    p->sigma_s = 300.0;
+    p->sigma_r = 0.3;
+    p->edge_thresh = 100;
+    p->vote_rho = 1;
+    p->chi = 25;
+    p->tau_x = 5;
+    p->lambda_x = 1;
+    p->tr_x = 16.0f;
+    p->sigma_g = 3.5;
+    p->box_nu = 1;
+    p->box_vs = 3;
+    p->lambda_g = 1;
+    p->xi_num = 1;
+    p->xi_den = 2;
+    p->thr_num = 1;
+    p->thr_den = 32;
+    p->near_px = 30;
+    p->max_lanes = LD_MAX_LANES;
+    p->ransac_hyps = 64;
+    p->ransac_rounds = 64;
+    p->seed = 0x1807027520ull;
+}
+
+int32_t ld_n_starts(const ld_params *p, int32_t w)
+{
+    if (!p || p->xi_den <= 0 || w < 0)
+        return 0;
+    return w + 2 * (int32_t)((int64_t)w * p->xi_num / p->xi_den);
+}
+
+int ld_tables(const ld_params *p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_q)
+{
+    if (check_params(p))
+        return LD_E_ARG;
+    build_tables(*p, ws_q, wr_q, wg_q);
+    return LD_OK;
+}
+
+int32_t ld_launches_per_detect(void) { return kLaunches; }
+
+const char *ld_launch_name(int32_t k) { return k >= 0 && k < kLaunches ? kLaunchNames[k] : ""; }
+
+int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batch, void *cuda_stream, ld_handle **out)
+{
+    if (!out)
+        return fail(nullptr, LD_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (const char *why = check_params(p))
+        return fail(nullptr, LD_E_ARG, why);
+    if (max_w < 16 || max_w > LD_MAX_W || max_h < 16 || max_h > LD_MAX_H || max_batch < 1 || max_batch > 65535)
+        return fail(nullptr, LD_E_ARG, "max_w / max_h / max_batch out of range");
+    ld_handle *h = new ld_handle();
+    h->p = *p;
+    h->max_w = max_w;
+    h->max_h = max_h;
+    h->max_batch = max_batch;
+    h->stream = (cudaStream_t)cuda_stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e, "device query");
+        delete h;
+        return LD_E_CUDA;
+    }
+    build_tables(h->p, h->ws_q, nullptr, nullptr);
+
+    // backtrack rows that fit for the largest frame decide the number of DP checkpoints
+    ld::KParams kmax = make_kparams(h, max_w, max_h, max_batch);
+    if (kmax.seg_rows < 1 || ld::road_smem_bytes(kmax) > (size_t)h->smem_optin) {
+        delete h;
+        return fail(nullptr, LD_E_ARG, "frame too large for the shared-memory budget");
+    }
+    const size_t n = max_batch, W = max_w, H = max_h, D = p->n_disp;
+    const int max_seg = (int)((H - 1 + kmax.seg_rows - 1) / kmax.seg_rows) + 1;
+    const size_t n_starts = (size_t)ld_n_starts(p, max_w);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t o_my = take(n * D * H * 4), o_fs = take(n * sizeof(ld::FrameState)), o_rows = take(n * 3 * H * 4);
+    const size_t o_py = take(n * D * 2), o_iy = take(n * D), o_ec = take(n * H * 4), o_ed = take(n * H * W * 8);
+    const size_t o_vc = take(n * H * 4), o_vb = take(n * H * W * 2), o_px = take(n * H * 2), o_ix = take(n * H);
+    const size_t o_ck = take(n * max_seg * 2 * W * 4), o_m1 = take(n * H * W * 4), o_he = take(n * n_starts * 8);
+    const size_t o_tab = take(sizeof(int32_t) * (ld::kWrEntries + ld::kWgEntries));
+    const size_t o_d = take(n * H * W * 4), o_i = take(n * H * W), o_l = take(n * sizeof(ld_lanes));
+    e = cudaMalloc(&h->ws, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, LD_E_NOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
+    }
+    char *b = (char *)h->ws;
+    ld::Work &w = h->w;
+    w.myT = (int32_t *)(b + o_my);
+    w.fs = (ld::FrameState *)(b + o_fs);
+    w.rows = (float *)(b + o_rows);
+    w.path_y = (int16_t *)(b + o_py);
+    w.inl_y = (uint8_t *)(b + o_iy);
+    w.ecount = (int32_t *)(b + o_ec);
+    w.edges = (int16_t *)(b + o_ed);
+    w.vcount = (int32_t *)(b + o_vc);
+    w.vbins = (int16_t *)(b + o_vb);
+    w.path_x = (int16_t *)(b + o_px);
+    w.inl_x = (uint8_t *)(b + o_ix);
+    w.ckpt = (int32_t *)(b + o_ck);
+    w.M1 = (int32_t *)(b + o_m1);
+    w.HE = (int64_t *)(b + o_he);
+    h->d_tables = (int32_t *)(b + o_tab);
+    w.wr = h->d_tables;
+    w.wg = h->d_tables + ld::kWrEntries;
+    w.max_w = max_w;
+    w.max_h = max_h;
+    w.max_seg = max_seg;
+    h->d_disp = (float *)(b + o_d);
+    h->d_img = (uint8_t *)(b + o_i);
+    h->d_lanes = (ld_lanes *)(b + o_l);
+
+    std::vector<int32_t> tab(ld::kWrEntries + ld::kWgEntries, 0);
+    build_tables(h->p, nullptr, tab.data() + 256, tab.data() + ld::kWrEntries);
+    // range weights indexed by q - c + 256: entry 256 + k and 256 - k hold wr(|k|); entries >= 512 stay 0
+    for (int k = 1; k < 256; ++k)
+        tab[256 - k] = tab[256 + k];
+    tab[0] = 0;
+    for (int k = 512; k < ld::kWrEntries; ++k)
+        tab[k] = 0;
+    e = cudaMemcpy(h->d_tables, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = ld::setup_fit(h->smem_optin);
+    if (e == cudaSuccess)
+        e = ld::setup_grad(h->smem_optin);
+    if (e == cudaSuccess)
+        e = ld::setup_lpv(h->smem_optin);
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e, "workspace set-up");
+        cudaFree(h->ws);
+        delete h;
+        return LD_E_CUDA;
+    }
+    for (int k = 0; k <= kLaunches && e == cudaSuccess; ++k)
+        e = cudaEventCreate(&h->ev[k]);
+    if (e != cudaSuccess) {
+        cuda_fail(nullptr, e, "event creation");
+        for (int k = 0; k <= kLaunches; ++k)
+            if (h->ev[k])
+                cudaEventDestroy(h->ev[k]);
+        cudaFree(h->ws);
+        delete h;
+        return LD_E_CUDA;
+    }
+    *out = h;
+    return LD_OK;
+}
+
+int ld_detect(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+              ld_lanes *out_lanes)
+{
+    int rc = check_call(h, disp, img, w, hh, n_frames, out_lanes);
+    if (rc != LD_OK)
+        return rc;
+    const ld::KParams kp = make_kparams(h, w, hh, n_frames);
+    h->last_w = w;
+    h->last_h = hh;
+    h->last_n = n_frames;
+    h->have_last = true;
+    // replay a captured graph when the same buffers and sizes come back
+    for (GraphSlot &g : h->graphs)
+        if (g.exec && g.disp == disp && g.img == img && g.out == out_lanes && g.w == w && g.h == hh && g.n == n_frames) {
+            cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
+            return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
+        }
+    // capture this call's launch sequence, then replay it
+    cudaStreamCaptureStatus st;
+    cudaError_t e = cudaStreamIsCapturing(h->stream, &st);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "stream query");
+    if (st != cudaStreamCaptureStatusNone || h->stream == nullptr)  // caller captures, or legacy stream
+        return enqueue(h, kp, disp, img, out_lanes);
+    e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "begin capture");
+    rc = enqueue(h, kp, disp, img, out_lanes);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (rc != LD_OK) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "graph instantiate");
+    GraphSlot &g = h->graphs[h->next_slot];
+    h->next_slot = (h->next_slot + 1) % kGraphSlots;
+    if (g.exec)
+        cudaGraphExecDestroy(g.exec);
+    g.exec = exec;
+    g.disp = disp;
+    g.img = img;
+    g.out = out_lanes;
+    g.w = w;
+    g.h = hh;
+    g.n = n_frames;
+    e = cudaGraphLaunch(exec, h->stream);
+    return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
+}
+
+int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+                    ld_lanes *out_lanes, float *ms_out)
+{
+    int rc = check_call(h, disp, img, w, hh, n_frames, out_lanes);
+    if (rc != LD_OK)
+        return rc;
+    if (!ms_out)
+        return fail(h, LD_E_ARG, "ms_out is NULL");
+    const ld::KParams kp = make_kparams(h, w, hh, n_frames);
+    h->last_w = w;
+    h->last_h = hh;
+    h->last_n = n_frames;
+    h->have_last = true;
+    rc = enqueue(h, kp, disp, img, out_lanes, true);
+    if (rc != LD_OK)
+        return rc;
+    cudaError_t e = cudaEventSynchronize(h->ev[kLaunches]);
+    for (int k = 0; k < kLaunches && e == cudaSuccess; ++k)
+        e = cudaEventElapsedTime(&ms_out[k], h->ev[k], h->ev[k + 1]);
+    return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "event timing");
+}
+
+int ld_detect_host(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+                   ld_lanes *out_lanes)
+{
+    int rc = check_call(h, disp, img, w, hh, n_frames, out_lanes);
+    if (rc != LD_OK)
+        return rc;
+    const size_t npx = (size_t)n_frames * hh * w;
+    cudaError_t e = cudaMemcpyAsync(h->d_disp, disp, npx * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_img, img, npx, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "input copy");
+    rc = ld_detect(h, h->d_disp, h->d_img, w, hh, n_frames, h->d_lanes);
+    if (rc != LD_OK)
+        return rc;
+    e = cudaMemcpyAsync(out_lanes, h->d_lanes, sizeof(ld_lanes) * n_frames, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "result copy");
+}
+
+size_t ld_debug_size(ld_handle *h, int32_t stage)
+{
+    if (!h || !h->have_last)
+        return 0;
+    const size_t W = h->last_w, H = h->last_h, D = h->p.n_disp;
+    switch (stage) {
+    case LD_STAGE_VDISP: return H * D * 4;
+    case LD_STAGE_PATH_Y: return D * 2;
+    case LD_STAGE_INL_Y: return D;
+    case LD_STAGE_ROWS: return 3 * H * 4;
+    case LD_STAGE_EDGES: return H * 4 + H * W * 8;
+    case LD_STAGE_PATH_X: return H * 2;
+    case LD_STAGE_INL_X: return H;
+    case LD_STAGE_M1: return H * W * 4;
+    case LD_STAGE_HE: return (size_t)ld_n_starts(&h->p, (int32_t)W) * 8;
+    default: return 0;
+    }
+}
+
+int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, size_t bytes)
+{
+    if (!h)
+        return LD_E_ARG;
+    if (!h->have_last)
+        return fail(h, LD_E_STATE, "no detect call yet");
+    if (frame < 0 || frame >= h->last_n || !host_dst)
+        return fail(h, LD_E_ARG, "frame out of range or null destination");
+    const size_t want = ld_debug_size(h, stage);
+    if (want == 0 || bytes != want)
+        return fail(h, LD_E_ARG, "unknown stage or wrong byte count");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "stream sync");
+    const size_t W = h->last_w, H = h->last_h, D = h->p.n_disp, f = frame;
+    ld::FrameState fs;
+    e = cudaMemcpy(&fs, h->w.fs + f, sizeof(fs), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "debug copy");
+    const bool no_road = fs.flags & (LD_F_DEGEN_Y | LD_F_NO_ROAD);
+    const bool no_vp = no_road || (fs.flags & LD_F_DEGEN_X);
+    char *dst = (char *)host_dst;
+    switch (stage) {
+    case LD_STAGE_VDISP: {
+        std::vector<int32_t> t(D * H);
+        e = cudaMemcpy(t.data(), h->w.myT + f * D * H, D * H * 4, cudaMemcpyDeviceToHost);
+        int32_t *o = (int32_t *)dst;
+        for (size_t v = 0; v < H; ++v)
+            for (size_t d = 0; d < D; ++d)
+                o[v * D + d] = t[d * H + v];
+        break;
+    }
+    case LD_STAGE_PATH_Y: e = cudaMemcpy(dst, h->w.path_y + f * D, D * 2, cudaMemcpyDeviceToHost); break;
+    case LD_STAGE_INL_Y: e = cudaMemcpy(dst, h->w.inl_y + f * D, D, cudaMemcpyDeviceToHost); break;
+    case LD_STAGE_ROWS: e = cudaMemcpy(dst, h->w.rows + f * 3 * H, 3 * H * 4, cudaMemcpyDeviceToHost); break;
+    case LD_STAGE_EDGES: {
+        e = cudaMemcpy(dst, h->w.ecount + f * H, H * 4, cudaMemcpyDeviceToHost);
+        std::memset(dst + H * 4, 0, H * W * 8);
+        if (e == cudaSuccess && !no_road) {
+            const int32_t *cnt = (const int32_t *)dst;
+            for (size_t v = 0; v < H && e == cudaSuccess; ++v)
+                if (cnt[v] > 0)
+                    e = cudaMemcpy(dst + H * 4 + v * W * 8, h->w.edges + (f * H + v) * W * 4, (size_t)cnt[v] * 8,
+                                   cudaMemcpyDeviceToHost);
+        }
+        break;
+    }
+    case LD_STAGE_PATH_X:
+    case LD_STAGE_INL_X: {
+        const size_t el = stage == LD_STAGE_PATH_X ? 2 : 1;
+        std::memset(dst, 0, H * el);
+        if (!no_road)
+            e = stage == LD_STAGE_PATH_X ? cudaMemcpy(dst, h->w.path_x + f * H, H * 2, cudaMemcpyDeviceToHost)
+                                         : cudaMemcpy(dst, h->w.inl_x + f * H, H, cudaMemcpyDeviceToHost);
+        break;
+    }
+    case LD_STAGE_M1: {
+        std::memset(dst, 0, H * W * 4);
+        const size_t vt = (size_t)fs.v_top;
+        if (!no_vp && vt < H)
+            e = cudaMemcpy(dst + vt * W * 4, h->w.M1 + (f * H + vt) * W, (H - vt) * W * 4, cudaMemcpyDeviceToHost);
+        break;
+    }
+    case LD_STAGE_HE: {
+        const size_t ns = (size_t)ld_n_starts(&h->p, (int32_t)W);
+        std::memset(dst, 0, ns * 8);
+        if (!no_vp)
+            e = cudaMemcpy(dst, h->w.HE + f * ns, ns * 8, cudaMemcpyDeviceToHost);
+        break;
+    }
+    default: return fail(h, LD_E_ARG, "unknown stage");
+    }
+    return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "debug copy");
+}
+
+const char *ld_last_error(const ld_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void ld_destroy(ld_handle *h)
+{
+    if (!h)
+        return;
+    cudaStreamSynchronize(h->stream);
+    for (GraphSlot &g : h->graphs)
+        if (g.exec)
+            cudaGraphExecDestroy(g.exec);
+    for (int k = 0; k <= kLaunches; ++k)
+        if (h->ev[k])
+            cudaEventDestroy(h->ev[k]);
+    cudaFree(h->ws);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Internal definitions shared by the lane-detection kernels and the host runtime.
+//
+// Exactness: every floating-point decision of the path (vote column, w_g angle, lane track, polynomial
+// evaluation and solves) is written with explicit round-to-nearest intrinsics (__fadd_rn, __fmul_rn,
+// __fdiv_rn, __dadd_rn, ...), one IEEE rounding per operation and no contraction, so the results are
+// fixed by the expression alone.  The library is also compiled with --fmad=false as a safety net.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ld.h"
+
+namespace ld {
+
+constexpr int kMaxHyps = 256;
+constexpr int kWgEntries = 16385;     // Eq. 23 table: sin(dtheta) in [0, 1/2] in steps of 2^-15
+constexpr int kWrEntries = 768;       // range-weight table indexed by q - c + 256 (entries >= 512 are 0)
+constexpr int kSentinel = 511;        // image value marking taps outside the frame
+
+// Per-launch constants, passed by value (they live in the kernel-parameter constant bank).
+struct KParams {
+    int32_t W, H, D, n_frames;
+    int32_t tau_y, lambda_y;
+    float tr_y;
+    int32_t eps_num, eps_den;
+    float varpi;
+    int32_t bilateral, rho;
+    int32_t edge_thresh2;
+    int32_t vote_rho, chi, tau_x, lambda_x;
+    float tr_x;
+    int32_t box_nu, box_vs, lambda_g;
+    int32_t S0, n_starts;
+    int32_t thr_num, thr_den, near_px, max_lanes;
+    int32_t hyps, rounds;
+    uint32_t key0, key1;
+    int32_t centre, e;                 // polynomial basis tau = (v - centre) / 2^e
+    int32_t seg_rows;                  // rows of DP backtrack held in shared memory by the V_px kernel
+    int32_t vote_cap;                  // votes per frame the V_px kernel stages in shared memory
+    int16_t ws[121];                   // Eq. 16 spatial weights, Q15, (2 rho + 1)^2 used
+};
+
+// Per-frame state written by the fit kernels and read downstream.
+struct FrameState {
+    int32_t flags, v_top, rounds_y, rounds_x;
+    double beta[3];
+    double gamma[5];
+};
+
+// Device workspace (all pointers device memory, sized for max_w x max_h x max_batch).
+struct Work {
+    int32_t *myT;        // [n][D][H] v-disparity, transposed so a DP step reads a contiguous row
+    FrameState *fs;      // [n]
+    float *rows;         // [n][3][H]: f(v), V_py(v), V_px(v)
+    int16_t *path_y;     // [n][D]
+    uint8_t *inl_y;      // [n][D]
+    int32_t *ecount;     // [n][H] road edge pixels per row
+    int16_t *edges;      // [n][H][W][4]: u, vote column (-1 none), G_x, G_y
+    int32_t *vcount;     // [n][H] votes per row
+    int16_t *vbins;      // [n][H][W] vote columns of each row
+    int16_t *path_x;     // [n][H]
+    uint8_t *inl_x;      // [n][H]
+    int32_t *ckpt;       // [n][max_seg][2][W] DP checkpoints (E row, band row)
+    int32_t *M1;         // [n][H][W]
+    int64_t *HE;         // [n][n_starts]
+    const int32_t *wr;   // [kWrEntries] Q15
+    const int32_t *wg;   // [kWgEntries] Q12
+    int32_t max_w, max_h, max_seg;
+};
+
+// ---------------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds, multipliers 0xD2511F53 / 0xCD9E8D57,
+// Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+// ---------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Correctly rounded conversion of an exact integer sum to double.  Valid for |x| < 2^85: the high part
+// x >> 32 is then exact in a double, and the final addition is the only rounding.
+__device__ __forceinline__ double i128_to_f64(__int128 x)
+{
+    const long long q = (long long)(x >> 32);
+    const unsigned int r = (unsigned int)(x & (__int128)0xffffffffu);
+    return __dadd_rn(__dmul_rn((double)q, 4294967296.0), (double)r);
+}
+
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// Polynomial value in float32 (Horner, two roundings per step) and the inlier test (y - g)^2 < tr.
+template <int M>
+__device__ __forceinline__ bool inlier_test(const float *cf, int x, int y, int centre, float sc, float tr)
+{
+    const float tau = __fmul_rn((float)(x - centre), sc);
+    float p = cf[M - 1];
+#pragma unroll
+    for (int k = M - 2; k >= 0; --k)
+        p = __fadd_rn(__fmul_rn(p, tau), cf[k]);
+    const float r = __fsub_rn((float)y, p);
+    return __fmul_rn(r, r) < tr;
+}
+
+// f64 Horner without contraction.
+template <int M>
+__device__ __forceinline__ double poly_f64(const double *c, double tau)
+{
+    double p = c[M - 1];
+#pragma unroll
+    for (int k = M - 2; k >= 0; --k)
+        p = __dadd_rn(__dmul_rn(p, tau), c[k]);
+    return p;
+}
+
+}  // namespace ld
+
+// Kernel launch helpers implemented in the kernel translation units.
+namespace ld {
+cudaError_t launch_vdisp(const KParams &kp, const Work &w, const float *disp, cudaStream_t s);
+cudaError_t launch_road(const KParams &kp, const Work &w, cudaStream_t s);
+cudaError_t launch_grad(const KParams &kp, const Work &w, const float *disp, const uint8_t *img, cudaStream_t s);
+cudaError_t launch_vpx(const KParams &kp, const Work &w, cudaStream_t s);
+cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s);
+cudaError_t launch_energy(const KParams &kp, const Work &w, cudaStream_t s);
+cudaError_t launch_select(const KParams &kp, const Work &w, ld_lanes *out, cudaStream_t s);
+size_t road_smem_bytes(const KParams &kp);
+size_t vpx_smem_bytes(const KParams &kp);
+int vpx_seg_rows(const KParams &kp, size_t budget);
+cudaError_t setup_fit(int smem_optin);
+cudaError_t setup_grad(int smem_optin);
+cudaError_t setup_lpv(int smem_optin);
+}  // namespace ld

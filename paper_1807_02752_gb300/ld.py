@@ -1,0 +1,239 @@
+"""Python binding of the CUDA lane-detection library (include/ld.h), argument marshalling only.
+
+Every step of the path runs in the library's kernels.  PyTorch is used for device memory and streams.
+If lib/libld.so has not been built, load() raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libld.so")
+
+MAX_LANES = 8
+OK, E_ARG, E_CUDA, E_NOMEM, E_STATE = 0, -1, -2, -3, -4
+F_NO_ROAD, F_CAP_Y, F_DEGEN_Y, F_CAP_X, F_DEGEN_X, F_NO_LANES = 1, 2, 4, 8, 16, 32
+STAGE_VDISP, STAGE_PATH_Y, STAGE_INL_Y, STAGE_ROWS, STAGE_EDGES, STAGE_PATH_X, STAGE_INL_X, STAGE_M1, STAGE_HE = range(1, 10)
+
+
+class Params(C.Structure):
+    """ld_params."""
+
+    _fields_ = [
+        ("n_disp", C.c_int32), ("tau_y", C.c_int32), ("lambda_y", C.c_int32), ("tr_y", C.c_float),
+        ("eps_num", C.c_int32), ("eps_den", C.c_int32), ("varpi", C.c_float), ("bilateral", C.c_int32),
+        ("bf_rho", C.c_int32), ("sigma_s", C.c_double), ("sigma_r", C.c_double), ("edge_thresh", C.c_int32),
+        ("vote_rho", C.c_int32), ("chi", C.c_int32), ("tau_x", C.c_int32), ("lambda_x", C.c_int32),
+        ("tr_x", C.c_float), ("sigma_g", C.c_double), ("box_nu", C.c_int32), ("box_vs", C.c_int32),
+        ("lambda_g", C.c_int32), ("xi_num", C.c_int32), ("xi_den", C.c_int32), ("thr_num", C.c_int32),
+        ("thr_den", C.c_int32), ("near_px", C.c_int32), ("max_lanes", C.c_int32), ("ransac_hyps", C.c_int32),
+        ("ransac_rounds", C.c_int32), ("seed", C.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+LANES_DTYPE = np.dtype([
+    ("n_lanes", "<i4"), ("flags", "<i4"), ("start_u", "<i4", (MAX_LANES,)), ("energy", "<i8", (MAX_LANES,)),
+    ("v_top", "<i4"), ("centre", "<i4"), ("scale_exp", "<i4"), ("rounds_y", "<i4"), ("rounds_x", "<i4"),
+    ("reserved", "<i4"), ("beta", "<f8", (3,)), ("gamma", "<f8", (5,)),
+])
+assert LANES_DTYPE.itemsize == 192
+
+_lib = None
+
+
+def load():
+    """Load lib/libld.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run paper_1807_02752_gb300/build.py)")
+    L = C.CDLL(LIB_PATH)
+    p, i32, P = C.c_void_p, C.c_int32, C.POINTER(Params)
+    L.ld_params_default.argtypes = [P]
+    L.ld_params_default.restype = None
+    L.ld_n_starts.argtypes = [P, i32]
+    L.ld_n_starts.restype = i32
+    L.ld_create.argtypes = [P, i32, i32, i32, p, C.POINTER(p)]
+    L.ld_create.restype = C.c_int
+    L.ld_detect.argtypes = [p, p, p, i32, i32, i32, p]
+    L.ld_detect.restype = C.c_int
+    L.ld_detect_host.argtypes = [p, p, p, i32, i32, i32, p]
+    L.ld_detect_host.restype = C.c_int
+    L.ld_debug_get.argtypes = [p, i32, i32, p, C.c_size_t]
+    L.ld_debug_get.restype = C.c_int
+    L.ld_debug_size.argtypes = [p, i32]
+    L.ld_debug_size.restype = C.c_size_t
+    L.ld_tables.argtypes = [P, p, p, p]
+    L.ld_tables.restype = C.c_int
+    L.ld_launches_per_detect.argtypes = []
+    L.ld_launches_per_detect.restype = i32
+    L.ld_launch_name.argtypes = [i32]
+    L.ld_launch_name.restype = C.c_char_p
+    L.ld_detect_timed.argtypes = [p, p, p, i32, i32, i32, p, p]
+    L.ld_detect_timed.restype = C.c_int
+    L.ld_last_error.argtypes = [p]
+    L.ld_last_error.restype = C.c_char_p
+    L.ld_destroy.argtypes = [p]
+    L.ld_destroy.restype = None
+    _lib = L
+    return L
+
+
+EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
+            "ld_debug_get", "ld_debug_size", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
+            "ld_destroy"]
+
+
+def launch_names():
+    L = load()
+    return [L.ld_launch_name(k).decode() for k in range(L.ld_launches_per_detect())]
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().ld_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def tables(p: Params | None = None):
+    p = p or default_params()
+    n = 2 * p.bf_rho + 1
+    ws = np.zeros(n * n, np.int32)
+    wr = np.zeros(256, np.int32)
+    wg = np.zeros(16385, np.int32)
+    rc = load().ld_tables(C.byref(p), ws.ctypes.data, wr.ctypes.data, wg.ctypes.data)
+    if rc != OK:
+        raise ValueError("invalid parameters")
+    return ws.reshape(n, n), wr, wg
+
+
+class LDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ld error {code}: {msg}")
+        self.code = code
+
+
+def lanes_to_dicts(arr: np.ndarray):
+    out = []
+    for r in arr:
+        n = int(r["n_lanes"])
+        out.append({"n_lanes": n, "flags": int(r["flags"]), "start_u": r["start_u"][:n].tolist(),
+                    "energy": r["energy"][:n].tolist(), "v_top": int(r["v_top"]), "centre": int(r["centre"]),
+                    "scale_exp": int(r["scale_exp"]), "rounds_y": int(r["rounds_y"]), "rounds_x": int(r["rounds_x"]),
+                    "beta": r["beta"].tolist(), "gamma": r["gamma"].tolist()})
+    return out
+
+
+class Detector:
+    """A library handle: workspace for frames up to max_w x max_h and batches up to max_batch."""
+
+    def __init__(self, max_w: int, max_h: int, max_batch: int, params: Params | None = None, stream=None):
+        import torch
+
+        self.L = load()
+        self.params = params if params is not None else default_params()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        rc = self.L.ld_create(C.byref(self.params), max_w, max_h, max_batch, C.c_void_p(stream.cuda_stream), C.byref(h))
+        if rc != OK:
+            raise LDError(rc, self.L.ld_last_error(None).decode())
+        self.h = h
+        self.max_w, self.max_h, self.max_batch = max_w, max_h, max_batch
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LDError(rc, self.L.ld_last_error(self.h).decode())
+
+    def n_starts(self, w: int) -> int:
+        return int(self.L.ld_n_starts(C.byref(self.params), w))
+
+    def alloc_lanes(self, n: int):
+        import torch
+
+        return torch.empty(n * LANES_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+
+    def detect(self, disp, img, out=None):
+        """Enqueue the path on device tensors disp [n,H,W] float32 and img [n,H,W] uint8.
+
+        Returns the device result buffer (uint8, n * 192 bytes); read it with lanes() after syncing.
+        """
+        assert disp.is_cuda and img.is_cuda and disp.dtype.itemsize == 4 and img.dtype.itemsize == 1
+        assert disp.is_contiguous() and img.is_contiguous() and disp.shape == img.shape
+        n, H, W = disp.shape
+        if out is None:
+            out = self.alloc_lanes(n)
+        self._check(self.L.ld_detect(self.h, disp.data_ptr(), img.data_ptr(), W, H, n, out.data_ptr()))
+        return out
+
+    @staticmethod
+    def lanes(out) -> np.ndarray:
+        return np.frombuffer(out.cpu().numpy().tobytes(), dtype=LANES_DTYPE)
+
+    def detect_host(self, disp: np.ndarray, img: np.ndarray) -> np.ndarray:
+        """Host buffers in, host results out (copies and kernels on the handle's stream, synchronous)."""
+        disp = np.ascontiguousarray(disp, np.float32)
+        img = np.ascontiguousarray(img, np.uint8)
+        n, H, W = disp.shape
+        res = np.zeros(n, LANES_DTYPE)
+        self._check(self.L.ld_detect_host(self.h, disp.ctypes.data, img.ctypes.data, W, H, n, res.ctypes.data))
+        return res
+
+    def detect_timed(self, disp, img, out):
+        """Eager launch with an event around every kernel; returns the per-kernel milliseconds."""
+        n, H, W = disp.shape
+        ms = np.zeros(self.L.ld_launches_per_detect(), np.float32)
+        self._check(self.L.ld_detect_timed(self.h, disp.data_ptr(), img.data_ptr(), W, H, n, out.data_ptr(),
+                                           ms.ctypes.data))
+        return ms
+
+    def detect_host_ptr(self, disp_ptr: int, img_ptr: int, W: int, H: int, n: int, res: np.ndarray):
+        self._check(self.L.ld_detect_host(self.h, disp_ptr, img_ptr, W, H, n, res.ctypes.data))
+
+    def debug(self, frame: int, stage: int, W: int, H: int):
+        size = int(self.L.ld_debug_size(self.h, stage))
+        buf = np.zeros(size, np.uint8)
+        self._check(self.L.ld_debug_get(self.h, frame, stage, buf.ctypes.data, size))
+        D = self.params.n_disp
+        if stage == STAGE_VDISP:
+            return buf.view(np.int32).reshape(H, D)
+        if stage == STAGE_PATH_Y:
+            return buf.view(np.int16)
+        if stage in (STAGE_INL_Y, STAGE_INL_X):
+            return buf
+        if stage == STAGE_ROWS:
+            return buf.view(np.float32).reshape(3, H)
+        if stage == STAGE_EDGES:
+            cnt = buf[:4 * H].view(np.int32)
+            ent = buf[4 * H:].view(np.int16).reshape(H, W, 4)
+            return cnt, ent
+        if stage == STAGE_PATH_X:
+            return buf.view(np.int16)
+        if stage == STAGE_M1:
+            return buf.view(np.int32).reshape(H, W)
+        if stage == STAGE_HE:
+            return buf.view(np.int64)
+        return buf
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ld_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
