@@ -886,9 +886,9 @@ int vpx_seg_rows(const KParams &kp, size_t budget)
 
 cudaError_t setup_fit(int smem_optin)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_road, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    cudaError_t e = allow_max_smem(k_road, smem_optin);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_vpx, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        e = allow_max_smem(k_vpx, smem_optin);
     return e;
 }
 

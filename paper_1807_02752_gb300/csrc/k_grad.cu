@@ -201,15 +201,15 @@ cudaError_t setup_grad(int smem_optin)
 {
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_grad<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        e = allow_max_smem(k_grad<1>, smem_optin);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_grad<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        e = allow_max_smem(k_grad<2>, smem_optin);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_grad<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        e = allow_max_smem(k_grad<3>, smem_optin);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_grad<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        e = allow_max_smem(k_grad<4>, smem_optin);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_grad<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        e = allow_max_smem(k_grad<5>, smem_optin);
     return e;
 }
 

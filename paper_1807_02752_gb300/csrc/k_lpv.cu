@@ -244,9 +244,9 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const 
 
 cudaError_t setup_lpv(int smem_optin)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_m1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    cudaError_t e = allow_max_smem(k_m1, smem_optin);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        e = allow_max_smem(k_select, smem_optin);
     return e;
 }
 

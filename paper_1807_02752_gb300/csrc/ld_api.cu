@@ -174,8 +174,8 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
     k.vote_cap = kVoteCap;
     const int n_ws = (2 * p.bf_rho + 1) * (2 * p.bf_rho + 1);
     for (int i = 0; i < n_ws; ++i)
-        k.ws[i] = (int16_t)h->ws_q[i];
-    k.seg_rows = ld::vpx_seg_rows(k, (size_t)h->smem_optin);
+        k.ws[i] = (uint16_t)h->ws_q[i];
+    k.seg_rows = ld::vpx_seg_rows(k, (size_t)h->smem_optin - 1024);
     return k;
 }
 
@@ -308,7 +308,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
 
     // backtrack rows that fit for the largest frame decide the number of DP checkpoints
     ld::KParams kmax = make_kparams(h, max_w, max_h, max_batch);
-    if (kmax.seg_rows < 1 || ld::road_smem_bytes(kmax) > (size_t)h->smem_optin) {
+    if (kmax.seg_rows < 1 || ld::road_smem_bytes(kmax) > (size_t)h->smem_optin - 1024) {
         delete h;
         return fail(nullptr, LD_E_ARG, "frame too large for the shared-memory budget");
     }

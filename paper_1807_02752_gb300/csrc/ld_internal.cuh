@@ -37,7 +37,7 @@ struct KParams {
     int32_t centre, e;                 // polynomial basis tau = (v - centre) / 2^e
     int32_t seg_rows;                  // rows of DP backtrack held in shared memory by the V_px kernel
     int32_t vote_cap;                  // votes per frame the V_px kernel stages in shared memory
-    int16_t ws[121];                   // Eq. 16 spatial weights, Q15, (2 rho + 1)^2 used
+    uint16_t ws[121];                  // Eq. 16 spatial weights, Q15 (up to 32768), (2 rho + 1)^2 used
 };
 
 // Per-frame state written by the fit kernels and read downstream.
@@ -97,6 +97,17 @@ __device__ __forceinline__ double i128_to_f64(__int128 x)
 }
 
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// Allow a kernel the largest dynamic shared memory the device offers next to its static shared memory.
+template <typename K>
+inline cudaError_t allow_max_smem(K kernel, int smem_optin)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)a.sharedSizeBytes);
+}
 
 // Polynomial value in float32 (Horner, two roundings per step) and the inlier test (y - g)^2 < tr.
 template <int M>
