@@ -11,8 +11,9 @@
 
 namespace {
 
-constexpr int kLaunches = 7;
-const char *const kLaunchNames[kLaunches] = {"k_vdisp", "k_road", "k_grad", "k_vpx", "k_m1", "k_energy", "k_select"};
+constexpr int kLaunches = 9;
+const char *const kLaunchNames[kLaunches] = {"k_vdisp", "k_road_dp", "k_fit_y", "k_grad", "k_vpx_dp",
+                                             "k_fit_x", "k_m1", "k_energy", "k_select"};
 constexpr int kGraphSlots = 4;
 constexpr int kVoteCap = 12288;
 
@@ -193,10 +194,12 @@ int enqueue(ld_handle *h, const ld::KParams &kp, const float *disp, const uint8_
         switch (k) {
         case 0: e = ld::launch_vdisp(kp, h->w, disp, s); break;
         case 1: e = ld::launch_road(kp, h->w, s); break;
-        case 2: e = ld::launch_grad(kp, h->w, disp, img, s); break;
-        case 3: e = ld::launch_vpx(kp, h->w, s); break;
-        case 4: e = ld::launch_m1(kp, h->w, s); break;
-        case 5: e = ld::launch_energy(kp, h->w, s); break;
+        case 2: e = ld::launch_fit_y(kp, h->w, s); break;
+        case 3: e = ld::launch_grad(kp, h->w, disp, img, s); break;
+        case 4: e = ld::launch_vpx(kp, h->w, s); break;
+        case 5: e = ld::launch_fit_x(kp, h->w, s); break;
+        case 6: e = ld::launch_m1(kp, h->w, s); break;
+        case 7: e = ld::launch_energy(kp, h->w, s); break;
         default: e = ld::launch_select(kp, h->w, out, s); break;
         }
         if (e != cudaSuccess)
@@ -312,7 +315,15 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
         delete h;
         return fail(nullptr, LD_E_ARG, "frame too large for the shared-memory budget");
     }
+    // DP energies stay far below the int32 sentinel of the DP kernels
+    const double e_x = ((double)p->vote_rho * (2.0 * p->chi + 1.0) * max_w + (double)p->lambda_x * p->tau_x) * max_h;
+    const double e_y = ((double)max_w + (double)p->lambda_y * p->tau_y) * p->n_disp;
+    if (e_x >= 1073741824.0 || e_y >= 1073741824.0) {
+        delete h;
+        return fail(nullptr, LD_E_ARG, "vote_rho, chi, lambda and the frame size allow DP energies beyond 2^30");
+    }
     const size_t n = max_batch, W = max_w, H = max_h, D = p->n_disp;
+    const size_t pmax = D > H ? D : H;
     const int max_seg = (int)((H - 1 + kmax.seg_rows - 1) / kmax.seg_rows) + 1;
     const size_t n_starts = (size_t)ld_n_starts(p, max_w);
     size_t off = 0;
@@ -325,6 +336,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     const size_t o_py = take(n * D * 2), o_iy = take(n * D), o_ec = take(n * H * 4), o_ed = take(n * H * W * 8);
     const size_t o_vc = take(n * H * 4), o_vb = take(n * H * W * 2), o_px = take(n * H * 2), o_ix = take(n * H);
     const size_t o_ck = take(n * max_seg * 2 * W * 4), o_m1 = take(n * H * W * 4), o_he = take(n * n_starts * 8);
+    const size_t o_pts = take(n * 2 * 3 * pmax * 2), o_np = take(n * 2 * 4);
     const size_t o_tab = take(sizeof(int32_t) * (ld::kWrEntries + ld::kWgEntries));
     const size_t o_d = take(n * H * W * 4), o_i = take(n * H * W), o_l = take(n * sizeof(ld_lanes));
     e = cudaMalloc(&h->ws, off);
@@ -349,6 +361,9 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     w.ckpt = (int32_t *)(b + o_ck);
     w.M1 = (int32_t *)(b + o_m1);
     w.HE = (int64_t *)(b + o_he);
+    w.pts = (int16_t *)(b + o_pts);
+    w.npts = (int32_t *)(b + o_np);
+    w.pmax = (int32_t)pmax;
     h->d_tables = (int32_t *)(b + o_tab);
     w.wr = h->d_tables;
     w.wg = h->d_tables + ld::kWrEntries;
@@ -369,7 +384,9 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
         tab[k] = 0;
     e = cudaMemcpy(h->d_tables, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = ld::setup_fit(h->smem_optin);
+        e = ld::setup_dp(h->smem_optin);
+    if (e == cudaSuccess)
+        e = ld::setup_ransac(h->smem_optin);
     if (e == cudaSuccess)
         e = ld::setup_grad(h->smem_optin);
     if (e == cudaSuccess)

@@ -60,12 +60,14 @@ struct Work {
     int16_t *vbins;      // [n][H][W] vote columns of each row
     int16_t *path_x;     // [n][H]
     uint8_t *inl_x;      // [n][H]
+    int16_t *pts;        // [n][2][3][pmax] DP path points with data (x, y, index) for the beta / gamma fits
+    int32_t *npts;       // [n][2]
     int32_t *ckpt;       // [n][max_seg][2][W] DP checkpoints (E row, band row)
     int32_t *M1;         // [n][H][W]
     int64_t *HE;         // [n][n_starts]
     const int32_t *wr;   // [kWrEntries] Q15
     const int32_t *wg;   // [kWgEntries] Q12
-    int32_t max_w, max_h, max_seg;
+    int32_t max_w, max_h, max_seg, pmax;
 };
 
 // ---------------------------------------------------------------------------------------------------
@@ -139,6 +141,8 @@ __device__ __forceinline__ double poly_f64(const double *c, double tau)
 namespace ld {
 cudaError_t launch_vdisp(const KParams &kp, const Work &w, const float *disp, cudaStream_t s);
 cudaError_t launch_road(const KParams &kp, const Work &w, cudaStream_t s);
+cudaError_t launch_fit_y(const KParams &kp, const Work &w, cudaStream_t s);
+cudaError_t launch_fit_x(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_grad(const KParams &kp, const Work &w, const float *disp, const uint8_t *img, cudaStream_t s);
 cudaError_t launch_vpx(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s);
@@ -147,7 +151,8 @@ cudaError_t launch_select(const KParams &kp, const Work &w, ld_lanes *out, cudaS
 size_t road_smem_bytes(const KParams &kp);
 size_t vpx_smem_bytes(const KParams &kp);
 int vpx_seg_rows(const KParams &kp, size_t budget);
-cudaError_t setup_fit(int smem_optin);
+cudaError_t setup_dp(int smem_optin);
+cudaError_t setup_ransac(int smem_optin);
 cudaError_t setup_grad(int smem_optin);
 cudaError_t setup_lpv(int smem_optin);
 }  // namespace ld
