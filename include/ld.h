@@ -170,6 +170,32 @@ const char *ld_launch_name(int32_t k);
 int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t h_px,
                     int32_t n_frames, ld_lanes *out_lanes, float *ms_out);
 
+/*
+ * Allocation-free road-profile path.  The paper has no counterpart: this entry point exists for callers
+ * that may not allocate device memory where they need the result, for example software whose memory is
+ * all reserved at start-up (safety-certified driving stacks forbid allocation in the per-frame path) or a
+ * plugin whose host application hands it only its input and output buffers.
+ *
+ * It computes, for n_frames frames, the v-disparity histogram (Sec. 2.2) and the DP path of Eq. 11-12 with
+ * the same readings and tie rules as ld_detect, and writes the path row v_d of each bin d to
+ * path_out[frame][d] (int16, n_disp entries per frame, entry 0 = -1) - the values ld_debug_get returns for
+ * LD_STAGE_PATH_Y after ld_detect.  disp is a DEVICE pointer to float32 [n_frames][h][w], path_out a DEVICE
+ * pointer; the caller owns both.  Only p->n_disp, p->tau_y and p->lambda_y are used.  The work is enqueued
+ * on cuda_stream (NULL = default stream) and the call returns without waiting.
+ *
+ * No cudaMalloc, cudaFree or allocating library routine is called.  The histogram scratch is a static
+ * device array of LD_STATIC_SCRATCH_BYTES bytes inside the library, which every GPU that loads the library
+ * keeps until the process exits; a request needing more (n_frames * n_disp * h * 4 bytes) returns LD_E_ARG.
+ * The first call on each device, with that device current, looks up the array's device address and
+ * configures the kernel; make that first call before any stream capture.  Every call shares the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race on it, so serialise them.  Each
+ * call overwrites every scratch entry it reads, so no stale contents leak between calls.
+ * Errors (message in ld_last_error(NULL)): LD_E_ARG, LD_E_CUDA.
+ */
+#define LD_STATIC_SCRATCH_BYTES (8u << 20)
+int ld_road_path_static(const ld_params *p, const float *disp, int32_t w, int32_t h_px, int32_t n_frames,
+                        int16_t *path_out, void *cuda_stream);
+
 /* Message of the last error on h (or of the last failed ld_create when h is NULL). */
 const char *ld_last_error(const ld_handle *h);
 

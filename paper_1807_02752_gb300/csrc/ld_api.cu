@@ -225,6 +225,10 @@ int check_call(ld_handle *h, const void *disp, const void *img, int w, int hh, i
 
 }  // namespace
 
+namespace ld {
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace ld
+
 extern "C" {
 
 void ld_params_default(ld_params *p)

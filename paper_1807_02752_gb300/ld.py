@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libld.so")
 
 MAX_LANES = 8
+LD_STATIC_SCRATCH_BYTES = 8 << 20
 OK, E_ARG, E_CUDA, E_NOMEM, E_STATE = 0, -1, -2, -3, -4
 F_NO_ROAD, F_CAP_Y, F_DEGEN_Y, F_CAP_X, F_DEGEN_X, F_NO_LANES = 1, 2, 4, 8, 16, 32
 STAGE_VDISP, STAGE_PATH_Y, STAGE_INL_Y, STAGE_ROWS, STAGE_EDGES, STAGE_PATH_X, STAGE_INL_X, STAGE_M1, STAGE_HE = range(1, 10)
@@ -82,13 +83,15 @@ def load():
     L.ld_last_error.restype = C.c_char_p
     L.ld_destroy.argtypes = [p]
     L.ld_destroy.restype = None
+    L.ld_road_path_static.argtypes = [P, p, i32, i32, i32, p, p]
+    L.ld_road_path_static.restype = C.c_int
     _lib = L
     return L
 
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
             "ld_debug_get", "ld_debug_size", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
-            "ld_destroy"]
+            "ld_destroy", "ld_road_path_static"]
 
 
 def launch_names():
