@@ -1,13 +1,22 @@
 // Sec. 2.3.1: road mask, bilateral filter (Eq. 15-16), Sobel gradients, edge test and sparse V_px votes
 // (Eq. 17), for the road rows of every frame.
 //
-// One CTA covers R output rows of one frame across the full width.  It stages the image rows the 11x11
-// window needs (R + 2 + 2 rho rows) in shared memory, with a sentinel value outside the frame whose range
-// weight is 0 (this is the clipped window of Eq. 15).  The bilateral output is computed only at pixels
-// whose 3x3 neighbourhood holds an interior road pixel: those are the only values the Sobel stencil and
-// the edge test read (Sec. 2.3.1: "we only focus on the pixels on the road surface").  Weights are Q15
-// integers, w = (ws * wr + 2^14) >> 15, sums are exact, and the output is (2 sum(w I) + sum(w)) / (2 sum(w)),
-// so the result does not depend on the order of the taps.
+// One CTA covers R output rows of one frame across the full width.  It stages the image rows the
+// (2 rho + 1)^2 window needs in shared memory, with a sentinel value outside the frame whose range weight
+// is 0 (this is the clipped window of Eq. 15).  The bilateral output is computed only at pixels whose
+// 3x3 neighbourhood holds an interior road pixel: those are the only values the Sobel stencil and the edge
+// test read (Sec. 2.3.1 keeps only the road surface).  Weights are Q15 integers,
+// w = (ws * wr[|I(i,j) - I(u,v)|] + 2^14) >> 15, sums are exact, and the output is
+// (2 sum(w I) + sum(w)) / (2 sum(w)), so the result does not depend on the order of the taps.
+//
+// GB300 mapping of the bilateral (the cost of the whole path sits here):
+//   - taps at equal distance share ws, so w depends only on (distance class, I(i,j) - I(u,v)); the CTA
+//     builds one 768-entry uint16 table per class in shared memory and a tap costs one table load, an
+//     address add and two accumulations;
+//   - the tile stores 2 I (a byte offset into a table), so the table address is base_c + 2 I(i,j) + class
+//     offset, and sum(w 2 I) keeps the same exact arithmetic;
+//   - a thread filters 4 horizontally adjacent pixels, sharing each window row it loads as 64-bit vectors;
+//   - pixel groups that need the filter are compacted first, so warps do not diverge on the road mask.
 //
 // Each road pixel with G_x^2 + G_y^2 > thr^2 is an edge pixel.  Its vote column is
 // floor(u + (v - V_py(v)) G_y / G_x + 0.5) in float32 (the line through the pixel perpendicular to the
@@ -20,6 +29,81 @@ namespace ld {
 namespace {
 
 constexpr int kThreads = 512;
+constexpr int kTabBytes = kWrEntries * 2;  // one uint16 table per distance class
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr)
+{
+    uint16_t v;
+    asm("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
+}
+
+struct GradLayout {
+    int TWP, IW, NG, TR, BR;
+};
+
+template <int RHO>
+__host__ __device__ inline GradLayout grad_layout(int W, int nr)
+{
+    constexpr int NL = (4 + 2 * RHO + 3) / 4;  // 4-value loads per window row of a 4-pixel group
+    GradLayout L;
+    L.IW = (W + 3) & ~3;
+    L.TWP = L.IW + 4 * NL;
+    L.NG = L.IW / 4;
+    L.TR = nr + 2 + 2 * RHO;
+    L.BR = nr + 2;
+    return L;
+}
+
+// Bilateral output of the 4 pixels (br, u0 .. u0+3); tile holds 2 I with the sentinel outside the frame.
+template <int RHO>
+__device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t *tile, int TWP, int br, int u0, int W,
+                                               uint32_t tab)
+{
+    constexpr int N = 2 * RHO + 1;
+    constexpr int NL = (4 + 2 * RHO + 3) / 4;
+    const uint16_t *crow = tile + (size_t)(br + RHO) * TWP + u0 + RHO;
+    uint32_t base[4], num[4], den[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t c2 = (u0 + p < W) ? crow[p] : 0u;  // pixels past the right edge: any valid index
+        base[p] = tab + 512u - c2;
+        num[p] = 0u;
+        den[p] = 0u;
+    }
+#pragma unroll
+    for (int dy = 0; dy < N; ++dy) {
+        const uint2 *rowp = reinterpret_cast<const uint2 *>(tile + (size_t)(br + dy) * TWP + u0);
+        uint32_t q[4 * NL];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const uint2 v = rowp[l];
+            q[4 * l] = v.x & 0xffffu;
+            q[4 * l + 1] = v.x >> 16;
+            q[4 * l + 2] = v.y & 0xffffu;
+            q[4 * l + 3] = v.y >> 16;
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+#pragma unroll
+            for (int dx = 0; dx < N; ++dx) {
+                const uint32_t qq = q[p + dx];
+                const uint32_t wq = lds_u16(base[p] + qq + kp.cls_off[dy * N + dx]);
+                num[p] += wq * qq;
+                den[p] += wq;
+            }
+        }
+    }
+    uint32_t out = 0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const uint32_t b = den[p] ? (num[p] + den[p]) / (2u * den[p]) : 0u;  // (2 sum(wI) + sum(w)) / (2 sum(w))
+        out |= (b & 0xffu) << (8 * p);
+    }
+    return out;
+}
 
 template <int RHO>
 __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work w, const float *__restrict__ disp,
@@ -30,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
     const int f = blockIdx.y;
     const int r0 = blockIdx.x * R;
     const int nr = min(R, H - r0);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const FrameState &fs = w.fs[f];
     const int vtop = fs.v_top;
     int32_t *ecnt = w.ecount + (size_t)f * H;
@@ -42,41 +126,45 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
         }
         return;
     }
+    const GradLayout L = grad_layout<RHO>(W, R);
+    const int TR = nr + 2 + 2 * RHO, BR = nr + 2;
 
-    const int TW = W + 2 * RHO;             // tile width (columns -RHO .. W-1+RHO)
-    const int TR = nr + 2 + 2 * RHO;        // tile rows (r0-1-RHO .. r0+nr+RHO)
-    const int BR = nr + 2;                  // bilateral rows (r0-1 .. r0+nr)
     unsigned char *p = smem;
-    int32_t *wr = reinterpret_cast<int32_t *>(p);
+    uint16_t *tabs = reinterpret_cast<uint16_t *>(p);           // [n_cls][768]
+    p += (size_t)kTabBytes * kp.n_cls;
+    int32_t *wr = reinterpret_cast<int32_t *>(p);               // [768]
     p += sizeof(int32_t) * kWrEntries;
-    int32_t *cnt = reinterpret_cast<int32_t *>(p);  // [2][R]: edges, votes per row
-    p += sizeof(int32_t) * 2 * R;
+    int32_t *cnt = reinterpret_cast<int32_t *>(p);              // [2][R] edges, votes per row; [2R] groups
+    p += sizeof(int32_t) * (2 * R + 4);
     float *rowF = reinterpret_cast<float *>(p);
     p += sizeof(float) * R;
     float *rowVy = reinterpret_cast<float *>(p);
     p += sizeof(float) * R;
-    uint16_t *tile = reinterpret_cast<uint16_t *>(p);
-    p += sizeof(uint16_t) * (size_t)TR * TW;
     p = reinterpret_cast<unsigned char *>(((size_t)p + 15) & ~(size_t)15);
-    uint8_t *ibf = p;
-    p += (size_t)BR * W;
-    uint8_t *road = p;                      // [nr][W]
+    uint16_t *tile = reinterpret_cast<uint16_t *>(p);           // [TR][TWP] 2 I, or 2 x sentinel
+    p += sizeof(uint16_t) * (size_t)L.TR * L.TWP;
+    uint8_t *ibf = p;                                           // [BR][IW]
+    p += (size_t)L.BR * L.IW;
+    uint8_t *road = p;                                          // [R][W]
+    p += (size_t)R * W;
+    p = reinterpret_cast<unsigned char *>(((size_t)p + 15) & ~(size_t)15);
+    int32_t *glist = reinterpret_cast<int32_t *>(p);            // [BR * NG] groups that need the filter
 
     for (int i = tid; i < kWrEntries; i += kThreads)
         wr[i] = w.wr[i];
-    for (int i = tid; i < 2 * R; i += kThreads)
+    for (int i = tid; i < 2 * R + 4; i += kThreads)
         cnt[i] = 0;
     const float *rows = w.rows + (size_t)f * 3 * H;
     for (int r = tid; r < nr; r += kThreads) {
         rowF[r] = rows[r0 + r];
         rowVy[r] = rows[H + r0 + r];
     }
-    // image tile with the sentinel outside the frame
     const uint8_t *im = img + (size_t)f * H * W;
-    for (int i = tid; i < TR * TW; i += kThreads) {
-        const int tr = i / TW, tc = i - tr * TW;
+    for (int i = tid; i < TR * L.TWP; i += kThreads) {
+        const int tr = i / L.TWP, tc = i - tr * L.TWP;
         const int v = r0 - 1 - RHO + tr, u = tc - RHO;
-        tile[i] = (v >= 0 && v < H && u >= 0 && u < W) ? (uint16_t)__ldg(im + (size_t)v * W + u) : (uint16_t)kSentinel;
+        tile[i] = (v >= 0 && v < H && u >= 0 && u < W) ? (uint16_t)(2u * __ldg(im + (size_t)v * W + u))
+                                                       : (uint16_t)(2 * kSentinel);
     }
     // road mask of the interior pixels of this CTA's rows: finite l > 0 with |l - f(v)| <= varpi, v >= v_top
     const float *dsp = disp + (size_t)f * H * W;
@@ -91,43 +179,50 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
         road[i] = m;
     }
     __syncthreads();
-
-    // bilateral output where the Sobel stencil of a road pixel reads it
-    for (int i = tid; i < BR * W; i += kThreads) {
-        const int br = i / W, u = i - br * W;   // bilateral row br <-> image row r0 - 1 + br
+    // per-class weight tables: T_c[k] = (ws_c * wr[k] + 2^14) >> 15, k = q - c + 256
+    for (int i = tid; i < kp.n_cls * kWrEntries; i += kThreads) {
+        const int c = i / kWrEntries, k = i - c * kWrEntries;
+        tabs[i] = (uint16_t)(((uint32_t)kp.cls_ws[c] * (uint32_t)wr[k] + 16384u) >> 15);
+    }
+    // groups of 4 pixels of the bilateral rows (r0-1 .. r0+nr) holding a pixel the Sobel stencil reads
+    for (int g0 = 0; g0 < BR * L.NG; g0 += kThreads) {
+        const int g = g0 + tid;
         bool need = false;
+        if (g < BR * L.NG) {
+            const int br = g / L.NG, u0 = 4 * (g - br * L.NG);
 #pragma unroll
-        for (int dr = -1; dr <= 1; ++dr) {
-            const int rr = br - 1 + dr;          // road-mask row
-            if (rr < 0 || rr >= nr)
-                continue;
-#pragma unroll
-            for (int du = -1; du <= 1; ++du) {
-                const int uu = u + du;
-                need |= uu >= 0 && uu < W && road[rr * W + uu];
+            for (int dr = -1; dr <= 1; ++dr) {
+                const int rr = br - 1 + dr;
+                if (rr < 0 || rr >= nr)
+                    continue;
+                const uint8_t *rm = road + (size_t)rr * W;
+                for (int u = max(u0 - 1, 0); u <= min(u0 + 4, W - 1); ++u)
+                    need |= rm[u] != 0;
             }
         }
-        if (!need)
-            continue;
-        const uint16_t *t0 = tile + (size_t)br * TW + u;  // window rows br .. br + 2 RHO, columns u .. u + 2 RHO
-        const int c = t0[RHO * TW + RHO];
-        if (!kp.bilateral) {
-            ibf[i] = (uint8_t)c;
-            continue;
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        int base = 0;
+        if (lane == 0 && m)
+            base = atomicAdd(&cnt[2 * R], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (need)
+            glist[base + __popc(m & ((1u << lane) - 1u))] = g;
+    }
+    __syncthreads();
+    const int ng = cnt[2 * R];
+    const uint32_t tab = smem_addr(tabs);
+    for (int k = tid; k < ng; k += kThreads) {
+        const int g = glist[k];
+        const int br = g / L.NG, u0 = 4 * (g - br * L.NG);
+        uint32_t out;
+        if (kp.bilateral) {
+            out = bilateral4<RHO>(kp, tile, L.TWP, br, u0, W, tab);
+        } else {
+            const uint16_t *c = tile + (size_t)(br + RHO) * L.TWP + u0 + RHO;
+            out = (uint32_t)(c[0] >> 1) | ((uint32_t)(c[1] >> 1) << 8) | ((uint32_t)(c[2] >> 1) << 16) |
+                  ((uint32_t)(c[3] >> 1) << 24);
         }
-        const int32_t *wrc = wr + 256 - c;
-        unsigned num = 0, den = 0;
-#pragma unroll
-        for (int dy = 0; dy <= 2 * RHO; ++dy) {
-#pragma unroll
-            for (int dx = 0; dx <= 2 * RHO; ++dx) {
-                const int q = t0[dy * TW + dx];
-                const int wq = (kp.ws[dy * (2 * RHO + 1) + dx] * wrc[q] + 16384) >> 15;
-                num += (unsigned)(wq * q);
-                den += (unsigned)wq;
-            }
-        }
-        ibf[i] = (uint8_t)((2u * num + den) / (2u * den));
+        *reinterpret_cast<uint32_t *>(ibf + (size_t)br * L.IW + u0) = out;
     }
     __syncthreads();
 
@@ -140,9 +235,9 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
             continue;
         const int r = i / W, u = i - r * W;
         const int v = r0 + r;
-        const uint8_t *a = ibf + (size_t)r * W;        // row v-1
-        const uint8_t *b = a + W;                       // row v
-        const uint8_t *cc = b + W;                      // row v+1
+        const uint8_t *a = ibf + (size_t)r * L.IW;      // row v-1
+        const uint8_t *b = a + L.IW;                      // row v
+        const uint8_t *cc = b + L.IW;                     // row v+1
         const int gx = ((int)a[u + 1] - (int)a[u - 1]) + 2 * ((int)b[u + 1] - (int)b[u - 1]) + ((int)cc[u + 1] - (int)cc[u - 1]);
         const int gy = ((int)cc[u - 1] - (int)a[u - 1]) + 2 * ((int)cc[u] - (int)a[u]) + ((int)cc[u + 1] - (int)a[u + 1]);
         if (gx * gx + gy * gy <= thr2)
@@ -173,23 +268,25 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
 }
 
 template <int RHO>
-size_t grad_smem(int W, int R)
+size_t grad_smem(int W, int R, int n_cls)
 {
-    const int nr = R;
-    size_t s = sizeof(int32_t) * kWrEntries + sizeof(int32_t) * 2 * R + 2 * sizeof(float) * R;
-    s += sizeof(uint16_t) * (size_t)(nr + 2 + 2 * RHO) * (W + 2 * RHO);
+    const GradLayout L = grad_layout<RHO>(W, R);
+    size_t s = (size_t)kTabBytes * n_cls + sizeof(int32_t) * kWrEntries + sizeof(int32_t) * (2 * R + 4) +
+               2 * sizeof(float) * R;
     s = (s + 15) & ~(size_t)15;
-    s += (size_t)(nr + 2) * W + (size_t)nr * W;
+    s += sizeof(uint16_t) * (size_t)L.TR * L.TWP + (size_t)L.BR * L.IW + (size_t)R * W;
+    s = (s + 15) & ~(size_t)15;
+    s += sizeof(int32_t) * (size_t)L.BR * L.NG;
     return s + 16;
 }
 
 template <int RHO>
 cudaError_t launch_grad_t(const KParams &kp, const Work &w, const float *disp, const uint8_t *img, cudaStream_t s)
 {
-    int R = 8;
-    while (R > 1 && grad_smem<RHO>(kp.W, R) > 100 * 1024)
+    int R = 16;
+    while (R > 1 && grad_smem<RHO>(kp.W, R, kp.n_cls) > 200 * 1024)
         --R;
-    const size_t smem = grad_smem<RHO>(kp.W, R);
+    const size_t smem = grad_smem<RHO>(kp.W, R, kp.n_cls);
     dim3 grid((kp.H + R - 1) / R, kp.n_frames);
     k_grad<RHO><<<grid, kThreads, smem, s>>>(kp, w, disp, img, R);
     return cudaGetLastError();

@@ -176,6 +176,25 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
     const int n_ws = (2 * p.bf_rho + 1) * (2 * p.bf_rho + 1);
     for (int i = 0; i < n_ws; ++i)
         k.ws[i] = (uint16_t)h->ws_q[i];
+    // distance classes of the bilateral taps: rank of dx^2 + dy^2 among the distinct values
+    {
+        const int rho = p.bf_rho, nn = 2 * rho + 1;
+        bool seen[2 * 5 * 5 + 1] = {};
+        for (int dy = -rho; dy <= rho; ++dy)
+            for (int dx = -rho; dx <= rho; ++dx)
+                seen[dx * dx + dy * dy] = true;
+        int rank[2 * 5 * 5 + 1] = {}, nc = 0;
+        for (int r2 = 0; r2 <= 2 * rho * rho; ++r2)
+            if (seen[r2])
+                rank[r2] = nc++;
+        k.n_cls = nc;
+        for (int dy = -rho; dy <= rho; ++dy)
+            for (int dx = -rho; dx <= rho; ++dx) {
+                const int c = rank[dx * dx + dy * dy];
+                k.cls_off[(dy + rho) * nn + dx + rho] = (uint16_t)(c * ld::kWrEntries * 2);
+                k.cls_ws[c] = (uint16_t)h->ws_q[(dy + rho) * nn + dx + rho];
+            }
+    }
     k.seg_rows = ld::vpx_seg_rows(k, (size_t)h->smem_optin - 1024);
     return k;
 }
