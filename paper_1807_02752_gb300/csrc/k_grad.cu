@@ -58,6 +58,9 @@ __host__ __device__ inline GradLayout grad_layout(int W, int nr)
 }
 
 // Bilateral output of the 4 pixels (br, u0 .. u0+3); tile holds 2 I with the sentinel outside the frame.
+// Per tap one 64-bit multiply-add accumulates both sums: acc += w * (2^31 + 2 I) keeps sum(w) in the bits
+// from 31 up and sum(w 2 I) < 2^31 below them.  The table address is formed modulo 2^32 from the same
+// 2^31 + 2 I operand (the base carries -2^31).
 template <int RHO>
 __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t *tile, int TWP, int br, int u0, int W,
                                                uint32_t tab)
@@ -65,13 +68,13 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
     constexpr int N = 2 * RHO + 1;
     constexpr int NL = (4 + 2 * RHO + 3) / 4;
     const uint16_t *crow = tile + (size_t)(br + RHO) * TWP + u0 + RHO;
-    uint32_t base[4], num[4], den[4];
+    uint32_t base[4];
+    unsigned long long acc[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const uint32_t c2 = (u0 + p < W) ? crow[p] : 0u;  // pixels past the right edge: any valid index
-        base[p] = tab + 512u - c2;
-        num[p] = 0u;
-        den[p] = 0u;
+        base[p] = tab + 512u - c2 - 0x80000000u;
+        acc[p] = 0ull;
     }
 #pragma unroll
     for (int dy = 0; dy < N; ++dy) {
@@ -80,10 +83,10 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             const uint2 v = rowp[l];
-            q[4 * l] = v.x & 0xffffu;
-            q[4 * l + 1] = v.x >> 16;
-            q[4 * l + 2] = v.y & 0xffffu;
-            q[4 * l + 3] = v.y >> 16;
+            q[4 * l] = __byte_perm(v.x, 0x80000000u, 0x7410);
+            q[4 * l + 1] = __byte_perm(v.x, 0x80000000u, 0x7432);
+            q[4 * l + 2] = __byte_perm(v.y, 0x80000000u, 0x7410);
+            q[4 * l + 3] = __byte_perm(v.y, 0x80000000u, 0x7432);
         }
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -91,30 +94,31 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
             for (int dx = 0; dx < N; ++dx) {
                 const uint32_t qq = q[p + dx];
                 const uint32_t wq = lds_u16(base[p] + qq + kp.cls_off[dy * N + dx]);
-                num[p] += wq * qq;
-                den[p] += wq;
+                acc[p] += (unsigned long long)wq * qq;
             }
         }
     }
     uint32_t out = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-        const uint32_t b = den[p] ? (num[p] + den[p]) / (2u * den[p]) : 0u;  // (2 sum(wI) + sum(w)) / (2 sum(w))
+        const uint32_t den = (uint32_t)(acc[p] >> 31), num2 = (uint32_t)acc[p] & 0x7fffffffu;
+        const uint32_t b = den ? (num2 + den) / (2u * den) : 0u;  // (2 sum(wI) + sum(w)) / (2 sum(w))
         out |= (b & 0xffu) << (8 * p);
     }
     return out;
 }
 
 template <int RHO>
-__global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work w, const float *__restrict__ disp,
-                                                   const uint8_t *__restrict__ img, int R)
+__global__ void __launch_bounds__(kThreads, 2) k_grad(const KParams kp, const Work w, const float *__restrict__ disp,
+                                                      const uint8_t *__restrict__ img, int R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NW = kThreads / 32;
     const int W = kp.W, H = kp.H;
     const int f = blockIdx.y;
     const int r0 = blockIdx.x * R;
     const int nr = min(R, H - r0);
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const FrameState &fs = w.fs[f];
     const int vtop = fs.v_top;
     int32_t *ecnt = w.ecount + (size_t)f * H;
@@ -132,8 +136,6 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
     unsigned char *p = smem;
     uint16_t *tabs = reinterpret_cast<uint16_t *>(p);           // [n_cls][768]
     p += (size_t)kTabBytes * kp.n_cls;
-    int32_t *wr = reinterpret_cast<int32_t *>(p);               // [768]
-    p += sizeof(int32_t) * kWrEntries;
     int32_t *cnt = reinterpret_cast<int32_t *>(p);              // [2][R] edges, votes per row; [2R] groups
     p += sizeof(int32_t) * (2 * R + 4);
     float *rowF = reinterpret_cast<float *>(p);
@@ -143,12 +145,13 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
     p = reinterpret_cast<unsigned char *>(((size_t)p + 15) & ~(size_t)15);
     uint16_t *tile = reinterpret_cast<uint16_t *>(p);           // [TR][TWP] 2 I, or 2 x sentinel
     p += sizeof(uint16_t) * (size_t)L.TR * L.TWP;
-    uint8_t *ibf = p;                                           // [BR][IW]
-    p += (size_t)L.BR * L.IW;
-    uint8_t *road = p;                                          // [R][W]
-    p += (size_t)R * W;
+    uint8_t *ibf = p;                                           // [BR][IW]; first holds the range LUT
+    int32_t *wr = reinterpret_cast<int32_t *>(p);               // [768], dead once the class tables exist
+    p += L.BR * L.IW > (int)sizeof(int32_t) * kWrEntries ? (size_t)L.BR * L.IW : sizeof(int32_t) * kWrEntries;
+    uint8_t *road = p;                                          // [R][IW]
+    p += (size_t)R * L.IW;
     p = reinterpret_cast<unsigned char *>(((size_t)p + 15) & ~(size_t)15);
-    int32_t *glist = reinterpret_cast<int32_t *>(p);            // [BR * NG] groups that need the filter
+    uint16_t *glist = reinterpret_cast<uint16_t *>(p);          // [BR * NG] groups that need the filter
 
     for (int i = tid; i < kWrEntries; i += kThreads)
         wr[i] = w.wr[i];
@@ -160,53 +163,66 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
         rowVy[r] = rows[H + r0 + r];
     }
     const uint8_t *im = img + (size_t)f * H * W;
-    for (int i = tid; i < TR * L.TWP; i += kThreads) {
-        const int tr = i / L.TWP, tc = i - tr * L.TWP;
-        const int v = r0 - 1 - RHO + tr, u = tc - RHO;
-        tile[i] = (v >= 0 && v < H && u >= 0 && u < W) ? (uint16_t)(2u * __ldg(im + (size_t)v * W + u))
-                                                       : (uint16_t)(2 * kSentinel);
+    for (int tr = warp; tr < TR; tr += NW) {
+        const int v = r0 - 1 - RHO + tr;
+        const bool in = v >= 0 && v < H;
+        const uint8_t *src = im + (size_t)(in ? v : 0) * W;
+        uint16_t *dst = tile + (size_t)tr * L.TWP;
+        for (int tc = lane; tc < L.TWP; tc += 32) {
+            const int u = tc - RHO;
+            dst[tc] = (in && u >= 0 && u < W) ? (uint16_t)(2u * __ldg(src + u)) : (uint16_t)(2 * kSentinel);
+        }
     }
     // road mask of the interior pixels of this CTA's rows: finite l > 0 with |l - f(v)| <= varpi, v >= v_top
     const float *dsp = disp + (size_t)f * H * W;
-    for (int i = tid; i < nr * W; i += kThreads) {
-        const int r = i / W, u = i - r * W;
+    for (int r = warp; r < nr; r += NW) {
         const int v = r0 + r;
-        uint8_t m = 0;
-        if (v >= vtop && v >= 1 && v <= H - 2 && u >= 1 && u <= W - 2) {
-            const float l = __ldg(dsp + (size_t)v * W + u);
-            m = l > 0.0f && l < __int_as_float(0x7f800000) && fabsf(__fsub_rn(l, rowF[r])) <= kp.varpi;
+        const bool rowok = v >= vtop && v >= 1 && v <= H - 2;
+        const float *src = dsp + (size_t)v * W;
+        const float F = rowF[r];
+        uint8_t *dst = road + (size_t)r * L.IW;
+        for (int u = lane; u < L.IW; u += 32) {
+            uint8_t m = 0;
+            if (rowok && u >= 1 && u <= W - 2) {
+                const float l = __ldg(src + u);
+                m = l > 0.0f && l < __int_as_float(0x7f800000) && fabsf(__fsub_rn(l, F)) <= kp.varpi;
+            }
+            dst[u] = m;
         }
-        road[i] = m;
     }
     __syncthreads();
     // per-class weight tables: T_c[k] = (ws_c * wr[k] + 2^14) >> 15, k = q - c + 256
-    for (int i = tid; i < kp.n_cls * kWrEntries; i += kThreads) {
-        const int c = i / kWrEntries, k = i - c * kWrEntries;
-        tabs[i] = (uint16_t)(((uint32_t)kp.cls_ws[c] * (uint32_t)wr[k] + 16384u) >> 15);
+    for (int c = 0; c < kp.n_cls; ++c) {
+        const uint32_t wsc = kp.cls_ws[c];
+        for (int k = tid; k < kWrEntries; k += kThreads)
+            tabs[c * kWrEntries + k] = (uint16_t)((wsc * (uint32_t)wr[k] + 16384u) >> 15);
     }
     // groups of 4 pixels of the bilateral rows (r0-1 .. r0+nr) holding a pixel the Sobel stencil reads
-    for (int g0 = 0; g0 < BR * L.NG; g0 += kThreads) {
-        const int g = g0 + tid;
-        bool need = false;
-        if (g < BR * L.NG) {
-            const int br = g / L.NG, u0 = 4 * (g - br * L.NG);
+    for (int br = warp; br < BR; br += NW) {
+        for (int j0 = 0; j0 < L.NG; j0 += 32) {
+            const int j = j0 + lane;
+            bool need = false;
+            if (j < L.NG) {
+                const int u0 = 4 * j;
 #pragma unroll
-            for (int dr = -1; dr <= 1; ++dr) {
-                const int rr = br - 1 + dr;
-                if (rr < 0 || rr >= nr)
-                    continue;
-                const uint8_t *rm = road + (size_t)rr * W;
-                for (int u = max(u0 - 1, 0); u <= min(u0 + 4, W - 1); ++u)
-                    need |= rm[u] != 0;
+                for (int dr = -1; dr <= 1; ++dr) {
+                    const int rr = br - 1 + dr;
+                    if (rr < 0 || rr >= nr)
+                        continue;
+                    const uint32_t *rm = reinterpret_cast<const uint32_t *>(road + (size_t)rr * L.IW) + j;
+                    const uint32_t left = j > 0 ? rm[-1] >> 24 : 0u;
+                    const uint32_t right = j + 1 < L.NG ? rm[1] & 0xffu : 0u;
+                    need |= (left | rm[0] | right) != 0u;
+                }
             }
+            const unsigned m = __ballot_sync(0xffffffffu, need);
+            int base = 0;
+            if (lane == 0 && m)
+                base = atomicAdd(&cnt[2 * R], __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (need)
+                glist[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(br * L.NG + j);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, need);
-        int base = 0;
-        if (lane == 0 && m)
-            base = atomicAdd(&cnt[2 * R], __popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (need)
-            glist[base + __popc(m & ((1u << lane) - 1u))] = g;
     }
     __syncthreads();
     const int ng = cnt[2 * R];
@@ -230,34 +246,37 @@ __global__ void __launch_bounds__(kThreads) k_grad(const KParams kp, const Work 
     const int thr2 = kp.edge_thresh2;
     int16_t *edges = w.edges + (size_t)f * H * W * 4;
     int16_t *vbins = w.vbins + (size_t)f * H * W;
-    for (int i = tid; i < nr * W; i += kThreads) {
-        if (!road[i])
-            continue;
-        const int r = i / W, u = i - r * W;
+    for (int r = warp; r < nr; r += NW) {
         const int v = r0 + r;
+        const uint8_t *rm = road + (size_t)r * L.IW;
         const uint8_t *a = ibf + (size_t)r * L.IW;      // row v-1
         const uint8_t *b = a + L.IW;                      // row v
         const uint8_t *cc = b + L.IW;                     // row v+1
-        const int gx = ((int)a[u + 1] - (int)a[u - 1]) + 2 * ((int)b[u + 1] - (int)b[u - 1]) + ((int)cc[u + 1] - (int)cc[u - 1]);
-        const int gy = ((int)cc[u - 1] - (int)a[u - 1]) + 2 * ((int)cc[u] - (int)a[u]) + ((int)cc[u + 1] - (int)a[u + 1]);
-        if (gx * gx + gy * gy <= thr2)
-            continue;
-        int bin = -1;
-        if (gx != 0) {
-            const float av = __fsub_rn((float)v, rowVy[r]);
-            const float bv = __fmul_rn(av, (float)gy);
-            const float qv = __fdiv_rn(bv, (float)gx);
-            const float vs = __fadd_rn((float)u, qv);
-            const float col = floorf(__fadd_rn(vs, 0.5f));
-            if (col >= 0.0f && col < (float)W)
-                bin = (int)col;
-        }
-        const int pe = atomicAdd(&cnt[r], 1);
-        const short4 e = make_short4((short)u, (short)bin, (short)gx, (short)gy);
-        *reinterpret_cast<short4 *>(edges + ((size_t)v * W + pe) * 4) = e;
-        if (bin >= 0) {
-            const int pv = atomicAdd(&cnt[R + r], 1);
-            vbins[(size_t)v * W + pv] = (int16_t)bin;
+        const float vy = rowVy[r];
+        for (int u = lane; u < W; u += 32) {
+            if (!rm[u])
+                continue;
+            const int gx = ((int)a[u + 1] - (int)a[u - 1]) + 2 * ((int)b[u + 1] - (int)b[u - 1]) + ((int)cc[u + 1] - (int)cc[u - 1]);
+            const int gy = ((int)cc[u - 1] - (int)a[u - 1]) + 2 * ((int)cc[u] - (int)a[u]) + ((int)cc[u + 1] - (int)a[u + 1]);
+            if (gx * gx + gy * gy <= thr2)
+                continue;
+            int bin = -1;
+            if (gx != 0) {
+                const float av = __fsub_rn((float)v, vy);
+                const float bv = __fmul_rn(av, (float)gy);
+                const float qv = __fdiv_rn(bv, (float)gx);
+                const float vs = __fadd_rn((float)u, qv);
+                const float col = floorf(__fadd_rn(vs, 0.5f));
+                if (col >= 0.0f && col < (float)W)
+                    bin = (int)col;
+            }
+            const int pe = atomicAdd(&cnt[r], 1);
+            const short4 e = make_short4((short)u, (short)bin, (short)gx, (short)gy);
+            *reinterpret_cast<short4 *>(edges + ((size_t)v * W + pe) * 4) = e;
+            if (bin >= 0) {
+                const int pv = atomicAdd(&cnt[R + r], 1);
+                vbins[(size_t)v * W + pv] = (int16_t)bin;
+            }
         }
     }
     __syncthreads();
@@ -271,21 +290,34 @@ template <int RHO>
 size_t grad_smem(int W, int R, int n_cls)
 {
     const GradLayout L = grad_layout<RHO>(W, R);
-    size_t s = (size_t)kTabBytes * n_cls + sizeof(int32_t) * kWrEntries + sizeof(int32_t) * (2 * R + 4) +
-               2 * sizeof(float) * R;
+    size_t s = (size_t)kTabBytes * n_cls + sizeof(int32_t) * (2 * R + 4) + 2 * sizeof(float) * R;
     s = (s + 15) & ~(size_t)15;
-    s += sizeof(uint16_t) * (size_t)L.TR * L.TWP + (size_t)L.BR * L.IW + (size_t)R * W;
+    const size_t ibf = (size_t)L.BR * L.IW > sizeof(int32_t) * kWrEntries ? (size_t)L.BR * L.IW : sizeof(int32_t) * kWrEntries;
+    s += sizeof(uint16_t) * (size_t)L.TR * L.TWP + ibf + (size_t)R * L.IW;
     s = (s + 15) & ~(size_t)15;
-    s += sizeof(int32_t) * (size_t)L.BR * L.NG;
+    s += sizeof(uint16_t) * (size_t)L.BR * L.NG;
     return s + 16;
+}
+
+// Rows per CTA: the most that let two CTAs share an SM, else the most that fit one CTA.
+template <int RHO>
+int grad_rows(int W, int n_cls)
+{
+    int R = 16;
+    while (R > 6 && grad_smem<RHO>(W, R, n_cls) > 112 * 1024)
+        --R;
+    if (grad_smem<RHO>(W, R, n_cls) <= 112 * 1024)
+        return R;
+    R = 16;
+    while (R > 1 && grad_smem<RHO>(W, R, n_cls) > 200 * 1024)
+        --R;
+    return R;
 }
 
 template <int RHO>
 cudaError_t launch_grad_t(const KParams &kp, const Work &w, const float *disp, const uint8_t *img, cudaStream_t s)
 {
-    int R = 16;
-    while (R > 1 && grad_smem<RHO>(kp.W, R, kp.n_cls) > 200 * 1024)
-        --R;
+    const int R = grad_rows<RHO>(kp.W, kp.n_cls);
     const size_t smem = grad_smem<RHO>(kp.W, R, kp.n_cls);
     dim3 grid((kp.H + R - 1) / R, kp.n_frames);
     k_grad<RHO><<<grid, kThreads, smem, s>>>(kp, w, disp, img, R);
