@@ -265,14 +265,28 @@ int32_t or_lsf(const int32_t *x, const int32_t *y, const uint8_t *use, int32_t n
     return solve_normal(Sx, Sy, m, e, coef);
 }
 
-/* Model value in float32 (Horner, one rounding per operation) and the inlier test of Sec. 2.2 and     */
-/* Sec. 2.3.3: r = (y - model)^2 < tr.                                                                */
-static int32_t is_inlier(const float *cf, int32_t m, int32_t x, int32_t y, int32_t centre, int32_t e, float tr)
+/* The polynomial through m sample points (tau_i, y_i), tau_i = (x_i - centre) / 2^e, in Newton form:     */
+/* divided differences c_i computed in float32 in place (c_i = y_i; for k = 1..m-1, i = m-1 down to k:   */
+/* c_i = (c_i - c_{i-1}) / (tau_i - tau_{i-k})).  For m points the least squares fit of Eq. 13 / Eq. 19   */
+/* is this interpolant; the Newton form computes it without squaring the conditioning of the system.      */
+static void newton_fit(const float *tau, const float *y, int32_t m, float *c)
+{
+    for (int32_t i = 0; i < m; i++)
+        c[i] = y[i];
+    for (int32_t k = 1; k < m; k++)
+        for (int32_t i = m - 1; i >= k; i--)
+            c[i] = (c[i] - c[i - 1]) / (tau[i] - tau[i - k]);
+}
+
+/* Model value in float32 (nested Newton form, one rounding per operation) and the inlier test of        */
+/* Sec. 2.2 and Sec. 2.3.3: r = (y - model)^2 < tr.                                                       */
+static int32_t is_inlier(const float *c, const float *nodes, int32_t m, int32_t x, int32_t y, int32_t centre,
+                         int32_t e, float tr)
 {
     float tau = (float)(x - centre) * ldexpf(1.0f, -e);
-    float p = cf[m - 1];
+    float p = c[m - 1];
     for (int32_t k = m - 2; k >= 0; k--)
-        p = p * tau + cf[k];
+        p = p * (tau - nodes[k]) + c[k];
     float r = (float)y - p;
     return r * r < tr;
 }
@@ -283,8 +297,9 @@ static int32_t is_inlier(const float *cf, int32_t m, int32_t x, int32_t y, int32
 /* working set S (member[j] = 1), listed in increasing j.  Draw j = 0, 1, ... takes word (j & 3) of    */
 /* Philox4x32-10 at counter (stage << 24 | round, hyp, j >> 2, 0), key = seed; the word x picks list   */
 /* position floor(x * |S| / 2^32).  A draw repeating a chosen point or a chosen x is skipped; after   */
-/* 8m draws without m distinct points the hypothesis is void.  The m points are fitted by Eq. 13 /     */
-/* Eq. 19 (exact through m points) and scored by the inliers among S.                                 */
+/* 8m draws without m distinct points the hypothesis is void.  The m points, in draw order, are fitted  */
+/* exactly (newton_fit: the least squares fit of Eq. 13 / Eq. 19 through m points) and scored by the    */
+/* inliers among S.                                                                                    */
 /* Returns the inlier count, or -1 for a void hypothesis.  chosen[m] and inliers[n] may be NULL.      */
 /* ------------------------------------------------------------------------------------------------ */
 int32_t or_hypothesis(const int32_t *x, const int32_t *y, const uint8_t *member, int32_t n, int32_t m,
@@ -318,20 +333,15 @@ int32_t or_hypothesis(const int32_t *x, const int32_t *y, const uint8_t *member,
             chosen[q] = q < got ? pick[q] : -1;
     if (got < m)
         return -1;
-    int32_t sx[5], sy[5];
+    float nodes[5], sy[5], c[5];
     for (int32_t q = 0; q < m; q++) {
-        sx[q] = x[pick[q]];
-        sy[q] = y[pick[q]];
+        nodes[q] = (float)(x[pick[q]] - centre) * ldexpf(1.0f, -e);
+        sy[q] = (float)y[pick[q]];
     }
-    double coef[5];
-    if (or_lsf(sx, sy, NULL, m, m, centre, e, coef) != 0)
-        return -1;
-    float cf[5];
-    for (int32_t k = 0; k < m; k++)
-        cf[k] = (float)coef[k];
+    newton_fit(nodes, sy, m, c);
     int32_t cnt = 0;
     for (int32_t j = 0; j < n; j++) {
-        int32_t in = member[j] && is_inlier(cf, m, x[j], y[j], centre, e, tr);
+        int32_t in = member[j] && is_inlier(c, nodes, m, x[j], y[j], centre, e, tr);
         if (inliers)
             inliers[j] = (uint8_t)in;
         cnt += in;

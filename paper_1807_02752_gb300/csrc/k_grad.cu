@@ -28,7 +28,7 @@ namespace ld {
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr int kTabBytes = kWrEntries * 2;  // one uint16 table per distance class
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -109,7 +109,7 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
 }
 
 template <int RHO>
-__global__ void __launch_bounds__(kThreads, 2) k_grad(const KParams kp, const Work w, const float *__restrict__ disp,
+__global__ void __launch_bounds__(kThreads, 1) k_grad(const KParams kp, const Work w, const float *__restrict__ disp,
                                                       const uint8_t *__restrict__ img, int R)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -304,11 +304,6 @@ template <int RHO>
 int grad_rows(int W, int n_cls)
 {
     int R = 16;
-    while (R > 6 && grad_smem<RHO>(W, R, n_cls) > 112 * 1024)
-        --R;
-    if (grad_smem<RHO>(W, R, n_cls) <= 112 * 1024)
-        return R;
-    R = 16;
     while (R > 1 && grad_smem<RHO>(W, R, n_cls) > 200 * 1024)
         --R;
     return R;

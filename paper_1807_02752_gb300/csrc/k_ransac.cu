@@ -11,16 +11,18 @@
 //     index; draw j takes word j & 3 of Philox4x32-10 at counter (stage << 24 | round, hypothesis, j >> 2, 0)
 //     with key = seed, and picks list position floor(word * |S| / 2^32); a draw repeating a chosen point or a
 //     chosen row is skipped, and after 8 M draws without M points the hypothesis is void;
-//   - the sample is fitted by the normal equations of Eq. 20 (exact integer sums over t = v - centre,
-//     rounded once to double, scaled by exact powers of two - the kappa of Eq. 20 - and solved by Gaussian
-//     elimination with partial pivoting; a pivot below 2^-40 is singular);
-//   - inliers are points of S with (y - g(v))^2 < tr, g evaluated in float32 from the float32 coefficients;
+//   - the sample is fitted exactly (for M points the least squares fit is the interpolant): Newton divided
+//     differences in float32 over tau = (v - centre) / 2^e, in draw order;
+//   - inliers are points of S with (y - g(v))^2 < tr, g evaluated in float32 in nested Newton form;
 //   - the hypothesis with most inliers (lowest index on ties) wins the round and its outliers leave S;
 //   - the loop ends after the first round with eps_den n_I >= eps_num |S|, when no hypothesis is valid, or
-//     at the round cap; the final fit is least squares over S.
+//     at the round cap; the final fit is least squares over S, by the normal equations of Eq. 20 (exact
+//     integer sums over t = v - centre, rounded once to double, scaled by exact powers of two - the kappa of
+//     Eq. 20 - and solved in float64 by Gaussian elimination with partial pivoting; a pivot below 2^-40 is
+//     singular).
 //
-// GB300 mapping: the FP64 pipe is narrow, so every THREAD fits one hypothesis (a warp solves 32 systems in
-// one pass of the pipe), then every WARP counts the inliers of one hypothesis at a time.
+// GB300 mapping: every THREAD fits one hypothesis in float32 (GB300's FP64 pipe is narrow, so float64 is
+// kept to the one final solve per round loop), then every WARP counts the inliers of one hypothesis at a time.
 #include "ld_internal.cuh"
 
 namespace ld {
@@ -154,10 +156,11 @@ __device__ __forceinline__ T *carve(unsigned char *&p, size_t count)
     return r;
 }
 
-// One hypothesis: the minimal sample of Philox draws and its exact fit (float32 coefficients in cf).
+// One hypothesis: the minimal sample of Philox draws and the polynomial through it in Newton form
+// (nodes = the sample's tau in draw order, c = float32 divided differences, computed in place).
 template <int M>
 __device__ bool hypothesis(const KParams &kp, const int16_t *xs, const int16_t *ys, const int16_t *list, int ns,
-                           int stage, int round, int h, float *cf)
+                           int stage, int round, int h, float *c, float *nodes)
 {
     int pick[M];
     int got = 0;
@@ -176,23 +179,32 @@ __device__ bool hypothesis(const KParams &kp, const int16_t *xs, const int16_t *
     }
     if (got < M)
         return false;
-    __int128 Sx[2 * M - 1], Sy[M];
+    const float sc = pow2f(-kp.e);
 #pragma unroll
-    for (int k = 0; k < 2 * M - 1; ++k)
-        Sx[k] = 0;
+    for (int q = 0; q < M; ++q) {
+        nodes[q] = __fmul_rn((float)(xs[pick[q]] - kp.centre), sc);
+        c[q] = (float)ys[pick[q]];
+    }
 #pragma unroll
-    for (int k = 0; k < M; ++k)
-        Sy[k] = 0;
+    for (int k = 1; k < M; ++k)
 #pragma unroll
-    for (int q = 0; q < M; ++q)
-        add_point<M>(Sx, Sy, xs[pick[q]], ys[pick[q]], kp.centre);
-    double cd[M];
-    if (solve_normal<M>(Sx, Sy, kp.e, cd) != 0)
-        return false;
-#pragma unroll
-    for (int k = 0; k < M; ++k)
-        cf[k] = __double2float_rn(cd[k]);
+        for (int i = M - 1; i >= k; --i)
+            c[i] = __fdiv_rn(__fsub_rn(c[i], c[i - 1]), __fsub_rn(nodes[i], nodes[i - k]));
     return true;
+}
+
+// Inlier test of a Newton-form hypothesis: (y - p(tau))^2 < tr, nested evaluation in float32.
+template <int M>
+__device__ __forceinline__ bool newton_inlier(const float *c, const float *nodes, int x, int y, int centre, float sc,
+                                              float tr)
+{
+    const float tau = __fmul_rn((float)(x - centre), sc);
+    float p = c[M - 1];
+#pragma unroll
+    for (int k = M - 2; k >= 0; --k)
+        p = __fadd_rn(__fmul_rn(p, __fsub_rn(tau, nodes[k])), c[k]);
+    const float r = __fsub_rn((float)y, p);
+    return __fmul_rn(r, r) < tr;
 }
 
 template <int M>
@@ -219,7 +231,7 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(const KParams kp, const Wor
     int *chunk = carve<int>(p, (P + 31) / 32 + 2);
     int *hyp_ok = carve<int>(p, kMaxHyps);
     int *hyp_cnt = carve<int>(p, kMaxHyps);
-    float *hyp_cf = carve<float>(p, kMaxHyps * M);
+    float *hyp_cf = carve<float>(p, kMaxHyps * 2 * M);  // per hypothesis: M divided differences, M nodes
     __int128 *red = carve<__int128>(p, kNW * (3 * M - 1));
     int *redc = carve<int>(p, kNW);
 
@@ -246,25 +258,27 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(const KParams kp, const Wor
             break;
         }
         for (int h = tid; h < kp.hyps; h += kFitThreads) {
-            float cf[M];
-            const bool ok = hypothesis<M>(kp, xs, ys, list, ns, stage, round, h, cf);
+            float c[M], nodes[M];
+            const bool ok = hypothesis<M>(kp, xs, ys, list, ns, stage, round, h, c, nodes);
             hyp_ok[h] = ok;
 #pragma unroll
-            for (int k = 0; k < M; ++k)
-                hyp_cf[h * M + k] = ok ? cf[k] : 0.0f;
+            for (int k = 0; k < M; ++k) {
+                hyp_cf[h * 2 * M + k] = ok ? c[k] : 0.0f;
+                hyp_cf[h * 2 * M + M + k] = ok ? nodes[k] : 0.0f;
+            }
         }
         __syncthreads();
         for (int h = warp; h < kp.hyps; h += kNW) {
             int cnt = -1;
             if (hyp_ok[h]) {
-                float cf[M];
+                float cf[2 * M];
 #pragma unroll
-                for (int k = 0; k < M; ++k)
-                    cf[k] = hyp_cf[h * M + k];
+                for (int k = 0; k < 2 * M; ++k)
+                    cf[k] = hyp_cf[h * 2 * M + k];
                 int c = 0;
                 for (int q = lane; q < ns; q += 32) {
                     const int j = list[q];
-                    c += inlier_test<M>(cf, xs[j], ys[j], centre, sc, tr);
+                    c += newton_inlier<M>(cf, cf + M, xs[j], ys[j], centre, sc, tr);
                 }
                 cnt = __reduce_add_sync(0xffffffffu, c);
             }
@@ -299,12 +313,12 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(const KParams kp, const Wor
             fl |= 2;
             break;
         }
-        float cf[M];
+        float cf[2 * M];
 #pragma unroll
-        for (int k = 0; k < M; ++k)
-            cf[k] = hyp_cf[bh * M + k];
+        for (int k = 0; k < 2 * M; ++k)
+            cf[k] = hyp_cf[bh * 2 * M + k];
         for (int j = tid; j < n; j += kFitThreads)
-            if (member[j] && !inlier_test<M>(cf, xs[j], ys[j], centre, sc, tr))
+            if (member[j] && !newton_inlier<M>(cf, cf + M, xs[j], ys[j], centre, sc, tr))
                 member[j] = 0;
         __syncthreads();
         if ((long long)kp.eps_den * bc >= (long long)kp.eps_num * ns)
@@ -473,7 +487,7 @@ size_t fit_smem(int P)
     add(4 * (size_t)((P + 31) / 32 + 2));
     add(4 * kMaxHyps);
     add(4 * kMaxHyps);
-    add(4 * kMaxHyps * M);
+    add(4 * kMaxHyps * 2 * M);
     add(16 * kNW * (3 * M - 1));
     add(4 * kNW);
     return s + 16;

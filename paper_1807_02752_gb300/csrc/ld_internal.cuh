@@ -116,19 +116,6 @@ inline cudaError_t allow_max_smem(K kernel, int smem_optin)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)a.sharedSizeBytes);
 }
 
-// Polynomial value in float32 (Horner, two roundings per step) and the inlier test (y - g)^2 < tr.
-template <int M>
-__device__ __forceinline__ bool inlier_test(const float *cf, int x, int y, int centre, float sc, float tr)
-{
-    const float tau = __fmul_rn((float)(x - centre), sc);
-    float p = cf[M - 1];
-#pragma unroll
-    for (int k = M - 2; k >= 0; --k)
-        p = __fadd_rn(__fmul_rn(p, tau), cf[k]);
-    const float r = __fsub_rn((float)y, p);
-    return __fmul_rn(r, r) < tr;
-}
-
 // f64 Horner without contraction.
 template <int M>
 __device__ __forceinline__ double poly_f64(const double *c, double tau)
