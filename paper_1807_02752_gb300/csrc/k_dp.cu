@@ -113,6 +113,25 @@ __device__ int block_compact(const uint8_t *flag, int n, int16_t *list, int *chu
 
 __device__ __forceinline__ int nib16(const uint16_t *row, int i) { return (row[i >> 2] >> (4 * (i & 3))) & 15; }
 
+// Shared-memory accesses through 32-bit shared addresses (keeps the hot DP loop on the shared-memory path
+// whatever pointers the compiler can prove).
+__device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int lds(uint32_t a)
+{
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts(uint32_t a, int v) { asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v)); }
+__device__ __forceinline__ void sts16(uint32_t a, uint32_t v) { asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v)); }
+__device__ __forceinline__ int lds16s(uint32_t a)
+{
+    short v;
+    asm volatile("ld.shared.s16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void atoms_add(uint32_t a, int v) { asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v)); }
+
 // ---------------------------------------------------------------------------------------------------
 // k_road_dp
 // ---------------------------------------------------------------------------------------------------
@@ -133,8 +152,11 @@ __global__ void __launch_bounds__(kRoadThreads) k_road_dp(const KParams kp, cons
     int16_t *pid = carve<int16_t>(p, D);
     uint16_t *bt = carve<uint16_t>(p, (size_t)D * Hq);
 
+    // E rows hold keys 16 E: a candidate's key 16 (E + lambda tau) + tau orders candidates by energy, then
+    // by the smaller tau, so the tie-broken argmin is a plain integer minimum (|16 E| < 2^30 always holds
+    // here: energies are bounded by (w + lambda_y tau_y) D).
     for (int v = tid; v < H + kPadY; v += kRoadThreads) {
-        E0[v] = v < H ? -my[(size_t)(D - 1) * H + v] : kSent;
+        E0[v] = v < H ? -16 * my[(size_t)(D - 1) * H + v] : kSent;
         E1[v] = kSent;
     }
     // data terms of the next two steps are loaded a step ahead of their use
@@ -149,7 +171,11 @@ __global__ void __launch_bounds__(kRoadThreads) k_road_dp(const KParams kp, cons
         }
     __syncthreads();
     int *Ep = E0, *Ec = E1;
-    const int tau = kp.tau_y, lam = kp.lambda_y;
+    const int tau = kp.tau_y;
+    int ck[TMAX + 1];  // key offset of step t; steps beyond tau_y never win
+#pragma unroll
+    for (int t = 0; t <= TMAX; ++t)
+        ck[t] = t <= tau ? 16 * kp.lambda_y * t + t : kSent;
     for (int d = D - 2; d >= 1; --d) {
         int nn[kRoadQ][4];
 #pragma unroll
@@ -171,18 +197,18 @@ __global__ void __launch_bounds__(kRoadThreads) k_road_dp(const KParams kp, cons
                 uint32_t code = 0;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    int best = e[c], arg = 0;
+                    int kk[TMAX + 1];
 #pragma unroll
-                    for (int t = 1; t <= TMAX; ++t) {
-                        const int cand = e[c + t] + lam * t;
-                        if (t <= tau && cand < best) {
-                            best = cand;
-                            arg = t;
-                        }
-                    }
+                    for (int t = 0; t <= TMAX; ++t)
+                        kk[t] = e[c + t] + ck[t];
+#pragma unroll
+                    for (int st = 1; st <= TMAX; st *= 2)
+#pragma unroll
+                        for (int j = 0; j + st <= TMAX; j += 2 * st)
+                            kk[j] = min(kk[j], kk[j + st]);
                     if (v0 + c < H)
-                        Ec[v0 + c] = -cur[q][c] + best;
-                    code |= (uint32_t)arg << (4 * c);
+                        Ec[v0 + c] = -16 * cur[q][c] + (kk[0] & ~15);
+                    code |= (uint32_t)(kk[0] & 15) << (4 * c);
                 }
                 bt[(size_t)d * Hq + i] = (uint16_t)code;
             }
@@ -235,64 +261,298 @@ __global__ void __launch_bounds__(kRoadThreads) k_road_dp(const KParams kp, cons
 // ---------------------------------------------------------------------------------------------------
 // k_vpx_dp
 // ---------------------------------------------------------------------------------------------------
+__device__ __forceinline__ int4 lds4(uint32_t a)
+{
+    int4 v;
+    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts4(uint32_t a, int4 v)
+{
+    asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w));
+}
+__device__ __forceinline__ void atoms_or(uint32_t a, uint32_t v) { asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(a), "r"(v)); }
+
+// Shared-memory layout of k_vpx_dp.
 struct VpxMem {
-    int *E0, *E1, *band;   // E rows are padded by kPadX sentinels on both sides
-    int *voff;             // [H + 1] offsets of the staged vote rows
+    int *E0, *E1;          // E rows, column 0 at index 0, padded by kPadX sentinels on both sides
+    int *D0, *D1;          // band deltas of the next row (double-buffered), [4 Wq]
+    int *voff;             // [H + 1] offsets of the staged vote rows (prefix of the per-row counts)
     int16_t *vb;           // [vote_cap]
     int16_t *path;         // [H]
     uint8_t *sup;          // [H]
     int *sh;
-    uint16_t *bt;          // [seg_rows][Wq]
+    int16_t *pid;          // [H]
+    unsigned char *dyn;    // backtrack rows [seg_rows][Wq] (uint16), later the column bitmaps of the votes
 };
 
-__device__ __forceinline__ void band_row(const KParams &kp, const Work &w, const VpxMem &S, int f, int r, int sign,
-                                         bool staged)
+// Vote columns of row r (staged in shared memory, else the frame's list in global memory).
+struct VoteRow {
+    const int16_t *p;
+    int n;
+};
+__device__ __forceinline__ VoteRow vote_row(const KParams &kp, const Work &w, const VpxMem &S, int f, int r, bool staged)
 {
-    // vote rows [v_top, H-1] have their counts as offset differences in shared memory
-    const int cnt = S.voff[r + 1] - S.voff[r];
-    const int16_t *src = staged ? S.vb + S.voff[r] : w.vbins + ((size_t)f * kp.H + r) * kp.W;
-    for (int q = threadIdx.x; q < cnt; q += blockDim.x)
-        atomicAdd(&S.band[src[q]], sign);
+    VoteRow vr;
+    vr.n = S.voff[r + 1] - S.voff[r];
+    vr.p = staged ? S.vb + S.voff[r] : w.vbins + ((size_t)f * kp.H + r) * kp.W;
+    return vr;
 }
 
-// One Eq. 18 step for the quads of cells owned by this thread; Ep, Ec point at column 0 of padded rows.
-template <int TAU>
-__device__ __forceinline__ void dp_row(const KParams &kp, const int *band, const int *Ep, int *Ec, uint16_t *btrow)
+// Scatter the band change between row v+1 and row v (votes of row v - chi enter, of row v + chi + 1 leave)
+// into the delta array `delta` (shared address).
+__device__ __forceinline__ void scatter_delta(const KParams &kp, const Work &w, const VpxMem &S, int f, int v, int vtop,
+                                              bool staged, uint32_t delta)
 {
-    const int W = kp.W, Wq = (W + 3) >> 2, lam = kp.lambda_x, rho = kp.vote_rho;
-    for (int i = threadIdx.x; i < Wq; i += blockDim.x) {
-        const int u0 = 4 * i;
-        int e[2 * TAU + 4];
-#pragma unroll
-        for (int j = 0; j < 2 * TAU + 4; ++j)
-            e[j] = Ep[u0 - TAU + j];
-        uint32_t code = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int best = e[c + TAU], arg = 0;
-#pragma unroll
-            for (int k = 1; k <= 2 * TAU; ++k) {
-                const int t = (k & 1) ? -((k + 1) >> 1) : (k >> 1);
-                const int cand = e[c + TAU + t] + lam * (t < 0 ? -t : t);
-                if (cand < best) {
-                    best = cand;
-                    arg = t;
-                }
-            }
-            const int u = u0 + c;
-            if (u < W) {
-                Ec[u] = -rho * band[u] + best;
-                code |= (uint32_t)(arg & 15) << (4 * c);
-            }
-        }
-        btrow[i] = (uint16_t)code;
+    const int vmax = kp.H - 1, chi = kp.chi;
+    if (v - chi >= vtop) {
+        const VoteRow vr = vote_row(kp, w, S, f, v - chi, staged);
+        for (int q = threadIdx.x; q < vr.n; q += blockDim.x)
+            atoms_add(delta + 4u * (uint32_t)vr.p[q], 1);
+    }
+    if (v + chi + 1 <= vmax) {
+        const VoteRow vr = vote_row(kp, w, S, f, v + chi + 1, staged);
+        for (int q = threadIdx.x; q < vr.n; q += blockDim.x)
+            atoms_add(delta + 4u * (uint32_t)vr.p[q], -1);
     }
 }
 
-__device__ __forceinline__ int bt_get(const uint16_t *bt, int Wq, int slot, int u)
+// One Eq. 18 row for the four cells u0 .. u0+3 of this thread.  ep, ec: shared addresses of column 0 of
+// E_{v+1} and E_v (16-byte aligned at column u0 - 8); band: this thread's band counts of row v.
+// PACKED: E rows hold 16 E and the candidate key 16 (E + lambda |tau|) + k (k = rank in the tie order
+// tau = 0, -1, +1, -2, ...) makes the tie-broken argmin an integer minimum; otherwise compare-select in tie
+// order.  Writes the four E_v values (sentinels past the last column) and the backtrack word.
+template <int TAU, bool PACKED>
+__device__ __forceinline__ void dp_quad(const KParams &kp, int u0, const int *band, uint32_t ep, uint32_t ec,
+                                        uint32_t btword)
+{
+    constexpr int NK = 2 * TAU + 1;
+    const int W = kp.W;
+    int e[20];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int4 v4 = lds4(ep + 4u * (uint32_t)(u0 - 8 + 4 * j));
+        e[4 * j] = v4.x;
+        e[4 * j + 1] = v4.y;
+        e[4 * j + 2] = v4.z;
+        e[4 * j + 3] = v4.w;
+    }
+    int out[4];
+    uint32_t code = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int best, arg;
+        if (PACKED) {
+            int kk[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const int t = (k & 1) ? -((k + 1) >> 1) : (k >> 1);
+                const int a = t < 0 ? -t : t;
+                kk[k] = e[8 + c + t] + 16 * kp.lambda_x * a + k;
+            }
+#pragma unroll
+            for (int st = 1; st < NK; st *= 2)
+#pragma unroll
+                for (int j = 0; j + st < NK; j += 2 * st)
+                    kk[j] = min(kk[j], kk[j + st]);
+            best = kk[0] & ~15;
+            arg = kk[0] & 15;
+        } else {
+            best = e[8 + c];
+            arg = 0;
+#pragma unroll
+            for (int k = 1; k < NK; ++k) {
+                const int t = (k & 1) ? -((k + 1) >> 1) : (k >> 1);
+                const int cand = e[8 + c + t] + kp.lambda_x * (t < 0 ? -t : t);
+                if (cand < best) {
+                    best = cand;
+                    arg = t & 15;
+                }
+            }
+        }
+        const bool in = u0 + c < W;
+        out[c] = in ? (PACKED ? 16 : 1) * -kp.vote_rho * band[c] + best : kSent;
+        code |= (uint32_t)(in ? arg : 0) << (4 * c);
+    }
+    sts4(ec + 4u * (uint32_t)u0, make_int4(out[0], out[1], out[2], out[3]));
+    sts16(btword, code);
+}
+
+// Rows hi down to lo of the DP.  On entry Ep holds E_{hi+1}, band the counts of row hi+1 for this thread's
+// cells, and delta buffer (hi & 1) the change from row hi+1 to row hi.  Each row: scatter the change for the
+// next row into the other buffer (while no thread reads it), fold this row's change into the register
+// counts, update the row, one barrier.  Checkpoints (forward pass only) save E_{v+1} and the counts of row
+// v+1 at the first row of every segment above the top one.
+template <int TAU, bool PACKED>
+__device__ void dp_rows(const KParams &kp, const Work &w, const VpxMem &S, int f, int hi, int lo, int vtop, bool staged,
+                        int *band, int *&Ep, int *&Ec, int slot_lo, bool checkpoint, int32_t *ck)
+{
+    const int W = kp.W, Wq = (W + 3) >> 2, SR = kp.seg_rows;
+    const int i = threadIdx.x, u0 = 4 * i;
+    const bool own = i < Wq;
+    const uint32_t d0 = sa(S.D0), d1 = sa(S.D1), bt = sa(S.dyn);
+    for (int v = hi; v >= lo; --v) {
+        if (checkpoint) {
+            const int seg = (v - vtop) / SR;
+            if (seg > 0 && v == min(vtop + (seg + 1) * SR - 1, kp.H - 2) && own) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (u0 + c < W) {
+                        ck[(size_t)(2 * seg) * W + u0 + c] = Ep[u0 + c];
+                        ck[(size_t)(2 * seg + 1) * W + u0 + c] = band[c];
+                    }
+            }
+        }
+        if (v - 1 >= lo)
+            scatter_delta(kp, w, S, f, v - 1, vtop, staged, ((v - 1) & 1) ? d1 : d0);
+        if (own) {
+            const uint32_t da = ((v & 1) ? d1 : d0) + 16u * (uint32_t)i;
+            const int4 dl = lds4(da);
+            sts4(da, make_int4(0, 0, 0, 0));
+            band[0] += dl.x;
+            band[1] += dl.y;
+            band[2] += dl.z;
+            band[3] += dl.w;
+            const int slot = checkpoint ? (v - vtop) % SR : v - slot_lo;
+            dp_quad<TAU, PACKED>(kp, u0, band, sa(Ep), sa(Ec), bt + 2u * ((uint32_t)slot * Wq + i));
+        }
+        __syncthreads();
+        int *tmp = Ep;
+        Ep = Ec;
+        Ec = tmp;
+    }
+}
+
+// Backtrack step of row `slot` at column u: tau from a 4-bit two's complement entry, or from the tie rank
+// of the packed form.
+__device__ __forceinline__ int bt_get(const uint16_t *bt, int Wq, int slot, int u, bool packed)
 {
     const int nib = nib16(bt + (size_t)slot * Wq, u);
-    return (nib ^ 8) - 8;  // 4-bit two's complement
+    if (packed)
+        return (nib & 1) ? -((nib + 1) >> 1) : (nib >> 1);
+    return (nib ^ 8) - 8;
+}
+
+// Exclusive prefix sum of a[0..n) in place, a[n] = total.  chunk: >= n/32 + 2 ints.
+__device__ void block_scan(int *a, int n, int *chunk)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nch = (n + 31) >> 5;
+    for (int c = warp; c < nch; c += nw) {
+        const int j = (c << 5) + lane;
+        const int x = j < n ? a[j] : 0;
+        int inc = x;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d)
+                inc += o;
+        }
+        if (j < n)
+            a[j] = inc - x;
+        if (lane == 31)
+            chunk[c] = inc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int c = 0; c < nch; ++c) {
+            const int t = chunk[c];
+            chunk[c] = s;
+            s += t;
+        }
+        a[n] = s;
+    }
+    __syncthreads();
+    for (int c = warp; c < nch; c += nw) {
+        const int j = (c << 5) + lane;
+        if (j < n)
+            a[j] += chunk[c];
+    }
+    __syncthreads();
+}
+
+template <int TAU, bool PACKED>
+__device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, int f, int vtop, bool staged)
+{
+    const int W = kp.W, H = kp.H, Wq = (W + 3) >> 2, vmax = H - 1, chi = kp.chi, SR = kp.seg_rows;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int i = tid, u0 = 4 * i;
+    const bool own = i < Wq;
+    // ---- counts of row vmax: rows [max(vtop, vmax - chi), vmax], gathered in D0 ----
+    for (int r = max(vtop, vmax - chi); r <= vmax; ++r) {
+        const VoteRow vr = vote_row(kp, w, S, f, r, staged);
+        for (int q = tid; q < vr.n; q += nt)
+            atoms_add(sa(S.D0) + 4u * (uint32_t)vr.p[q], 1);
+    }
+    __syncthreads();
+    int band[4] = {0, 0, 0, 0};
+    if (own) {
+        const int4 b4 = lds4(sa(S.D0) + 16u * i);
+        band[0] = b4.x;
+        band[1] = b4.y;
+        band[2] = b4.z;
+        band[3] = b4.w;
+        sts4(sa(S.D0) + 16u * i, make_int4(0, 0, 0, 0));
+        int e4[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            e4[c] = u0 + c < W ? (PACKED ? 16 : 1) * -kp.vote_rho * band[c] : kSent;
+        sts4(sa(S.E0) + 16u * i, make_int4(e4[0], e4[1], e4[2], e4[3]));
+    }
+    __syncthreads();
+    // ---- forward DP over rows vmax-1 .. vtop ----
+    const int nrows = vmax - vtop;
+    const int nseg = (nrows + SR - 1) / SR;
+    int32_t *ck = w.ckpt + (size_t)f * w.max_seg * 2 * W;
+    int *Ep = S.E0, *Ec = S.E1;
+    if (nrows > 0) {
+        scatter_delta(kp, w, S, f, vmax - 1, vtop, staged, ((vmax - 1) & 1) ? sa(S.D1) : sa(S.D0));
+        __syncthreads();
+        dp_rows<TAU, PACKED>(kp, w, S, f, vmax - 1, vtop, vtop, staged, band, Ep, Ec, vtop, true, ck);
+    }
+    // ---- path start: smallest u minimising E_{vtop} ----
+    int bv = 0x7fffffff, bi = 0x7fffffff;
+    for (int u = tid; u < W; u += nt)
+        if (Ep[u] < bv) {
+            bv = Ep[u];
+            bi = u;
+        }
+    const int ustar = block_argmin(bv, bi, S.sh + kMaxChunks);
+    const uint16_t *bt = reinterpret_cast<const uint16_t *>(S.dyn);
+    int upath = ustar;
+    if (tid == 0) {
+        S.path[vtop] = (int16_t)upath;
+        const int hi = min(vtop + SR - 1, vmax - 1);
+        for (int v = vtop; v <= hi && nseg > 0; ++v) {
+            upath += bt_get(bt, Wq, (v - vtop) % SR, upath, PACKED);
+            S.path[v + 1] = (int16_t)upath;
+        }
+    }
+    __syncthreads();
+    // ---- lower segments: restore the checkpoint, recompute the backtrack rows, follow them ----
+    for (int sg = 1; sg < nseg; ++sg) {
+        const int lo = vtop + sg * SR, hi = min(vtop + (sg + 1) * SR - 1, vmax - 1);
+        if (own)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (u0 + c < W) {
+                    S.E0[u0 + c] = ck[(size_t)(2 * sg) * W + u0 + c];
+                    band[c] = ck[(size_t)(2 * sg + 1) * W + u0 + c];
+                }
+        Ep = S.E0;
+        Ec = S.E1;
+        scatter_delta(kp, w, S, f, hi, vtop, staged, (hi & 1) ? sa(S.D1) : sa(S.D0));
+        __syncthreads();
+        dp_rows<TAU, PACKED>(kp, w, S, f, hi, lo, vtop, staged, band, Ep, Ec, lo, false, ck);
+        if (tid == 0) {
+            int u = S.path[lo];
+            for (int v = lo; v <= hi; ++v) {
+                u += bt_get(bt, Wq, v - lo, u, PACKED);
+                S.path[v + 1] = (int16_t)u;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 template <int TAU>
@@ -308,154 +568,102 @@ __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
 
     VpxMem S;
     unsigned char *p = smem;
-    S.E0 = carve<int>(p, W + 2 * kPadX) + kPadX;
-    S.E1 = carve<int>(p, W + 2 * kPadX) + kPadX;
-    S.band = carve<int>(p, W);
+    S.E0 = carve<int>(p, 4 * Wq + 2 * kPadX) + kPadX;
+    S.E1 = carve<int>(p, 4 * Wq + 2 * kPadX) + kPadX;
+    S.D0 = carve<int>(p, 4 * Wq);
+    S.D1 = carve<int>(p, 4 * Wq);
     S.voff = carve<int>(p, H + 1);
     S.vb = carve<int16_t>(p, kp.vote_cap);
     S.path = carve<int16_t>(p, H);
     S.sup = carve<uint8_t>(p, H);
     S.sh = carve<int>(p, kMaxChunks + 64);
-    int16_t *pid = carve<int16_t>(p, H);
-    S.bt = carve<uint16_t>(p, (size_t)kp.seg_rows * Wq);
+    S.pid = carve<int16_t>(p, H);
+    S.dyn = carve<unsigned char>(p, 0);
 
-    // ---- stage the vote rows [vtop, vmax] in shared memory when they fit ----
+    // ---- vote rows [vtop, vmax]: offsets by a block scan, staged in shared memory when they fit ----
     for (int v = tid; v < H; v += nt)
         S.voff[v] = v >= vtop ? w.vcount[(size_t)f * H + v] : 0;
-    for (int u = tid; u < W; u += nt)
-        S.band[u] = 0;
-    for (int u = tid - kPadX; u < W + kPadX; u += nt) {
+    for (int u = tid; u < 4 * Wq; u += nt) {
+        S.D0[u] = 0;
+        S.D1[u] = 0;
+    }
+    for (int u = tid - kPadX; u < 4 * Wq + kPadX; u += nt)
         if (u < 0 || u >= W) {
             S.E0[u] = kSent;
             S.E1[u] = kSent;
         }
-    }
     __syncthreads();
-    if (tid == 0) {
-        int s = 0;
-        for (int v = 0; v < H; ++v) {
-            const int c = S.voff[v];
-            S.voff[v] = s;
-            s += c;
-        }
-        S.voff[H] = s;
-    }
-    __syncthreads();
-    const bool staged = S.voff[H] <= kp.vote_cap;
+    block_scan(S.voff, H, S.sh);
+    const int votes = S.voff[H];
+    const bool staged = votes <= kp.vote_cap;
     if (staged) {
-        for (int v = vtop + warp; v <= vmax; v += nw) {
-            const int cnt = S.voff[v + 1] - S.voff[v];
-            const int16_t *src = w.vbins + ((size_t)f * H + v) * W;
-            for (int q = lane; q < cnt; q += 32)
-                S.vb[S.voff[v] + q] = src[q];
-        }
-    }
-    __syncthreads();
-
-    // ---- band of row vmax: rows [max(vtop, vmax - chi), vmax] ----
-    for (int r = max(vtop, vmax - chi); r <= vmax; ++r)
-        band_row(kp, w, S, f, r, +1, staged);
-    __syncthreads();
-    for (int u = tid; u < W; u += nt)
-        S.E0[u] = -kp.vote_rho * S.band[u];
-    __syncthreads();
-
-    // ---- forward DP over rows vmax-1 .. vtop; segment k = rows [vtop + k S, vtop + (k+1) S - 1] ----
-    const int SR = kp.seg_rows;
-    const int nrows = vmax - vtop;
-    const int nseg = (nrows + SR - 1) / SR;
-    int32_t *ck = w.ckpt + (size_t)f * w.max_seg * 2 * W;
-    int *Ep = S.E0, *Ec = S.E1;
-    int seg = nseg - 1, seg_lo = vtop + seg * SR;
-    for (int v = vmax - 1; v >= vtop; --v) {
-        if (v < seg_lo) {
-            --seg;
-            seg_lo -= SR;
-        }
-        if (seg > 0 && v == min(seg_lo + SR - 1, vmax - 1)) {
-            for (int u = tid; u < W; u += nt) {
-                ck[(size_t)(2 * seg) * W + u] = Ep[u];
-                ck[(size_t)(2 * seg + 1) * W + u] = S.band[u];
+        for (int r0 = vtop + 4 * warp; r0 <= vmax; r0 += 4 * nw) {
+            const int r = r0 + (lane >> 3);
+            if (r <= vmax) {
+                const int off = S.voff[r], cnt = S.voff[r + 1] - off;
+                const int16_t *src = w.vbins + ((size_t)f * H + r) * W;
+                for (int q = lane & 7; q < cnt; q += 8)
+                    S.vb[off + q] = src[q];
             }
-            __syncthreads();
         }
-        if (v - chi >= vtop)
-            band_row(kp, w, S, f, v - chi, +1, staged);
-        if (v + chi + 1 <= vmax)
-            band_row(kp, w, S, f, v + chi + 1, -1, staged);
-        __syncthreads();
-        dp_row<TAU>(kp, S.band, Ep, Ec, S.bt + (size_t)(v - seg_lo) * Wq);
-        __syncthreads();
-        int *tmp = Ep;
-        Ep = Ec;
-        Ec = tmp;
-    }
-    // ---- path start: smallest u minimising E_{vtop} ----
-    int bv = 0x7fffffff, bi = 0x7fffffff;
-    for (int u = tid; u < W; u += nt)
-        if (Ep[u] < bv) {
-            bv = Ep[u];
-            bi = u;
-        }
-    const int ustar = block_argmin(bv, bi, S.sh + kMaxChunks);
-    if (tid == 0) {
-        S.path[vtop] = (int16_t)ustar;
-        const int hi = min(vtop + SR - 1, vmax - 1);
-        for (int v = vtop; v <= hi && nseg > 0; ++v)
-            S.path[v + 1] = (int16_t)(S.path[v] + bt_get(S.bt, Wq, v - vtop, S.path[v]));
     }
     __syncthreads();
-    // ---- lower segments: restore the checkpoint, recompute the backtrack rows, follow them ----
-    for (int sg = 1; sg < nseg; ++sg) {
-        const int lo = vtop + sg * SR, hi = min(vtop + (sg + 1) * SR - 1, vmax - 1);
-        for (int u = tid; u < W; u += nt) {
-            S.E0[u] = ck[(size_t)(2 * sg) * W + u];
-            S.band[u] = ck[(size_t)(2 * sg + 1) * W + u];
+    // each vote enters at most 2 chi + 1 band rows, so |E| <= varrho (2 chi + 1) votes + lambda_x tau_x rows
+    const bool packed = ((double)kp.vote_rho * (2.0 * chi + 1.0) * votes + (double)kp.lambda_x * kp.tau_x * H) * 16.0 <
+                        536870912.0;
+    if (packed)
+        vpx_dp_body<TAU, true>(kp, w, S, f, vtop, staged);
+    else
+        vpx_dp_body<TAU, false>(kp, w, S, f, vtop, staged);
+
+    // ---- rows whose path cell holds votes: a vote of rows [v - chi, v + chi] in column u_v ----
+    // Column bitmaps of the vote rows (bit r - rb of column u), in the space the backtrack rows used, built
+    // for blocks of B path rows at a time (a block needs the vote rows [R0 - chi, R1 + chi)).
+    uint32_t *cb = reinterpret_cast<uint32_t *>(S.dyn);
+    const int words = (int)(((size_t)kp.seg_rows * 2 * Wq) / (4 * (size_t)W));
+    const int B = max(32, (words * 32 - 2 * chi - 32) / 32 * 32);
+    for (int R0 = vtop; R0 <= vmax; R0 += B) {
+        const int R1 = min(R0 + B, vmax + 1), rb = R0 - chi;
+        const int HB = (R1 + chi - rb + 31) >> 5;
+        for (int j = tid; j < W * HB; j += nt)
+            cb[j] = 0u;
+        __syncthreads();
+        const int rlo = max(vtop, R0 - chi), rhi = min(vmax, R1 - 1 + chi);
+        for (int r0 = rlo + 4 * warp; r0 <= rhi; r0 += 4 * nw) {
+            const int r = r0 + (lane >> 3);
+            if (r <= rhi) {
+                const VoteRow vr = vote_row(kp, w, S, f, r, staged);
+                for (int q = lane & 7; q < vr.n; q += 8)
+                    atoms_or(sa(cb + (size_t)vr.p[q] * HB + ((r - rb) >> 5)), 1u << ((r - rb) & 31));
+            }
         }
         __syncthreads();
-        Ep = S.E0;
-        Ec = S.E1;
-        for (int v = hi; v >= lo; --v) {
-            if (v - chi >= vtop)
-                band_row(kp, w, S, f, v - chi, +1, staged);
-            if (v + chi + 1 <= vmax)
-                band_row(kp, w, S, f, v + chi + 1, -1, staged);
-            __syncthreads();
-            dp_row<TAU>(kp, S.band, Ep, Ec, S.bt + (size_t)(v - lo) * Wq);
-            __syncthreads();
-            int *tmp = Ep;
-            Ep = Ec;
-            Ec = tmp;
+        for (int v = R0 + tid; v < R1; v += nt) {
+            const uint32_t *col = cb + (size_t)S.path[v] * HB;
+            const int lo = max(vtop, v - chi) - rb, hi = min(vmax, v + chi) - rb;
+            uint8_t sp = 0;
+            for (int wd = lo >> 5; wd <= hi >> 5; ++wd) {
+                uint32_t m = col[wd];
+                if (wd == lo >> 5)
+                    m &= 0xffffffffu << (lo & 31);
+                if (wd == hi >> 5)
+                    m &= 0xffffffffu >> (31 - (hi & 31));
+                sp |= m != 0u;
+            }
+            S.sup[v] = sp;
         }
-        if (tid == 0)
-            for (int v = lo; v <= hi; ++v)
-                S.path[v + 1] = (int16_t)(S.path[v] + bt_get(S.bt, Wq, v - lo, S.path[v]));
         __syncthreads();
     }
-
-    // ---- rows whose path cell holds votes: some vote of rows [v - chi, v + chi] in column u_v ----
-    for (int v = tid; v < H; v += nt)
+    for (int v = tid; v < vtop; v += nt)
         S.sup[v] = 0;
     __syncthreads();
-    for (int r = vtop + warp; r <= vmax; r += nw) {
-        const int cnt = S.voff[r + 1] - S.voff[r];
-        const int16_t *src = staged ? S.vb + S.voff[r] : w.vbins + ((size_t)f * H + r) * W;
-        const int lo = max(vtop, r - chi), hi = min(vmax, r + chi);
-        for (int q = lane; q < cnt; q += 32) {
-            const int b = src[q];
-            for (int v = lo; v <= hi; ++v)
-                if (S.path[v] == b)
-                    S.sup[v] = 1;
-        }
-    }
-    __syncthreads();
     const int t = vmax - vtop + 1;
-    const int k = block_compact(S.sup + vtop, t, pid, S.sh);
+    const int k = block_compact(S.sup + vtop, t, S.pid, S.sh);
     int16_t *gp = w.pts + ((size_t)f * 2 + 1) * 3 * w.pmax;
     for (int j = tid; j < k; j += nt) {
-        gp[j] = (int16_t)(vtop + pid[j]);
-        gp[w.pmax + j] = S.path[vtop + pid[j]];
-        gp[2 * w.pmax + j] = (int16_t)(vtop + pid[j]);
+        gp[j] = (int16_t)(vtop + S.pid[j]);
+        gp[w.pmax + j] = S.path[vtop + S.pid[j]];
+        gp[2 * w.pmax + j] = (int16_t)(vtop + S.pid[j]);
     }
     for (int v = tid; v < H; v += nt)
         w.path_x[(size_t)f * H + v] = v >= vtop ? S.path[v] : (int16_t)0;
@@ -472,12 +680,13 @@ int vpx_threads(int W)
 
 size_t vpx_fixed_bytes(const KParams &kp)
 {
-    const size_t W = kp.W, H = kp.H;
+    const size_t W = kp.W, H = kp.H, Wq = (W + 3) / 4;
     size_t s = 0;
     auto add = [&](size_t bytes) { s = ((s + 15) & ~(size_t)15) + bytes; };
-    add(4 * (W + 2 * kPadX));
-    add(4 * (W + 2 * kPadX));
-    add(4 * W);
+    add(4 * (4 * Wq + 2 * kPadX));
+    add(4 * (4 * Wq + 2 * kPadX));
+    add(4 * 4 * Wq);
+    add(4 * 4 * Wq);
     add(4 * (H + 1));
     add(2 * (size_t)kp.vote_cap);
     add(2 * H);
@@ -486,6 +695,12 @@ size_t vpx_fixed_bytes(const KParams &kp)
     add(2 * H);
     return ((s + 15) & ~(size_t)15) + 64;
 }
+
+// Bytes of the reusable region: the backtrack rows, later the column bitmaps of blocks of vote rows.
+size_t vpx_dyn_bytes(const KParams &kp) { return (size_t)kp.seg_rows * 2 * ((kp.W + 3) / 4); }
+
+// Words per column the bitmaps of a block of 32 path rows need: 32 + 2 chi rows, one word of alignment.
+size_t vpx_min_dyn_bytes(const KParams &kp) { return (size_t)4 * kp.W * ((32 + 2 * kp.chi + 32 + 31) / 32 + 1); }
 
 using VpxKernel = void (*)(KParams, Work);
 VpxKernel vpx_kernel(int tau)
@@ -522,15 +737,12 @@ size_t road_smem_bytes(const KParams &kp)
     return s + 64;
 }
 
-size_t vpx_smem_bytes(const KParams &kp)
-{
-    return vpx_fixed_bytes(kp) + (size_t)kp.seg_rows * 2 * ((kp.W + 3) / 4);
-}
+size_t vpx_smem_bytes(const KParams &kp) { return vpx_fixed_bytes(kp) + vpx_dyn_bytes(kp); }
 
 int vpx_seg_rows(const KParams &kp, size_t budget)
 {
     const size_t fixed = vpx_fixed_bytes(kp);
-    if (budget <= fixed)
+    if (budget <= fixed + vpx_min_dyn_bytes(kp))
         return 0;
     return (int)((budget - fixed) / (2 * ((kp.W + 3) / 4)));
 }
