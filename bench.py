@@ -185,32 +185,49 @@ def run_ours(args):
     disp = [torch.from_numpy(d0).cuda(), torch.from_numpy(d1).cuda()]
     img = [torch.from_numpy(i0).cuda(), torch.from_numpy(i1).cuda()]
     p = ld.default_params(n_disp=cfg.n_disp)
-    stream = torch.cuda.Stream()
-    det = ld.Detector(W, H, n, p, stream=stream)
-    outs = [det.alloc_lanes(n), det.alloc_lanes(n)]
+    # S streams, one library handle each; consecutive batches alternate between them so one batch's
+    # per-frame serial stages overlap the next batch's dense stages
+    S = max(1, args.streams)
+    streams = [torch.cuda.Stream() for _ in range(S)]
+    dets = [ld.Detector(W, H, n, p, stream=st) for st in streams]
+    det = dets[0]
+    stream = streams[0]
+    outs = [[d.alloc_lanes(n), d.alloc_lanes(n)] for d in dets]
     torch.cuda.synchronize()
 
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    with torch.cuda.stream(stream):
-        for s in range(max(args.warmup, 3)):
-            det.detect(disp[s & 1], img[s & 1], outs[s & 1])
-        stream.synchronize()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t_wall0 = time.time()
-        evs[0].record(stream)
-        for s in range(args.steps):
-            det.detect(disp[s & 1], img[s & 1], outs[s & 1])
-            evs[s + 1].record(stream)
-        stream.synchronize()
-        torch.cuda.synchronize()
-        t_wall1 = time.time()
-        if world > 1:
-            dist.barrier()
-    total_ms = evs[0].elapsed_time(evs[-1])
-    step_ms = np.array([evs[s].elapsed_time(evs[s + 1]) for s in range(args.steps)])
+    for s in range(max(args.warmup, 3) * S):
+        k = s % S
+        with torch.cuda.stream(streams[k]):
+            dets[k].detect(disp[s & 1], img[s & 1], outs[k][s & 1])
+    torch.cuda.synchronize()
+    ev_start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_end = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    main = torch.cuda.current_stream()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0.record(main)
+    for st in streams:
+        st.wait_event(ev0)
+    for s in range(args.steps):
+        k = s % S
+        with torch.cuda.stream(streams[k]):
+            ev_start[s].record(streams[k])
+            dets[k].detect(disp[s & 1], img[s & 1], outs[k][s & 1])
+            ev_end[s].record(streams[k])
+    for st in streams:
+        main.wait_stream(st)
+    ev1.record(main)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if world > 1:
+        dist.barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    step_ms = np.array([ev_start[s].elapsed_time(ev_end[s]) for s in range(args.steps)])
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -223,22 +240,32 @@ def run_ours(args):
     per = np.zeros(len(names))
     with torch.cuda.stream(stream):
         for s in range(kp_steps):
-            per += det.detect_timed(disp[s & 1], img[s & 1], outs[s & 1])
+            per += det.detect_timed(disp[s & 1], img[s & 1], outs[0][s & 1])
     per /= kp_steps
     if clocks:
         clocks.stop()
 
-    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region; one host
+    # thread per handle, so one batch's copies overlap another batch's kernels
     hd = [torch.from_numpy(d0).pin_memory(), torch.from_numpy(d1).pin_memory()]
     hi = [torch.from_numpy(i0).pin_memory(), torch.from_numpy(i1).pin_memory()]
-    res = np.zeros(n, ld.LANES_DTYPE)
-    e2e_steps = max(3, min(args.steps, 20))
-    det.detect_host_ptr(hd[0].data_ptr(), hi[0].data_ptr(), W, H, n, res)
+    e2e_steps = max(2 * S, min(args.steps, 40))
+    res = [np.zeros(n, ld.LANES_DTYPE) for _ in range(S)]
+    for k in range(S):
+        dets[k].detect_host_ptr(hd[k & 1].data_ptr(), hi[k & 1].data_ptr(), W, H, n, res[k])
+
+    def e2e_worker(k):
+        for s in range(k, e2e_steps, S):
+            dets[k].detect_host_ptr(hd[s & 1].data_ptr(), hi[s & 1].data_ptr(), W, H, n, res[k])
+
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        det.detect_host_ptr(hd[s & 1].data_ptr(), hi[s & 1].data_ptr(), W, H, n, res)
+    ths = [threading.Thread(target=e2e_worker, args=(k,)) for k in range(S)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
     e2e_s = time.perf_counter() - t0
     te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -289,6 +316,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
             "data": "synthetic (seeded KITTI-shaped scenes; KITTI is not available)",
             "config": {"workload": f"{WORKLOAD} plain form", "frames_per_step": n, "width": W, "height": H,
+                       "streams": S,
                        "n_disp": cfg.n_disp, "outliers": cfg.outlier_frac, "invalid": cfg.invalid_frac,
                        "l2": "inputs larger than L2 (two alternating 149 MB input batches)",
                        "parallelism": f"replicas x{world}"},
@@ -301,7 +329,8 @@ def run_ours(args):
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    det.close()
+    for d in dets:
+        d.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -352,6 +381,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--streams", type=int, default=2, help="library handles on separate streams, batches alternate")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
