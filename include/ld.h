@@ -72,7 +72,7 @@ typedef struct ld_params {
     int32_t lambda_g;         /* Eq. 24 recursion weight (1) */
     int32_t xi_num, xi_den;   /* xi = 1/2: lane starts s in [-floor(xi W), W + floor(xi W)) */
     int32_t thr_num, thr_den; /* lane threshold t = ceil(thr * min H) (not given; 1/32) */
-    int32_t near_px;          /* minima closer than this are "nearby" (not given; 30) */
+    int32_t near_px;          /* minima closer than this are suppressed (not given; 30) */
     int32_t max_lanes;        /* <= LD_MAX_LANES */
     int32_t ransac_hyps;      /* hypotheses per RANSAC round (64, at most 256) */
     int32_t ransac_rounds;    /* RANSAC round cap (64) */

@@ -292,7 +292,7 @@ static int32_t is_inlier(const float *c, const float *nodes, int32_t m, int32_t 
 }
 
 /* ------------------------------------------------------------------------------------------------ */
-/* One RANSAC hypothesis (Alg. 4 / Alg. 6: "select a specified number of candidates randomly, fit").  */
+/* One RANSAC hypothesis (Alg. 4 / Alg. 6: a random sample of the working set and the fit through it).   */
 /* Reading: the sample is minimal (m points: 3 for beta, 5 for gamma) and drawn from the current      */
 /* working set S (member[j] = 1), listed in increasing j.  Draw j = 0, 1, ... takes word (j & 3) of    */
 /* Philox4x32-10 at counter (stage << 24 | round, hyp, j >> 2, 0), key = seed; the word x picks list   */

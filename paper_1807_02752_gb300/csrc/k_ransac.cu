@@ -5,8 +5,8 @@
 //   k_fit<5>  Alg. 6 on the V_px DP path M_x (points (v, u_v)), fit of Eq. 19 / Eq. 20 -> gamma; then
 //             V_px(v) (Eq. 22) per road row.
 //
-// Reading of the loop ("select a specified number of candidates randomly, fit, count inliers, remove
-// outliers, repeat until n_I / n reaches eps", Alg. 4 / Alg. 6):
+// Reading of the loop of Alg. 4 / Alg. 6 (draw a random sample, fit it, count inliers, drop the outliers,
+// repeat until the inlier fraction reaches eps, then fit the inliers):
 //   - each round draws `hyps` minimal samples (M points) from the working set S, listed in increasing point
 //     index; draw j takes word j & 3 of Philox4x32-10 at counter (stage << 24 | round, hypothesis, j >> 2, 0)
 //     with key = seed, and picks list position floor(word * |S| / 2^32); a draw repeating a chosen point or a
