@@ -16,12 +16,13 @@
 // A path point whose cell holds no count carries no observation; the kernels hand the points with data to
 // the RANSAC fit (k_fit), in increasing index order.
 //
-// Each DP step is one row of the map.  A thread owns four adjacent cells: it loads the window of the
-// previous row they share once and writes their four 4-bit backtrack entries as one 16-bit word.  The CTA
-// is sized to the row (one thread per four cells), so the per-row barriers involve few warps.  Rows are
-// padded with sentinels so the candidate loops have no bounds checks.  The V_px DP keeps as many backtrack
-// rows in shared memory as fit; taller road areas are processed in segments, with the DP state
-// checkpointed at segment boundaries and recomputed during the backtrack.
+// Each DP step is one row of the map.  In the road DP a thread owns four adjacent cells and writes their
+// four 4-bit backtrack entries as one 16-bit word; in the V_px DP a thread owns a pair of cells (more warps
+// per row, which is the latency-bound loop of the path) and writes one byte.  A thread loads the window of
+// the previous row its cells share once.  The CTA is sized to the row, so the per-row barriers involve few
+// warps.  Rows are padded with sentinels so the candidate loops have no bounds checks.  The V_px DP keeps
+// the backtrack rows of the top of the road in shared memory; the rows below go to a per-frame global
+// buffer (L2-resident) and come back in blocks for the backtrack.
 #include "ld_internal.cuh"
 
 namespace ld {
@@ -33,7 +34,7 @@ constexpr int kRoadQ = (LD_MAX_H / 4 + kRoadThreads - 1) / kRoadThreads;  // qua
 constexpr int kMaxChunks = (LD_MAX_H + 31) / 32 + 2;
 constexpr int kSent = 0x3fffffff;  // larger than any DP energy (checked when the handle is created)
 constexpr int kPadY = 20;          // >= 3 + tau_y
-constexpr int kPadX = 16;          // >= 3 + tau_x
+constexpr int kPadX = 16;          // >= tau_x rounded up to even, + 1
 
 template <typename T>
 __device__ __forceinline__ T *carve(unsigned char *&p, size_t count)
@@ -124,12 +125,6 @@ __device__ __forceinline__ int lds(uint32_t a)
 }
 __device__ __forceinline__ void sts(uint32_t a, int v) { asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v)); }
 __device__ __forceinline__ void sts16(uint32_t a, uint32_t v) { asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v)); }
-__device__ __forceinline__ int lds16s(uint32_t a)
-{
-    short v;
-    asm volatile("ld.shared.s16 %0, [%1];" : "=h"(v) : "r"(a));
-    return v;
-}
 __device__ __forceinline__ void atoms_add(uint32_t a, int v) { asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v)); }
 
 // ---------------------------------------------------------------------------------------------------
@@ -261,29 +256,39 @@ __global__ void __launch_bounds__(kRoadThreads) k_road_dp(const KParams kp, cons
 // ---------------------------------------------------------------------------------------------------
 // k_vpx_dp
 // ---------------------------------------------------------------------------------------------------
-__device__ __forceinline__ int4 lds4(uint32_t a)
+__device__ __forceinline__ int2 lds2(uint32_t a)
 {
-    int4 v;
-    asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    int2 v;
+    asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
     return v;
 }
-__device__ __forceinline__ void sts4(uint32_t a, int4 v)
+__device__ __forceinline__ void sts2(uint32_t a, int2 v)
 {
-    asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w));
+    asm volatile("st.shared.v2.s32 [%0], {%1, %2};" ::"r"(a), "r"(v.x), "r"(v.y));
+}
+__device__ __forceinline__ void sts8(uint32_t a, uint32_t v) { asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v)); }
+__device__ __forceinline__ uint32_t lds8(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
 }
 __device__ __forceinline__ void atoms_or(uint32_t a, uint32_t v) { asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(a), "r"(v)); }
+
+// A thread owns the cell pairs j = tid + p * blockDim.x (p < NP), cells 2j and 2j + 1.  A backtrack row
+// holds one byte per pair (two 4-bit entries), padded to 16 bytes (vpx_row_bytes).
 
 // Shared-memory layout of k_vpx_dp.
 struct VpxMem {
     int *E0, *E1;          // E rows, column 0 at index 0, padded by kPadX sentinels on both sides
-    int *D0, *D1;          // band deltas of the next row (double-buffered), [4 Wq]
+    int *D0, *D1;          // band deltas of the next row (double-buffered), [2 pairs]
     int *voff;             // [H + 1] offsets of the staged vote rows (prefix of the per-row counts)
     int16_t *vb;           // [vote_cap]
     int16_t *path;         // [H]
     uint8_t *sup;          // [H]
     int *sh;
     int16_t *pid;          // [H]
-    unsigned char *dyn;    // backtrack rows [seg_rows][Wq] (uint16), later the column bitmaps of the votes
+    unsigned char *dyn;    // backtrack rows [seg_rows][row bytes], later the column bitmaps of the votes
 };
 
 // Vote columns of row r (staged in shared memory, else the frame's list in global memory).
@@ -317,38 +322,37 @@ __device__ __forceinline__ void scatter_delta(const KParams &kp, const Work &w, 
     }
 }
 
-// One Eq. 18 row for the four cells u0 .. u0+3 of this thread.  ep, ec: shared addresses of column 0 of
-// E_{v+1} and E_v (16-byte aligned at column u0 - 8); band: this thread's band counts of row v.
-// PACKED: E rows hold 16 E and the candidate key 16 (E + lambda |tau|) + k (k = rank in the tie order
-// tau = 0, -1, +1, -2, ...) makes the tie-broken argmin an integer minimum; otherwise compare-select in tie
-// order.  Writes the four E_v values (sentinels past the last column) and the backtrack word.
+// One Eq. 18 row for the cells u0 = 2j, u0 + 1.  ep, ec: shared addresses of column 0 of E_{v+1} and E_v;
+// the window [u0 - TW, u0 + 1 + TW] (TW = tau_x rounded up to even) is read as 8-byte loads.  pen[k]: the
+// penalty of candidate k in tie order tau = 0, -1, +1, -2, ... (16 lambda_x |tau| + k when PACKED, so the
+// tie-broken argmin is an integer minimum; lambda_x |tau| otherwise, compare-select in tie order).
+// Writes E_v of the two cells (a sentinel past the last column) and returns the backtrack byte.
 template <int TAU, bool PACKED>
-__device__ __forceinline__ void dp_quad(const KParams &kp, int u0, const int *band, uint32_t ep, uint32_t ec,
-                                        uint32_t btword)
+__device__ __forceinline__ uint32_t dp_pair(const KParams &kp, int u0, int b0, int b1, const int *pen, uint32_t ep,
+                                            uint32_t ec)
 {
     constexpr int NK = 2 * TAU + 1;
-    const int W = kp.W;
-    int e[20];
+    constexpr int TW = (TAU + 1) & ~1;
+    constexpr int NL = TW + 1;  // 8-byte loads: values u0 - TW .. u0 + 1 + TW
+    int e[2 * NL];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        const int4 v4 = lds4(ep + 4u * (uint32_t)(u0 - 8 + 4 * j));
-        e[4 * j] = v4.x;
-        e[4 * j + 1] = v4.y;
-        e[4 * j + 2] = v4.z;
-        e[4 * j + 3] = v4.w;
+    for (int j = 0; j < NL; ++j) {
+        const int2 v2 = lds2(ep + 4u * (uint32_t)(u0 - TW + 2 * j));
+        e[2 * j] = v2.x;
+        e[2 * j + 1] = v2.y;
     }
-    int out[4];
+    const int band[2] = {b0, b1};
+    int out[2];
     uint32_t code = 0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 2; ++c) {
         int best, arg;
         if (PACKED) {
             int kk[NK];
 #pragma unroll
             for (int k = 0; k < NK; ++k) {
                 const int t = (k & 1) ? -((k + 1) >> 1) : (k >> 1);
-                const int a = t < 0 ? -t : t;
-                kk[k] = e[8 + c + t] + 16 * kp.lambda_x * a + k;
+                kk[k] = e[TW + c + t] + pen[k];
             }
 #pragma unroll
             for (int st = 1; st < NK; st *= 2)
@@ -358,76 +362,31 @@ __device__ __forceinline__ void dp_quad(const KParams &kp, int u0, const int *ba
             best = kk[0] & ~15;
             arg = kk[0] & 15;
         } else {
-            best = e[8 + c];
+            best = e[TW + c];
             arg = 0;
 #pragma unroll
             for (int k = 1; k < NK; ++k) {
                 const int t = (k & 1) ? -((k + 1) >> 1) : (k >> 1);
-                const int cand = e[8 + c + t] + kp.lambda_x * (t < 0 ? -t : t);
+                const int cand = e[TW + c + t] + pen[k];
                 if (cand < best) {
                     best = cand;
                     arg = t & 15;
                 }
             }
         }
-        const bool in = u0 + c < W;
+        const bool in = u0 + c < kp.W;
         out[c] = in ? (PACKED ? 16 : 1) * -kp.vote_rho * band[c] + best : kSent;
         code |= (uint32_t)(in ? arg : 0) << (4 * c);
     }
-    sts4(ec + 4u * (uint32_t)u0, make_int4(out[0], out[1], out[2], out[3]));
-    sts16(btword, code);
+    sts2(ec + 4u * (uint32_t)u0, make_int2(out[0], out[1]));
+    return code;
 }
 
-// Rows hi down to lo of the DP.  On entry Ep holds E_{hi+1}, band the counts of row hi+1 for this thread's
-// cells, and delta buffer (hi & 1) the change from row hi+1 to row hi.  Each row: scatter the change for the
-// next row into the other buffer (while no thread reads it), fold this row's change into the register
-// counts, update the row, one barrier.  Checkpoints (forward pass only) save E_{v+1} and the counts of row
-// v+1 at the first row of every segment above the top one.
-template <int TAU, bool PACKED>
-__device__ void dp_rows(const KParams &kp, const Work &w, const VpxMem &S, int f, int hi, int lo, int vtop, bool staged,
-                        int *band, int *&Ep, int *&Ec, int slot_lo, bool checkpoint, int32_t *ck)
+// Backtrack step at column u of a row starting at shared address rowa: tau from a 4-bit two's complement
+// entry, or from the tie rank of the packed form.
+__device__ __forceinline__ int bt_step(uint32_t rowa, int u, bool packed)
 {
-    const int W = kp.W, Wq = (W + 3) >> 2, SR = kp.seg_rows;
-    const int i = threadIdx.x, u0 = 4 * i;
-    const bool own = i < Wq;
-    const uint32_t d0 = sa(S.D0), d1 = sa(S.D1), bt = sa(S.dyn);
-    for (int v = hi; v >= lo; --v) {
-        if (checkpoint) {
-            const int seg = (v - vtop) / SR;
-            if (seg > 0 && v == min(vtop + (seg + 1) * SR - 1, kp.H - 2) && own) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (u0 + c < W) {
-                        ck[(size_t)(2 * seg) * W + u0 + c] = Ep[u0 + c];
-                        ck[(size_t)(2 * seg + 1) * W + u0 + c] = band[c];
-                    }
-            }
-        }
-        if (v - 1 >= lo)
-            scatter_delta(kp, w, S, f, v - 1, vtop, staged, ((v - 1) & 1) ? d1 : d0);
-        if (own) {
-            const uint32_t da = ((v & 1) ? d1 : d0) + 16u * (uint32_t)i;
-            const int4 dl = lds4(da);
-            sts4(da, make_int4(0, 0, 0, 0));
-            band[0] += dl.x;
-            band[1] += dl.y;
-            band[2] += dl.z;
-            band[3] += dl.w;
-            const int slot = checkpoint ? (v - vtop) % SR : v - slot_lo;
-            dp_quad<TAU, PACKED>(kp, u0, band, sa(Ep), sa(Ec), bt + 2u * ((uint32_t)slot * Wq + i));
-        }
-        __syncthreads();
-        int *tmp = Ep;
-        Ep = Ec;
-        Ec = tmp;
-    }
-}
-
-// Backtrack step of row `slot` at column u: tau from a 4-bit two's complement entry, or from the tie rank
-// of the packed form.
-__device__ __forceinline__ int bt_get(const uint16_t *bt, int Wq, int slot, int u, bool packed)
-{
-    const int nib = nib16(bt + (size_t)slot * Wq, u);
+    const int nib = (int)(lds8(rowa + ((uint32_t)u >> 1)) >> (4 * (u & 1))) & 15;
     if (packed)
         return (nib & 1) ? -((nib + 1) >> 1) : (nib >> 1);
     return (nib ^ 8) - 8;
@@ -453,14 +412,24 @@ __device__ void block_scan(int *a, int n, int *chunk)
             chunk[c] = inc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int c = 0; c < nch; ++c) {
-            const int t = chunk[c];
-            chunk[c] = s;
-            s += t;
+    if (threadIdx.x < 32) {
+        // exclusive scan of the chunk totals by one warp
+        int carry = 0;
+        for (int c0 = 0; c0 < nch; c0 += 32) {
+            const int c = c0 + threadIdx.x;
+            const int x = c < nch ? chunk[c] : 0;
+            int inc = x;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o = __shfl_up_sync(0xffffffffu, inc, d);
+                if ((int)threadIdx.x >= d)
+                    inc += o;
+            }
+            if (c < nch)
+                chunk[c] = carry + inc - x;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
         }
-        a[n] = s;
+        if (threadIdx.x == 0)
+            a[n] = carry;
     }
     __syncthreads();
     for (int c = warp; c < nch; c += nw) {
@@ -471,44 +440,86 @@ __device__ void block_scan(int *a, int n, int *chunk)
     __syncthreads();
 }
 
-template <int TAU, bool PACKED>
+// Forward DP over rows vmax-1 .. vtop, then the backtrack.  Backtrack rows of the top seg_rows rows stay
+// in shared memory; lower rows go to the frame's global buffer and come back in blocks of seg_rows rows
+// for the backtrack.
+template <int TAU, bool PACKED, int NP>
 __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, int f, int vtop, bool staged)
 {
-    const int W = kp.W, H = kp.H, Wq = (W + 3) >> 2, vmax = H - 1, chi = kp.chi, SR = kp.seg_rows;
+    const int W = kp.W, H = kp.H, vmax = H - 1, chi = kp.chi, SR = kp.seg_rows;
+    const int NPr = vpx_pairs(W), RB = vpx_row_bytes(W);
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int i = tid, u0 = 4 * i;
-    const bool own = i < Wq;
-    // ---- counts of row vmax: rows [max(vtop, vmax - chi), vmax], gathered in D0 ----
-    for (int r = max(vtop, vmax - chi); r <= vmax; ++r) {
-        const VoteRow vr = vote_row(kp, w, S, f, r, staged);
-        for (int q = tid; q < vr.n; q += nt)
-            atoms_add(sa(S.D0) + 4u * (uint32_t)vr.p[q], 1);
-    }
-    __syncthreads();
-    int band[4] = {0, 0, 0, 0};
-    if (own) {
-        const int4 b4 = lds4(sa(S.D0) + 16u * i);
-        band[0] = b4.x;
-        band[1] = b4.y;
-        band[2] = b4.z;
-        band[3] = b4.w;
-        sts4(sa(S.D0) + 16u * i, make_int4(0, 0, 0, 0));
-        int e4[4];
+    constexpr int NK = 2 * TAU + 1;
+    int pen[NK];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-            e4[c] = u0 + c < W ? (PACKED ? 16 : 1) * -kp.vote_rho * band[c] : kSent;
-        sts4(sa(S.E0) + 16u * i, make_int4(e4[0], e4[1], e4[2], e4[3]));
+    for (int k = 0; k < NK; ++k) {
+        const int t = (k & 1) ? -((k + 1) >> 1) : (k >> 1);
+        pen[k] = PACKED ? 16 * kp.lambda_x * (t < 0 ? -t : t) + k : kp.lambda_x * (t < 0 ? -t : t);
+    }
+    const uint32_t d0 = sa(S.D0), d1 = sa(S.D1), bt = sa(S.dyn);
+    uint8_t *gbt = w.gbt + (size_t)f * w.max_h * vpx_row_bytes(w.max_w);
+    // ---- counts of row vmax: the votes of rows [max(vtop, vmax - chi), vmax], gathered in D0 ----
+    {
+        const int r0 = max(vtop, vmax - chi);
+        if (staged) {
+            for (int q = S.voff[r0] + tid; q < S.voff[vmax + 1]; q += nt)
+                atoms_add(d0 + 4u * (uint32_t)S.vb[q], 1);
+        } else {
+            for (int r = r0; r <= vmax; ++r) {
+                const VoteRow vr = vote_row(kp, w, S, f, r, staged);
+                for (int q = tid; q < vr.n; q += nt)
+                    atoms_add(d0 + 4u * (uint32_t)vr.p[q], 1);
+            }
+        }
     }
     __syncthreads();
-    // ---- forward DP over rows vmax-1 .. vtop ----
-    const int nrows = vmax - vtop;
-    const int nseg = (nrows + SR - 1) / SR;
-    int32_t *ck = w.ckpt + (size_t)f * w.max_seg * 2 * W;
+    int band[NP][2];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int j = tid + p * nt;
+        band[p][0] = band[p][1] = 0;
+        if (j < NPr) {
+            const int2 b2 = lds2(d0 + 8u * (uint32_t)j);
+            band[p][0] = b2.x;
+            band[p][1] = b2.y;
+            sts2(d0 + 8u * (uint32_t)j, make_int2(0, 0));
+            int e2[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+                e2[c] = 2 * j + c < W ? (PACKED ? 16 : 1) * -kp.vote_rho * band[p][c] : kSent;
+            sts2(sa(S.E0) + 8u * (uint32_t)j, make_int2(e2[0], e2[1]));
+        }
+    }
+    __syncthreads();
     int *Ep = S.E0, *Ec = S.E1;
-    if (nrows > 0) {
-        scatter_delta(kp, w, S, f, vmax - 1, vtop, staged, ((vmax - 1) & 1) ? sa(S.D1) : sa(S.D0));
+    if (vmax - 1 >= vtop) {
+        scatter_delta(kp, w, S, f, vmax - 1, vtop, staged, ((vmax - 1) & 1) ? d1 : d0);
         __syncthreads();
-        dp_rows<TAU, PACKED>(kp, w, S, f, vmax - 1, vtop, vtop, staged, band, Ep, Ec, vtop, true, ck);
+    }
+    for (int v = vmax - 1; v >= vtop; --v) {
+        if (v - 1 >= vtop)
+            scatter_delta(kp, w, S, f, v - 1, vtop, staged, ((v - 1) & 1) ? d1 : d0);
+        const uint32_t dv = (v & 1) ? d1 : d0;
+        const int r = v - vtop;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int j = tid + p * nt;
+            if (j < NPr) {
+                const int2 dl = lds2(dv + 8u * (uint32_t)j);
+                sts2(dv + 8u * (uint32_t)j, make_int2(0, 0));
+                band[p][0] += dl.x;
+                band[p][1] += dl.y;
+                const uint32_t code = dp_pair<TAU, PACKED>(kp, 2 * j, band[p][0], band[p][1], pen, sa(Ep), sa(Ec));
+                if (r < SR)
+                    sts8(bt + (uint32_t)(r * RB + j), code);
+                else
+                    gbt[(size_t)v * RB + j] = (uint8_t)code;
+            }
+        }
+        __syncthreads();
+        int *tmp = Ep;
+        Ep = Ec;
+        Ec = tmp;
     }
     // ---- path start: smallest u minimising E_{vtop} ----
     int bv = 0x7fffffff, bi = 0x7fffffff;
@@ -518,48 +529,38 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
             bi = u;
         }
     const int ustar = block_argmin(bv, bi, S.sh + kMaxChunks);
-    const uint16_t *bt = reinterpret_cast<const uint16_t *>(S.dyn);
-    int upath = ustar;
-    if (tid == 0) {
-        S.path[vtop] = (int16_t)upath;
-        const int hi = min(vtop + SR - 1, vmax - 1);
-        for (int v = vtop; v <= hi && nseg > 0; ++v) {
-            upath += bt_get(bt, Wq, (v - vtop) % SR, upath, PACKED);
-            S.path[v + 1] = (int16_t)upath;
+    // ---- backtrack, one block of seg_rows rows at a time ----
+    int u = ustar;
+    for (int lo = vtop; lo <= vmax; lo += SR) {
+        const int hi = min(lo + SR - 1, vmax - 1);
+        if (lo > vtop) {
+            // rows lo .. hi from the global buffer into shared memory (16-byte copies)
+            __syncthreads();
+            const int n16 = (hi - lo + 1) * (RB >> 4);
+            const uint4 *src = reinterpret_cast<const uint4 *>(gbt + (size_t)lo * RB);
+            uint4 *dst = reinterpret_cast<uint4 *>(S.dyn);
+            for (int q = tid; q < n16; q += nt)
+                dst[q] = src[q];
+            __syncthreads();
         }
-    }
-    __syncthreads();
-    // ---- lower segments: restore the checkpoint, recompute the backtrack rows, follow them ----
-    for (int sg = 1; sg < nseg; ++sg) {
-        const int lo = vtop + sg * SR, hi = min(vtop + (sg + 1) * SR - 1, vmax - 1);
-        if (own)
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (u0 + c < W) {
-                    S.E0[u0 + c] = ck[(size_t)(2 * sg) * W + u0 + c];
-                    band[c] = ck[(size_t)(2 * sg + 1) * W + u0 + c];
-                }
-        Ep = S.E0;
-        Ec = S.E1;
-        scatter_delta(kp, w, S, f, hi, vtop, staged, (hi & 1) ? sa(S.D1) : sa(S.D0));
-        __syncthreads();
-        dp_rows<TAU, PACKED>(kp, w, S, f, hi, lo, vtop, staged, band, Ep, Ec, lo, false, ck);
         if (tid == 0) {
-            int u = S.path[lo];
-            for (int v = lo; v <= hi; ++v) {
-                u += bt_get(bt, Wq, v - lo, u, PACKED);
+            if (lo == vtop)
+                S.path[vtop] = (int16_t)u;
+            uint32_t rowa = bt;
+            for (int v = lo; v <= hi; ++v, rowa += (uint32_t)RB) {
+                u += bt_step(rowa, u, PACKED);
                 S.path[v + 1] = (int16_t)u;
             }
         }
-        __syncthreads();
     }
+    __syncthreads();
 }
 
-template <int TAU>
+template <int TAU, int NP>
 __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int f = blockIdx.x, W = kp.W, H = kp.H, Wq = (W + 3) >> 2;
+    const int f = blockIdx.x, W = kp.W, H = kp.H, NPr = vpx_pairs(W);
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const FrameState fs0 = w.fs[f];
     if (fs0.flags & LD_F_NO_LANES)
@@ -568,10 +569,10 @@ __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
 
     VpxMem S;
     unsigned char *p = smem;
-    S.E0 = carve<int>(p, 4 * Wq + 2 * kPadX) + kPadX;
-    S.E1 = carve<int>(p, 4 * Wq + 2 * kPadX) + kPadX;
-    S.D0 = carve<int>(p, 4 * Wq);
-    S.D1 = carve<int>(p, 4 * Wq);
+    S.E0 = carve<int>(p, 2 * NPr + 2 * kPadX) + kPadX;
+    S.E1 = carve<int>(p, 2 * NPr + 2 * kPadX) + kPadX;
+    S.D0 = carve<int>(p, 2 * NPr);
+    S.D1 = carve<int>(p, 2 * NPr);
     S.voff = carve<int>(p, H + 1);
     S.vb = carve<int16_t>(p, kp.vote_cap);
     S.path = carve<int16_t>(p, H);
@@ -583,11 +584,11 @@ __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
     // ---- vote rows [vtop, vmax]: offsets by a block scan, staged in shared memory when they fit ----
     for (int v = tid; v < H; v += nt)
         S.voff[v] = v >= vtop ? w.vcount[(size_t)f * H + v] : 0;
-    for (int u = tid; u < 4 * Wq; u += nt) {
+    for (int u = tid; u < 2 * NPr; u += nt) {
         S.D0[u] = 0;
         S.D1[u] = 0;
     }
-    for (int u = tid - kPadX; u < 4 * Wq + kPadX; u += nt)
+    for (int u = tid - kPadX; u < 2 * NPr + kPadX; u += nt)
         if (u < 0 || u >= W) {
             S.E0[u] = kSent;
             S.E1[u] = kSent;
@@ -597,13 +598,32 @@ __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
     const int votes = S.voff[H];
     const bool staged = votes <= kp.vote_cap;
     if (staged) {
-        for (int r0 = vtop + 4 * warp; r0 <= vmax; r0 += 4 * nw) {
-            const int r = r0 + (lane >> 3);
-            if (r <= vmax) {
-                const int off = S.voff[r], cnt = S.voff[r + 1] - off;
-                const int16_t *src = w.vbins + ((size_t)f * H + r) * W;
-                for (int q = lane & 7; q < cnt; q += 8)
-                    S.vb[off + q] = src[q];
+        // every thread takes votes q = tid + k nt; its rows come from a binary search over the offsets,
+        // kStageBatch searches and loads in flight at once
+        constexpr int kStageBatch = 8;
+        for (int q0 = 0; q0 < votes; q0 += kStageBatch * nt) {
+            int16_t val[kStageBatch];
+#pragma unroll
+            for (int k = 0; k < kStageBatch; ++k) {
+                const int q = q0 + k * nt + tid;
+                val[k] = 0;
+                if (q < votes) {
+                    int lo = vtop, hi = vmax + 1;  // voff[lo] <= q < voff[hi]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (S.voff[mid] <= q)
+                            lo = mid;
+                        else
+                            hi = mid;
+                    }
+                    val[k] = __ldg(w.vbins + ((size_t)f * H + lo) * W + (q - S.voff[lo]));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kStageBatch; ++k) {
+                const int q = q0 + k * nt + tid;
+                if (q < votes)
+                    S.vb[q] = val[k];
             }
         }
     }
@@ -612,15 +632,15 @@ __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
     const bool packed = ((double)kp.vote_rho * (2.0 * chi + 1.0) * votes + (double)kp.lambda_x * kp.tau_x * H) * 16.0 <
                         536870912.0;
     if (packed)
-        vpx_dp_body<TAU, true>(kp, w, S, f, vtop, staged);
+        vpx_dp_body<TAU, true, NP>(kp, w, S, f, vtop, staged);
     else
-        vpx_dp_body<TAU, false>(kp, w, S, f, vtop, staged);
+        vpx_dp_body<TAU, false, NP>(kp, w, S, f, vtop, staged);
 
     // ---- rows whose path cell holds votes: a vote of rows [v - chi, v + chi] in column u_v ----
     // Column bitmaps of the vote rows (bit r - rb of column u), in the space the backtrack rows used, built
     // for blocks of B path rows at a time (a block needs the vote rows [R0 - chi, R1 + chi)).
     uint32_t *cb = reinterpret_cast<uint32_t *>(S.dyn);
-    const int words = (int)(((size_t)kp.seg_rows * 2 * Wq) / (4 * (size_t)W));
+    const int words = (int)(((size_t)kp.seg_rows * vpx_row_bytes(W)) / (4 * (size_t)W));
     const int B = max(32, (words * 32 - 2 * chi - 32) / 32 * 32);
     for (int R0 = vtop; R0 <= vmax; R0 += B) {
         const int R1 = min(R0 + B, vmax + 1), rb = R0 - chi;
@@ -671,51 +691,56 @@ __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
         w.npts[f * 2 + 1] = k;
 }
 
+// Threads: one per cell pair up to 1024 (two pairs per thread past 2048 columns).
+int vpx_np(int W) { return vpx_pairs(W) > 1024 ? 2 : 1; }
 int vpx_threads(int W)
 {
-    const int nq = (W + 3) / 4;
-    int nt = (nq + 31) / 32 * 32;
+    const int np = vpx_np(W);
+    int nt = ((vpx_pairs(W) + np - 1) / np + 31) / 32 * 32;
     return nt < 64 ? 64 : nt > 1024 ? 1024 : nt;
 }
 
 size_t vpx_fixed_bytes(const KParams &kp)
 {
-    const size_t W = kp.W, H = kp.H, Wq = (W + 3) / 4;
+    const size_t W = kp.W, H = kp.H, NPr = vpx_pairs(kp.W);
     size_t s = 0;
     auto add = [&](size_t bytes) { s = ((s + 15) & ~(size_t)15) + bytes; };
-    add(4 * (4 * Wq + 2 * kPadX));
-    add(4 * (4 * Wq + 2 * kPadX));
-    add(4 * 4 * Wq);
-    add(4 * 4 * Wq);
+    add(4 * (2 * NPr + 2 * kPadX));
+    add(4 * (2 * NPr + 2 * kPadX));
+    add(4 * 2 * NPr);
+    add(4 * 2 * NPr);
     add(4 * (H + 1));
     add(2 * (size_t)kp.vote_cap);
     add(2 * H);
     add(H);
     add(4 * (kMaxChunks + 64));
     add(2 * H);
+    (void)W;
     return ((s + 15) & ~(size_t)15) + 64;
 }
 
 // Bytes of the reusable region: the backtrack rows, later the column bitmaps of blocks of vote rows.
-size_t vpx_dyn_bytes(const KParams &kp) { return (size_t)kp.seg_rows * 2 * ((kp.W + 3) / 4); }
+size_t vpx_dyn_bytes(const KParams &kp) { return (size_t)kp.seg_rows * vpx_row_bytes(kp.W); }
 
 // Words per column the bitmaps of a block of 32 path rows need: 32 + 2 chi rows, one word of alignment.
 size_t vpx_min_dyn_bytes(const KParams &kp) { return (size_t)4 * kp.W * ((32 + 2 * kp.chi + 32 + 31) / 32 + 1); }
 
 using VpxKernel = void (*)(KParams, Work);
-VpxKernel vpx_kernel(int tau)
+template <int NP>
+VpxKernel vpx_kernel_np(int tau)
 {
     switch (tau) {
-    case 0: return k_vpx_dp<0>;
-    case 1: return k_vpx_dp<1>;
-    case 2: return k_vpx_dp<2>;
-    case 3: return k_vpx_dp<3>;
-    case 4: return k_vpx_dp<4>;
-    case 5: return k_vpx_dp<5>;
-    case 6: return k_vpx_dp<6>;
-    default: return k_vpx_dp<7>;
+    case 0: return k_vpx_dp<0, NP>;
+    case 1: return k_vpx_dp<1, NP>;
+    case 2: return k_vpx_dp<2, NP>;
+    case 3: return k_vpx_dp<3, NP>;
+    case 4: return k_vpx_dp<4, NP>;
+    case 5: return k_vpx_dp<5, NP>;
+    case 6: return k_vpx_dp<6, NP>;
+    default: return k_vpx_dp<7, NP>;
     }
 }
+VpxKernel vpx_kernel(int tau, int W) { return vpx_np(W) == 2 ? vpx_kernel_np<2>(tau) : vpx_kernel_np<1>(tau); }
 
 using RoadKernel = void (*)(KParams, Work);
 RoadKernel road_kernel(int tau) { return tau <= 6 ? k_road_dp<6> : k_road_dp<15>; }
@@ -744,7 +769,7 @@ int vpx_seg_rows(const KParams &kp, size_t budget)
     const size_t fixed = vpx_fixed_bytes(kp);
     if (budget <= fixed + vpx_min_dyn_bytes(kp))
         return 0;
-    return (int)((budget - fixed) / (2 * ((kp.W + 3) / 4)));
+    return (int)((budget - fixed) / vpx_row_bytes(kp.W));
 }
 
 cudaError_t setup_dp(int smem_optin)
@@ -752,8 +777,11 @@ cudaError_t setup_dp(int smem_optin)
     cudaError_t e = allow_max_smem(k_road_dp<6>, smem_optin);
     if (e == cudaSuccess)
         e = allow_max_smem(k_road_dp<15>, smem_optin);
-    for (int t = 0; t <= 7 && e == cudaSuccess; ++t)
-        e = allow_max_smem(vpx_kernel(t), smem_optin);
+    for (int t = 0; t <= 7 && e == cudaSuccess; ++t) {
+        e = allow_max_smem(vpx_kernel_np<1>(t), smem_optin);
+        if (e == cudaSuccess)
+            e = allow_max_smem(vpx_kernel_np<2>(t), smem_optin);
+    }
     return e;
 }
 
@@ -765,7 +793,7 @@ cudaError_t launch_road(const KParams &kp, const Work &w, cudaStream_t s)
 
 cudaError_t launch_vpx(const KParams &kp, const Work &w, cudaStream_t s)
 {
-    vpx_kernel(kp.tau_x)<<<kp.n_frames, vpx_threads(kp.W), vpx_smem_bytes(kp), s>>>(kp, w);
+    vpx_kernel(kp.tau_x, kp.W)<<<kp.n_frames, vpx_threads(kp.W), vpx_smem_bytes(kp), s>>>(kp, w);
     return cudaGetLastError();
 }
 

@@ -12,11 +12,14 @@
 // GB300 mapping of the bilateral (the cost of the whole path sits here):
 //   - taps at equal distance share ws, so w depends only on (distance class, I(i,j) - I(u,v)); the CTA
 //     builds one 768-entry uint16 table per class in shared memory and a tap costs one table load, an
-//     address add and two accumulations;
+//     address add and two 32-bit accumulations (sum(w) and sum(w 2 I) on separate pipes);
 //   - the tile stores 2 I (a byte offset into a table), so the table address is base_c + 2 I(i,j) + class
 //     offset, and sum(w 2 I) keeps the same exact arithmetic;
 //   - a thread filters 4 horizontally adjacent pixels, sharing each window row it loads as 64-bit vectors;
 //   - pixel groups that need the filter are compacted first, so warps do not diverge on the road mask.
+// Staging: the image rows of a CTA (and its disparity rows) are one contiguous range of global memory,
+// read with 16-byte loads that each thread issues before it uses any of them; the weight tables are
+// built from registers while those loads are in flight.
 //
 // Each road pixel with G_x^2 + G_y^2 > thr^2 is an edge pixel.  Its vote column is
 // floor(u + (v - V_py(v)) G_y / G_x + 0.5) in float32 (the line through the pixel perpendicular to the
@@ -30,6 +33,8 @@ namespace {
 
 constexpr int kThreads = 1024;
 constexpr int kTabBytes = kWrEntries * 2;  // one uint16 table per distance class
+constexpr int kLoadsImg = 2, kLoadsDisp = 3;  // 16-byte staging loads per thread and pass
+static_assert(kThreads >= kWrEntries, "one thread per range-weight entry builds the class tables");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -58,9 +63,7 @@ __host__ __device__ inline GradLayout grad_layout(int W, int nr)
 }
 
 // Bilateral output of the 4 pixels (br, u0 .. u0+3); tile holds 2 I with the sentinel outside the frame.
-// Per tap one 64-bit multiply-add accumulates both sums: acc += w * (2^31 + 2 I) keeps sum(w) in the bits
-// from 31 up and sum(w 2 I) < 2^31 below them.  The table address is formed modulo 2^32 from the same
-// 2^31 + 2 I operand (the base carries -2^31).
+// sum(w) <= 121 * 2^15 and sum(w 2 I) <= 121 * 2^15 * 510 < 2^31 both fit 32-bit accumulators.
 template <int RHO>
 __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t *tile, int TWP, int br, int u0, int W,
                                                uint32_t tab)
@@ -68,13 +71,13 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
     constexpr int N = 2 * RHO + 1;
     constexpr int NL = (4 + 2 * RHO + 3) / 4;
     const uint16_t *crow = tile + (size_t)(br + RHO) * TWP + u0 + RHO;
-    uint32_t base[4];
-    unsigned long long acc[4];
+    uint32_t base[4], sw[4], swi[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const uint32_t c2 = (u0 + p < W) ? crow[p] : 0u;  // pixels past the right edge: any valid index
-        base[p] = tab + 512u - c2 - 0x80000000u;
-        acc[p] = 0ull;
+        base[p] = tab + 512u - c2;
+        sw[p] = 0u;
+        swi[p] = 0u;
     }
 #pragma unroll
     for (int dy = 0; dy < N; ++dy) {
@@ -83,10 +86,10 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
             const uint2 v = rowp[l];
-            q[4 * l] = __byte_perm(v.x, 0x80000000u, 0x7410);
-            q[4 * l + 1] = __byte_perm(v.x, 0x80000000u, 0x7432);
-            q[4 * l + 2] = __byte_perm(v.y, 0x80000000u, 0x7410);
-            q[4 * l + 3] = __byte_perm(v.y, 0x80000000u, 0x7432);
+            q[4 * l] = __byte_perm(v.x, 0u, 0x4410);
+            q[4 * l + 1] = __byte_perm(v.x, 0u, 0x4432);
+            q[4 * l + 2] = __byte_perm(v.y, 0u, 0x4410);
+            q[4 * l + 3] = __byte_perm(v.y, 0u, 0x4432);
         }
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -94,15 +97,15 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
             for (int dx = 0; dx < N; ++dx) {
                 const uint32_t qq = q[p + dx];
                 const uint32_t wq = lds_u16(base[p] + qq + kp.cls_off[dy * N + dx]);
-                acc[p] += (unsigned long long)wq * qq;
+                sw[p] += wq;
+                swi[p] += wq * qq;
             }
         }
     }
     uint32_t out = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-        const uint32_t den = (uint32_t)(acc[p] >> 31), num2 = (uint32_t)acc[p] & 0x7fffffffu;
-        const uint32_t b = den ? (num2 + den) / (2u * den) : 0u;  // (2 sum(wI) + sum(w)) / (2 sum(w))
+        const uint32_t b = sw[p] ? (swi[p] + sw[p]) / (2u * sw[p]) : 0u;  // (2 sum(wI) + sum(w)) / (2 sum(w))
         out |= (b & 0xffu) << (8 * p);
     }
     return out;
@@ -145,58 +148,143 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad(const KParams kp, const Wo
     p = reinterpret_cast<unsigned char *>(((size_t)p + 15) & ~(size_t)15);
     uint16_t *tile = reinterpret_cast<uint16_t *>(p);           // [TR][TWP] 2 I, or 2 x sentinel
     p += sizeof(uint16_t) * (size_t)L.TR * L.TWP;
-    uint8_t *ibf = p;                                           // [BR][IW]; first holds the range LUT
-    int32_t *wr = reinterpret_cast<int32_t *>(p);               // [768], dead once the class tables exist
-    p += L.BR * L.IW > (int)sizeof(int32_t) * kWrEntries ? (size_t)L.BR * L.IW : sizeof(int32_t) * kWrEntries;
+    uint8_t *ibf = p;                                           // [BR][IW] bilateral output, row br = v - r0 + 1
+    p += (size_t)L.BR * L.IW;
     uint8_t *road = p;                                          // [R][IW]
     p += (size_t)R * L.IW;
     p = reinterpret_cast<unsigned char *>(((size_t)p + 15) & ~(size_t)15);
     uint16_t *glist = reinterpret_cast<uint16_t *>(p);          // [BR * NG] groups that need the filter
 
-    for (int i = tid; i < kWrEntries; i += kThreads)
-        wr[i] = w.wr[i];
+    // ---- staging.  The in-frame image rows [va, vb) and the disparity rows [r0, r0 + nr) are contiguous in
+    // global memory; each is read as 16-byte loads of the aligned chunks inside it plus single loads of
+    // its head and tail.  Every global load of this phase is issued before any is used.
+    const float *rows = w.rows + (size_t)f * 3 * H;
+    const int va = max(r0 - 1 - RHO, 0), vb = min(r0 + nr + RHO + 1, H);
+    const uint8_t *gs = img + ((size_t)f * H + va) * W;
+    const int nbytes = (vb - va) * W;
+    uint16_t *tdst = tile + (size_t)(va - (r0 - 1 - RHO)) * L.TWP + RHO;  // tile cell of pixel (va, 0)
+    const int headI = min((int)((16u - ((uint32_t)(uintptr_t)gs & 15u)) & 15u), nbytes);
+    const int nI = (nbytes - headI) >> 4, tailI = headI + 16 * nI;
+    const uint4 *bodyI = reinterpret_cast<const uint4 *>(gs + headI);
+    const float *ds = disp + ((size_t)f * H + r0) * W;
+    const int nel = nr * W;
+    const int headD = min((int)(((16u - ((uint32_t)(uintptr_t)ds & 15u)) & 15u) >> 2), nel);
+    const int nD = (nel - headD) >> 2, tailD = headD + 4 * nD;
+    const float4 *bodyD = reinterpret_cast<const float4 *>(ds + headD);
+    const int nsI = headI + nbytes - tailI, nsD = headD + nel - tailD;  // single loads (at most 30 and 6)
+    const int ooI = tid < headI ? tid : tailI + (tid - headI);
+    const int ooD = tid < headD ? tid : tailD + (tid - headD);
+
+    const uint32_t wrk = tid < kWrEntries ? (uint32_t)__ldg(w.wr + tid) : 0u;
+    const float fr = tid < nr ? __ldg(rows + r0 + tid) : 0.0f;
+    const float vyr = tid < nr ? __ldg(rows + H + r0 + tid) : 0.0f;
+    const uint32_t bI = tid < nsI ? (uint32_t)__ldg(gs + ooI) : 0u;
+    const float lD = tid < nsD ? __ldg(ds + ooD) : 0.0f;
+    uint4 xi[kLoadsImg];
+    float4 xd[kLoadsDisp];
+#pragma unroll
+    for (int k = 0; k < kLoadsImg; ++k)
+        if (k * kThreads + tid < nI)
+            xi[k] = __ldg(bodyI + k * kThreads + tid);
+#pragma unroll
+    for (int k = 0; k < kLoadsDisp; ++k)
+        if (k * kThreads + tid < nD)
+            xd[k] = __ldg(bodyD + k * kThreads + tid);
+
+    // per-class weight tables T_c[k] = (ws_c * wr[k] + 2^14) >> 15, k = q - c + 256, one thread per k
+    if (tid < kWrEntries)
+        for (int c = 0; c < kp.n_cls; ++c)
+            tabs[c * kWrEntries + tid] = (uint16_t)(((uint32_t)kp.cls_ws[c] * wrk + 16384u) >> 15);
     for (int i = tid; i < 2 * R + 4; i += kThreads)
         cnt[i] = 0;
-    const float *rows = w.rows + (size_t)f * 3 * H;
-    for (int r = tid; r < nr; r += kThreads) {
-        rowF[r] = rows[r0 + r];
-        rowVy[r] = rows[H + r0 + r];
+    if (tid < nr) {
+        // rows that hold no interior road pixel get f(v) = NaN, which fails the on-road test below
+        const int v = r0 + tid;
+        rowF[tid] = (v >= vtop && v >= 1 && v <= H - 2) ? fr : __int_as_float(0x7fc00000);
+        rowVy[tid] = vyr;
     }
-    const uint8_t *im = img + (size_t)f * H * W;
     for (int tr = warp; tr < TR; tr += NW) {
         const int v = r0 - 1 - RHO + tr;
-        const bool in = v >= 0 && v < H;
-        const uint8_t *src = im + (size_t)(in ? v : 0) * W;
         uint16_t *dst = tile + (size_t)tr * L.TWP;
-        for (int tc = lane; tc < L.TWP; tc += 32) {
-            const int u = tc - RHO;
-            dst[tc] = (in && u >= 0 && u < W) ? (uint16_t)(2u * __ldg(src + u)) : (uint16_t)(2 * kSentinel);
+        if (v < 0 || v >= H) {
+            for (int tc = lane; tc < L.TWP; tc += 32)
+                dst[tc] = (uint16_t)(2 * kSentinel);
+        } else {
+            for (int t = lane; t < L.TWP - W; t += 32)  // pad columns [0, rho) and [W + rho, TWP)
+                dst[t < RHO ? t : W + t] = (uint16_t)(2 * kSentinel);
         }
     }
-    // road mask of the interior pixels of this CTA's rows: finite l > 0 with |l - f(v)| <= varpi, v >= v_top
-    const float *dsp = disp + (size_t)f * H * W;
-    for (int r = warp; r < nr; r += NW) {
-        const int v = r0 + r;
-        const bool rowok = v >= vtop && v >= 1 && v <= H - 2;
-        const float *src = dsp + (size_t)v * W;
-        const float F = rowF[r];
-        uint8_t *dst = road + (size_t)r * L.IW;
-        for (int u = lane; u < L.IW; u += 32) {
-            uint8_t m = 0;
-            if (rowok && u >= 1 && u <= W - 2) {
-                const float l = __ldg(src + u);
-                m = l > 0.0f && l < __int_as_float(0x7f800000) && fabsf(__fsub_rn(l, F)) <= kp.varpi;
+    for (int i = tid; i < nr * (L.IW - W); i += kThreads) {
+        const int r = i / (L.IW - W);
+        road[(size_t)r * L.IW + W + (i - r * (L.IW - W))] = 0;
+    }
+    __syncthreads();  // rowF
+
+    // road mask of the interior pixels: l > 0 with |l - f(v)| <= varpi (an infinite or NaN l fails the
+    // second test because f(v) is finite), v >= v_top, 1 <= u <= W-2
+    auto mask = [&](int row, int col, float l) {
+        const bool m = l > 0.0f && fabsf(__fsub_rn(l, rowF[row])) <= kp.varpi && col >= 1 && col <= W - 2;
+        road[(size_t)row * L.IW + col] = (uint8_t)m;
+    };
+    if (tid < nsI) {
+        const int row = ooI / W;
+        tdst[row * L.TWP + ooI - row * W] = (uint16_t)(2u * bI);
+    }
+    if (tid < nsD) {
+        const int row = ooD / W;
+        mask(row, ooD - row * W, lD);
+    }
+    for (int pass = 0; pass * kLoadsImg * kThreads < nI || pass * kLoadsDisp * kThreads < nD; ++pass) {
+        if (pass > 0) {
+#pragma unroll
+            for (int k = 0; k < kLoadsImg; ++k) {
+                const int i = (pass * kLoadsImg + k) * kThreads + tid;
+                if (i < nI)
+                    xi[k] = __ldg(bodyI + i);
             }
-            dst[u] = m;
+#pragma unroll
+            for (int k = 0; k < kLoadsDisp; ++k) {
+                const int i = (pass * kLoadsDisp + k) * kThreads + tid;
+                if (i < nD)
+                    xd[k] = __ldg(bodyD + i);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kLoadsImg; ++k) {
+            const int i = (pass * kLoadsImg + k) * kThreads + tid;
+            if (i < nI) {
+                const uint32_t wv[4] = {xi[k].x, xi[k].y, xi[k].z, xi[k].w};
+                const int off = headI + 16 * i;
+                int row = off / W, col = off - row * W;
+#pragma unroll
+                for (int b = 0; b < 16; ++b) {
+                    tdst[row * L.TWP + col] = (uint16_t)(2u * ((wv[b >> 2] >> (8 * (b & 3))) & 0xffu));
+                    if (++col == W) {
+                        col = 0;
+                        ++row;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kLoadsDisp; ++k) {
+            const int i = (pass * kLoadsDisp + k) * kThreads + tid;
+            if (i < nD) {
+                const float xv[4] = {xd[k].x, xd[k].y, xd[k].z, xd[k].w};
+                const int off = headD + 4 * i;
+                int row = off / W, col = off - row * W;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    mask(row, col, xv[b]);
+                    if (++col == W) {
+                        col = 0;
+                        ++row;
+                    }
+                }
+            }
         }
     }
     __syncthreads();
-    // per-class weight tables: T_c[k] = (ws_c * wr[k] + 2^14) >> 15, k = q - c + 256
-    for (int c = 0; c < kp.n_cls; ++c) {
-        const uint32_t wsc = kp.cls_ws[c];
-        for (int k = tid; k < kWrEntries; k += kThreads)
-            tabs[c * kWrEntries + k] = (uint16_t)((wsc * (uint32_t)wr[k] + 16384u) >> 15);
-    }
     // groups of 4 pixels of the bilateral rows (r0-1 .. r0+nr) holding a pixel the Sobel stencil reads
     for (int br = warp; br < BR; br += NW) {
         for (int j0 = 0; j0 < L.NG; j0 += 32) {
@@ -246,18 +334,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad(const KParams kp, const Wo
     const int thr2 = kp.edge_thresh2;
     int16_t *edges = w.edges + (size_t)f * H * W * 4;
     int16_t *vbins = w.vbins + (size_t)f * H * W;
-    for (int r = warp; r < nr; r += NW) {
+    // one thread per group of 4 pixels: 32-bit loads of the mask and of the three bilateral rows
+    for (int k = tid; k < nr * L.NG; k += kThreads) {
+        const int r = k / L.NG, j = k - r * L.NG;
+        const uint32_t m4 = reinterpret_cast<const uint32_t *>(road + (size_t)r * L.IW)[j];
+        if (!m4)
+            continue;
         const int v = r0 + r;
-        const uint8_t *rm = road + (size_t)r * L.IW;
-        const uint8_t *a = ibf + (size_t)r * L.IW;      // row v-1
-        const uint8_t *b = a + L.IW;                      // row v
-        const uint8_t *cc = b + L.IW;                     // row v+1
+        uint32_t x0[3], x1[3], x2[3];  // bytes 4j-4 .. 4j-1, 4j .. 4j+3, 4j+4 .. 4j+7 of rows v-1, v, v+1
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const uint32_t *rw = reinterpret_cast<const uint32_t *>(ibf + (size_t)(r + d) * L.IW);
+            x0[d] = j > 0 ? rw[j - 1] : 0u;
+            x1[d] = rw[j];
+            x2[d] = j + 1 < L.NG ? rw[j + 1] : 0u;
+        }
         const float vy = rowVy[r];
-        for (int u = lane; u < W; u += 32) {
-            if (!rm[u])
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            if (!((m4 >> (8 * p)) & 0xffu))
                 continue;
-            const int gx = ((int)a[u + 1] - (int)a[u - 1]) + 2 * ((int)b[u + 1] - (int)b[u - 1]) + ((int)cc[u + 1] - (int)cc[u - 1]);
-            const int gy = ((int)cc[u - 1] - (int)a[u - 1]) + 2 * ((int)cc[u] - (int)a[u]) + ((int)cc[u + 1] - (int)a[u + 1]);
+            const int u = 4 * j + p;
+            int lf[3], cn[3], rt[3];  // I(u-1), I(u), I(u+1) of rows v-1, v, v+1
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                lf[d] = p == 0 ? (int)(x0[d] >> 24) : (int)((x1[d] >> (8 * (p - 1))) & 0xffu);
+                cn[d] = (int)((x1[d] >> (8 * p)) & 0xffu);
+                rt[d] = p == 3 ? (int)(x2[d] & 0xffu) : (int)((x1[d] >> (8 * (p + 1))) & 0xffu);
+            }
+            const int gx = (rt[0] - lf[0]) + 2 * (rt[1] - lf[1]) + (rt[2] - lf[2]);
+            const int gy = (lf[2] - lf[0]) + 2 * (cn[2] - cn[0]) + (rt[2] - rt[0]);
             if (gx * gx + gy * gy <= thr2)
                 continue;
             int bin = -1;
@@ -292,14 +398,13 @@ size_t grad_smem(int W, int R, int n_cls)
     const GradLayout L = grad_layout<RHO>(W, R);
     size_t s = (size_t)kTabBytes * n_cls + sizeof(int32_t) * (2 * R + 4) + 2 * sizeof(float) * R;
     s = (s + 15) & ~(size_t)15;
-    const size_t ibf = (size_t)L.BR * L.IW > sizeof(int32_t) * kWrEntries ? (size_t)L.BR * L.IW : sizeof(int32_t) * kWrEntries;
-    s += sizeof(uint16_t) * (size_t)L.TR * L.TWP + ibf + (size_t)R * L.IW;
+    s += sizeof(uint16_t) * (size_t)L.TR * L.TWP + (size_t)L.BR * L.IW + (size_t)R * L.IW;
     s = (s + 15) & ~(size_t)15;
     s += sizeof(uint16_t) * (size_t)L.BR * L.NG;
     return s + 16;
 }
 
-// Rows per CTA: the most that let two CTAs share an SM, else the most that fit one CTA.
+// Rows per CTA: the most whose shared memory stays within 200 KB (one 1024-thread CTA per SM).
 template <int RHO>
 int grad_rows(int W, int n_cls)
 {

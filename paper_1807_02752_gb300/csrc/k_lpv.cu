@@ -1,7 +1,8 @@
 // Sec. 2.4, lane position validation (Alg. 7):
 //
 //   k_m1      w_g of every road edge pixel (Eq. 23), M_0 = (2 nu + 1) x (2 varsigma + 1) box sum of
-//             G_x w_g, M_1 = G * M_0 with G = [1,2,1]^T [1,0,-1] (a convolution: M_0(u+1) - M_0(u-1)).
+//             G_x w_g, M_1 = G * M_0 with G = [1,2,1]^T [1,0,-1] (a convolution: M_0(u+1) - M_0(u-1)),
+//             evaluated through the horizontal difference D of M_0 (below).
 //   k_energy  for every start s in [-floor(xi W), W + floor(xi W)) the track of Eq. 25 from the bottom
 //             row up to v_top and its energy E = M_1(round(u_v), v) + lambda_g E (Eq. 24).
 //   k_select  strict interior local minima of H below t = ceil(thr min H), then suppression of nearby
@@ -18,12 +19,41 @@ namespace ld {
 namespace {
 
 constexpr int kM1Threads = 512;
-constexpr int kEnThreads = 256;
+constexpr int kEnThreads = 128;
+constexpr int kEnBatch = 16;   // track rows whose M_1 loads are in flight together
 constexpr int kSelThreads = 256;
 
-__global__ void __launch_bounds__(kM1Threads) k_m1(const KParams kp, const Work w, int R)
+// k_m1 works on D(u, v) = M_0(u+1, v) - M_0(u-1, v).  An edge pixel at (u_e, v_e) adds g = G_x w_g to the
+// (2 nu + 1)-box sums T(x, v_e) for x in [u_e - nu, u_e + nu], so on the interior columns
+// D = T(x+1) - T(x-1) telescopes to +g at u_e - nu - 1 and u_e - nu, -g at u_e + nu and u_e + nu + 1
+// (4 shared-memory atomics per edge instead of (2 nu + 1)(2 varsigma + 1)); M_0 is zero outside the
+// frame, so column 0 holds T(1) and column W-1 holds -T(W-2).  M_1(u, v) = X(v-1) + 2 X(v) + X(v+1) with
+// X(g) = sum_{|y| <= varsigma} D(u, g + y) on rows g inside the frame (0 outside), which a thread per
+// column evaluates as a sliding sum.  All integer: the result does not depend on the order of the adds.
+constexpr int kM1MaxEdgeRows = 64;
+
+struct M1Layout {
+    int R, Wc;  // M_1 rows per CTA, columns of D per shared-memory chunk
+};
+
+inline M1Layout m1_layout(int W, int vs)
 {
-    extern __shared__ __align__(16) int32_t m0[];   // [R + 2][W]: M_0 rows r0-1 .. r0+R
+    const size_t budget = 110 * 1024;  // two CTAs per SM
+    M1Layout L;
+    for (L.R = 16; L.R >= 8; --L.R)
+        if ((size_t)(L.R + 2 + 2 * vs) * W * sizeof(int32_t) <= budget) {
+            L.Wc = W;
+            return L;
+        }
+    L.R = 16;
+    L.Wc = (int)(budget / ((size_t)(L.R + 2 + 2 * vs) * sizeof(int32_t))) & ~31;
+    return L;
+}
+
+__global__ void __launch_bounds__(kM1Threads, 2) k_m1(const KParams kp, const Work w, int R, int Wc)
+{
+    extern __shared__ __align__(16) int32_t dd[];   // [nr + 2 + 2 varsigma][Wc]: rows r0-1-varsigma ..
+    __shared__ int32_t eoff[kM1MaxEdgeRows + 1];
     const int W = kp.W, H = kp.H;
     const int f = blockIdx.y;
     const int r0 = blockIdx.x * R;
@@ -32,22 +62,55 @@ __global__ void __launch_bounds__(kM1Threads) k_m1(const KParams kp, const Work 
     const int vtop = fs.v_top, vmax = H - 1;
     if ((fs.flags & LD_F_NO_LANES) || r0 + nr - 1 < vtop)
         return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int nu = kp.box_nu, vs = kp.box_vs;
-    for (int i = tid; i < (nr + 2) * W; i += kM1Threads)
-        m0[i] = 0;
-    __syncthreads();
+    const int d0 = r0 - 1 - vs;                      // frame row of D row 0
+    const int ndr = nr + 2 + 2 * vs;
+    // edge rows that reach the M_0 rows r0-1 .. r0+nr, and the prefix of their edge counts
+    const int elo = max(vtop, d0), ehi = min(vmax, r0 + nr + vs);
+    const int ner = max(0, ehi - elo + 1);           // <= kM1MaxEdgeRows (R <= 16, varsigma <= 8)
+    if (tid < 32) {
+        const int32_t *ec = w.ecount + (size_t)f * H + elo;
+        const int a = 2 * lane < ner ? ec[2 * lane] : 0;
+        const int b = 2 * lane + 1 < ner ? ec[2 * lane + 1] : 0;
+        int s = a + b;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, s, d);
+            if (lane >= d)
+                s += t;
+        }
+        eoff[2 * lane] = s - a - b;
+        eoff[2 * lane + 1] = s - b;
+        if (lane == 31)
+            eoff[kM1MaxEdgeRows] = s;
+    }
     const float *Vpy = w.rows + (size_t)f * 3 * H + H;
     const float *Vpx = Vpy + H;
-    // scatter G_x w_g of the edge pixels of rows [r0-1-vs, r0+nr+vs] into the M_0 rows they reach
-    const int elo = max(vtop, r0 - 1 - vs), ehi = min(vmax, r0 + nr + vs);
-    for (int v = elo + warp; v <= ehi; v += kM1Threads / 32) {
-        const int cnt = w.ecount[(size_t)f * H + v];
-        const short4 *src = reinterpret_cast<const short4 *>(w.edges + ((size_t)f * H + v) * W * 4);
-        const float vx = Vpx[v], vy = Vpy[v];
-        for (int q = lane; q < cnt; q += 32) {
-            const short4 e = src[q];
+    int32_t *M1 = w.M1 + (size_t)f * H * W;
+    const int rs = max(r0, vtop);
+    for (int c0 = 0; c0 < W; c0 += Wc) {
+        const int c1 = min(W, c0 + Wc), cw = c1 - c0;
+        for (int i = tid; i < ndr * cw; i += kM1Threads)
+            dd[i] = 0;
+        __syncthreads();
+        const int total = eoff[ner];
+        for (int q = tid; q < total; q += kM1Threads) {
+            int lo = 0, hi = ner;  // eoff[lo] <= q < eoff[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (eoff[mid] <= q)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const int v = elo + lo;
+            const short4 e = reinterpret_cast<const short4 *>(w.edges + ((size_t)f * H + v) * W * 4)[q - eoff[lo]];
             const int u = e.x, gx = e.z, gy = e.w;
+            if (u + nu + 1 < c0 || u - nu - 1 >= c1)
+                if (!(c0 == 0 && abs(u - 1) <= nu) && !(c1 == W && abs(u - (W - 2)) <= nu))
+                    continue;
+            const float vx = Vpx[v], vy = Vpy[v];
             const float tu = (float)(-gy), tv = (float)gx;
             const float ru = __fsub_rn(vx, (float)u), rv = __fsub_rn(vy, (float)v);
             const float cr = __fsub_rn(__fmul_rn(tu, rv), __fmul_rn(tv, ru));
@@ -60,41 +123,46 @@ __global__ void __launch_bounds__(kM1Threads) k_m1(const KParams kp, const Work 
                 if (s <= 0.25f)
                     wg = __ldg(w.wg + (int)__fmul_rn(__fsqrt_rn(s), 32768.0f));
             }
-            const int gw = gx * wg;
-            if (gw == 0)
+            const int g = gx * wg;
+            if (g == 0)
                 continue;
-            for (int y = -vs; y <= vs; ++y) {
-                const int rr = v + y - (r0 - 1);
-                if (rr < 0 || rr >= nr + 2 || v + y < 0 || v + y > vmax)
-                    continue;
-                for (int x = -nu; x <= nu; ++x) {
-                    const int uu = u + x;
-                    if (uu >= 0 && uu < W)
-                        atomicAdd(&m0[rr * W + uu], gw);
-                }
+            int32_t *drow = dd + (size_t)(v - d0) * cw;  // column t of the frame at drow[t - c0]
+            const int tgt[4] = {u - nu - 1, u - nu, u + nu, u + nu + 1};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int t = tgt[k];
+                if (t >= 1 && t <= W - 2 && t >= c0 && t < c1)
+                    atomicAdd(drow + (t - c0), k < 2 ? g : -g);
+            }
+            if (c0 == 0 && abs(u - 1) <= nu)
+                atomicAdd(drow, g);
+            if (c1 == W && abs(u - (W - 2)) <= nu)
+                atomicAdd(drow + (W - 1 - c0), -g);
+        }
+        __syncthreads();
+        for (int u = c0 + tid; u < c1; u += kM1Threads) {
+            const int32_t *col = dd + (u - c0);
+            int box = 0;  // sum of D over the rows of M_0 row r0 - 1 (D rows 0 .. 2 varsigma)
+            for (int i = 0; i <= 2 * vs; ++i)
+                box += col[(size_t)i * cw];
+            int xp = r0 - 1 >= 0 ? box : 0;
+            box += col[(size_t)(2 * vs + 1) * cw] - col[0];
+            int xc = box;  // M_0 row r0 (inside the frame)
+            for (int r = 0; r < nr; ++r) {
+                const int g = r0 + r;
+                box += col[(size_t)(r + 2 + 2 * vs) * cw] - col[(size_t)(r + 1) * cw];  // M_0 row g + 1
+                const int xn = g + 1 <= vmax ? box : 0;
+                if (g >= rs)
+                    M1[(size_t)g * W + u] = xp + 2 * xc + xn;
+                xp = xc;
+                xc = xn;
             }
         }
-    }
-    __syncthreads();
-    // M_1 rows r0 .. r0+nr-1 (>= v_top): sum_dv (1,2,1)[dv] (M_0(u+1, v+dv) - M_0(u-1, v+dv))
-    int32_t *M1 = w.M1 + (size_t)f * H * W;
-    const int rstart = max(r0, vtop);
-    for (int i = (rstart - r0) * W + tid; i < nr * W; i += kM1Threads) {
-        const int r = i / W, u = i - r * W;
-        const int32_t *a = m0 + (size_t)r * W;   // M_0 row v-1
-        int s = 0;
-#pragma unroll
-        for (int dv = 0; dv < 3; ++dv) {
-            const int32_t *row = a + dv * W;
-            const int rgt = u + 1 < W ? row[u + 1] : 0;
-            const int lft = u >= 1 ? row[u - 1] : 0;
-            s += (dv == 1 ? 2 : 1) * (rgt - lft);
-        }
-        M1[(size_t)(r0 + r) * W + u] = s;
+        __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kEnThreads) k_energy(const KParams kp, const Work w)
+__global__ void __launch_bounds__(kEnThreads, 8) k_energy(const KParams kp, const Work w)
 {
     extern __shared__ float vrow[];   // [2][H]: V_px, V_py
     const int W = kp.W, H = kp.H;
@@ -114,21 +182,35 @@ __global__ void __launch_bounds__(kEnThreads) k_energy(const KParams kp, const W
         return;
     const int32_t *M1 = w.M1 + (size_t)f * H * W;
     const float fW = (float)W;
-    const long long lam = kp.lambda_g;
+    const bool lam = kp.lambda_g != 0;  // lambda_g is 0 or 1
+    // the track recursion does not depend on M_1: kEnBatch rows of track columns are computed and their
+    // M_1 loads issued before the energy recursion consumes them, so loads overlap instead of chaining
     float u = (float)(i - kp.S0);
     long long E = 0;
-    for (int v = vmax; v >= vtop; --v) {
-        if (v < vmax) {
-            const float vx = vrow[v + 1], vy = vrow[H + v + 1];
-            const float num = __fsub_rn(__fadd_rn(vx, __fmul_rn((float)v, u)), __fmul_rn(vy, u));
-            const float den = __fsub_rn((float)(v + 1), vy);
-            u = __fdiv_rn(num, den);
+    for (int v0 = vmax; v0 >= vtop; v0 -= kEnBatch) {
+        int32_t m[kEnBatch];
+        float fv = (float)v0;  // (float)v, exact (v < 2^24)
+#pragma unroll
+        for (int b = 0; b < kEnBatch; ++b) {
+            const int v = v0 - b;
+            m[b] = 0;
+            if (v >= vtop) {
+                if (v < vmax) {
+                    const float vx = vrow[v + 1], vy = vrow[H + v + 1];
+                    const float num = __fsub_rn(__fadd_rn(vx, __fmul_rn(fv, u)), __fmul_rn(vy, u));
+                    const float den = __fsub_rn(__fadd_rn(fv, 1.0f), vy);
+                    u = __fdiv_rn(num, den);
+                }
+                const float col = floorf(__fadd_rn(u, 0.5f));
+                if (col >= 0.0f && col < fW)
+                    m[b] = __ldg(M1 + (size_t)v * W + (int)col);
+            }
+            fv = __fsub_rn(fv, 1.0f);
         }
-        const float col = floorf(__fadd_rn(u, 0.5f));
-        long long m = 0;
-        if (col >= 0.0f && col < fW)
-            m = __ldg(M1 + (size_t)v * W + (int)col);
-        E = m + lam * E;
+#pragma unroll
+        for (int b = 0; b < kEnBatch; ++b)
+            if (v0 - b >= vtop)
+                E = (long long)m[b] + (lam ? E : 0ll);
     }
     w.HE[(size_t)f * kp.n_starts + i] = (int64_t)E;
 }
@@ -250,20 +332,12 @@ cudaError_t setup_lpv(int smem_optin)
     return e;
 }
 
-int m1_rows(int W)
-{
-    int R = 16;
-    while (R > 1 && sizeof(int32_t) * (size_t)(R + 2) * W > 160 * 1024)
-        --R;
-    return R;
-}
-
 cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s)
 {
-    const int R = m1_rows(kp.W);
-    const size_t smem = sizeof(int32_t) * (size_t)(R + 2) * kp.W;
-    dim3 grid((kp.H + R - 1) / R, kp.n_frames);
-    k_m1<<<grid, kM1Threads, smem, s>>>(kp, w, R);
+    const M1Layout L = m1_layout(kp.W, kp.box_vs);
+    const size_t smem = sizeof(int32_t) * (size_t)(L.R + 2 + 2 * kp.box_vs) * L.Wc;
+    dim3 grid((kp.H + L.R - 1) / L.R, kp.n_frames);
+    k_m1<<<grid, kM1Threads, smem, s>>>(kp, w, L.R, L.Wc);
     return cudaGetLastError();
 }
 

@@ -3,12 +3,14 @@
 // A pixel counts when its disparity l is finite and > 0 (0 marks pixels invalidated by the left-right
 // check, Eq. 10); its bin is floor(l + 0.5) in float32 and bins >= D are dropped.
 //
-// One CTA covers kRows consecutive rows of one frame.  Those rows are contiguous in memory, so the CTA
-// streams them as one flat range (coalesced 128-byte warp loads, several loads in flight per thread).
-// Counts go to a shared-memory histogram per row with warp-aggregated atomics: lanes holding the same
-// (row, bin) key elect one leader that adds the group's size.  On road rows most pixels of a warp share
-// one bin, so this turns up to 32 conflicting atomics into one.  The histogram is written transposed,
-// [D][H] per frame, so that each step of the road DP (Eq. 12) reads one contiguous row.
+// One CTA covers kRows consecutive rows of one frame.  Those rows are one contiguous range of memory, so
+// the CTA streams it as 16-byte loads of the aligned chunks inside it (several in flight per thread) plus
+// single loads of its head and tail; each warp streams one contiguous span.  Counts go to a shared-memory
+// histogram per row.  Disparity is locally smooth (a road row holds one or two bins, an obstacle one), so
+// each thread keeps a run of equal (row, bin) keys in registers and adds the run with one shared-memory
+// atomic when the key changes: far fewer atomics than pixels, and no 32-way conflicts on the dominant
+// bin.  The histogram is written transposed, [D][H] per frame, so that each step of the road DP (Eq. 12)
+// reads one contiguous row.
 #include "ld_internal.cuh"
 
 namespace ld {
@@ -16,7 +18,7 @@ namespace ld {
 namespace {
 constexpr int kRows = 8;
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
+constexpr int kUnroll = 4;  // 16-byte loads in flight per thread
 
 __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *__restrict__ myT,
                                                     const float *__restrict__ disp)
@@ -26,38 +28,76 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
     const int f = blockIdx.y;
     const int r0 = blockIdx.x * kRows;
     const int nr = min(kRows, H - r0);
-    for (int i = threadIdx.x; i < kRows * D; i += kThreads)
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kRows * D; i += kThreads)
         hist[i] = 0;
     __syncthreads();
 
     const float *src = disp + ((size_t)f * H + r0) * W;
     const int n = nr * W;
-    const float fD = (float)D;
-    for (int base = 0; base < n; base += kThreads * kUnroll) {
-        float val[kUnroll];
+    // bin of a pixel: floor(l + 0.5) when l > 0 and the bin is below D, else -1.  A NaN fails l > 0, and
+    // +inf (or any l past the last bin) converts to a value >= D, so one compare covers finiteness too.
+    auto bin_of = [&](float l) {
+        const int b = __float2int_rd(__fadd_rn(l, 0.5f));
+        return (l > 0.0f && b < D) ? b : -1;
+    };
+    const int head = min((int)(((16u - ((uint32_t)(uintptr_t)src & 15u)) & 15u) >> 2), n);
+    const int nb = (n - head) >> 2, tail0 = head + 4 * nb;
+    if (tid < head + n - tail0) {
+        const int off = tid < head ? tid : tail0 + (tid - head);
+        const int b = bin_of(__ldg(src + off));
+        if (b >= 0)
+            atomicAdd(&hist[(off / W) * D + b], 1);
+    }
+    // each warp takes one contiguous span of the 16-byte chunks (about one row), so a lane's successive
+    // loads (128 pixels apart) mostly stay in one row and its run key changes only with the bin
+    const float4 *body = reinterpret_cast<const float4 *>(src + head);
+    constexpr int kWarps = kThreads / 32;
+    const int lane = tid & 31, span = (nb + kWarps - 1) / kWarps;
+    const int w0 = (tid >> 5) * span, w1 = min(nb, w0 + span);
+    // row and column of the lane's first pixel, then advanced by 128 pixels per step (no division)
+    int off0 = head + 4 * (w0 + lane);
+    int row = off0 / W, col = off0 - row * W;
+    int run_key = -1, run_cnt = 0;
+    for (int base = w0; base < w1; base += 32 * kUnroll) {
+        float4 x[kUnroll];
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
-            const int i = base + k * kThreads + threadIdx.x;
-            val[k] = i < n ? __ldg(src + i) : 0.0f;
+            const int i = base + 32 * k + lane;
+            if (i < w1)
+                x[k] = __ldg(body + i);
         }
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
-            const int i = base + k * kThreads + threadIdx.x;
-            int key = -1;
-            const float l = val[k];
-            if (i < n && l > 0.0f && l < __int_as_float(0x7f800000)) {
-                const float b = floorf(__fadd_rn(l, 0.5f));
-                if (b < fD)
-                    key = (i / W) * D + (int)b;
+            const int i = base + 32 * k + lane;
+            if (i < w1) {
+                const float l[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
+                const int rb = row * D;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int b = bin_of(l[e]);
+                    const int key = b < 0 ? -1 : (col + e < W ? rb : rb + D) + b;
+                    if (key >= 0 && key != run_key) {
+                        if (run_cnt)
+                            atomicAdd(&hist[run_key], run_cnt);
+                        run_key = key;
+                        run_cnt = 0;
+                    }
+                    run_cnt += key >= 0;
+                }
             }
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
-            if (key >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1)
-                atomicAdd(&hist[key], __popc(peers));
+            col += 128;
+            while (col >= W) {
+                col -= W;
+                ++row;
+            }
         }
     }
+    if (run_cnt)
+        atomicAdd(&hist[run_key], run_cnt);
     __syncthreads();
     int32_t *dst = myT + (size_t)f * D * H;
-    for (int i = threadIdx.x; i < D * nr; i += kThreads) {
+    for (int i = tid; i < D * nr; i += kThreads) {
         const int d = i / nr, r = i - d * nr;
         dst[(size_t)d * H + r0 + r] = hist[r * D + d];
     }

@@ -332,7 +332,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     }
     build_tables(h->p, h->ws_q, nullptr, nullptr);
 
-    // backtrack rows that fit for the largest frame decide the number of DP checkpoints
+    // the V_px DP needs shared memory for a block of backtrack rows and the vote bitmaps of the largest frame
     ld::KParams kmax = make_kparams(h, max_w, max_h, max_batch);
     if (kmax.seg_rows < 1 || ld::road_smem_bytes(kmax) > (size_t)h->smem_optin - 1024) {
         delete h;
@@ -347,7 +347,6 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     }
     const size_t n = max_batch, W = max_w, H = max_h, D = p->n_disp;
     const size_t pmax = D > H ? D : H;
-    const int max_seg = (int)((H - 1 + kmax.seg_rows - 1) / kmax.seg_rows) + 1;
     const size_t n_starts = (size_t)ld_n_starts(p, max_w);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -358,7 +357,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     const size_t o_my = take(n * D * H * 4), o_fs = take(n * sizeof(ld::FrameState)), o_rows = take(n * 3 * H * 4);
     const size_t o_py = take(n * D * 2), o_iy = take(n * D), o_ec = take(n * H * 4), o_ed = take(n * H * W * 8);
     const size_t o_vc = take(n * H * 4), o_vb = take(n * H * W * 2), o_px = take(n * H * 2), o_ix = take(n * H);
-    const size_t o_ck = take(n * max_seg * 2 * W * 4), o_m1 = take(n * H * W * 4), o_he = take(n * n_starts * 8);
+    const size_t o_bt = take(n * H * (size_t)ld::vpx_row_bytes(max_w)), o_m1 = take(n * H * W * 4), o_he = take(n * n_starts * 8);
     const size_t o_pts = take(n * 2 * 3 * pmax * 2), o_np = take(n * 2 * 4);
     const size_t o_tab = take(sizeof(int32_t) * (ld::kWrEntries + ld::kWgEntries));
     const size_t o_d = take(n * H * W * 4), o_i = take(n * H * W), o_l = take(n * sizeof(ld_lanes));
@@ -381,7 +380,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     w.vbins = (int16_t *)(b + o_vb);
     w.path_x = (int16_t *)(b + o_px);
     w.inl_x = (uint8_t *)(b + o_ix);
-    w.ckpt = (int32_t *)(b + o_ck);
+    w.gbt = (uint8_t *)(b + o_bt);
     w.M1 = (int32_t *)(b + o_m1);
     w.HE = (int64_t *)(b + o_he);
     w.pts = (int16_t *)(b + o_pts);
@@ -392,7 +391,6 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     w.wg = h->d_tables + ld::kWrEntries;
     w.max_w = max_w;
     w.max_h = max_h;
-    w.max_seg = max_seg;
     h->d_disp = (float *)(b + o_d);
     h->d_img = (uint8_t *)(b + o_i);
     h->d_lanes = (ld_lanes *)(b + o_l);

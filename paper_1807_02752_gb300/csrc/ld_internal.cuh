@@ -67,12 +67,12 @@ struct Work {
     uint8_t *inl_x;      // [n][H]
     int16_t *pts;        // [n][2][3][pmax] DP path points with data (x, y, index) for the beta / gamma fits
     int32_t *npts;       // [n][2]
-    int32_t *ckpt;       // [n][max_seg][2][W] DP checkpoints (E row, band row)
+    uint8_t *gbt;        // [n][max_h][vpx_row_bytes(max_w)] V_px backtrack rows below the shared-memory block
     int32_t *M1;         // [n][H][W]
     int64_t *HE;         // [n][n_starts]
     const int32_t *wr;   // [kWrEntries] Q15
     const int32_t *wg;   // [kWgEntries] Q12
-    int32_t max_w, max_h, max_seg, pmax;
+    int32_t max_w, max_h, pmax;
 };
 
 // ---------------------------------------------------------------------------------------------------
@@ -102,6 +102,10 @@ __device__ __forceinline__ double i128_to_f64(__int128 x)
     const unsigned int r = (unsigned int)(x & (__int128)0xffffffffu);
     return __dadd_rn(__dmul_rn((double)q, 4294967296.0), (double)r);
 }
+
+// Bytes of one V_px backtrack row: one byte per pair of cells (two 4-bit entries), padded to 16 bytes.
+__host__ __device__ inline int vpx_pairs(int W) { return (W + 1) >> 1; }
+__host__ __device__ inline int vpx_row_bytes(int W) { return (vpx_pairs(W) + 15) & ~15; }
 
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
 

@@ -108,11 +108,24 @@ def test_param_variants(torch_cuda):
     disp, img, _ = scenes.make_batch(cfg, 3, first_frame=11)
     for kw in ({"bilateral": 0}, {"bf_rho": 3, "sigma_r": 0.2}, {"ransac_hyps": 1}, {"ransac_hyps": 256, "seed": 7},
                {"chi": 5, "tau_x": 7, "lambda_x": 3}, {"thr_den": 4, "near_px": 5, "max_lanes": 2},
-               {"ransac_rounds": 1}):
+               {"ransac_rounds": 1}, {"box_nu": 0, "box_vs": 0}, {"box_nu": 3, "box_vs": 8},
+               {"box_nu": 8, "box_vs": 1}):
         p = ld.default_params(n_disp=cfg.n_disp, **kw)
         det = ld.Detector(cfg.width, cfg.height, 3, p)
         res = _run(torch_cuda, det, disp, img)
         for f in range(3):
+            compare_frame(det, res[f], f, disp[f], img[f], p)
+
+
+def test_wide_frames_chunked_m1(torch_cuda):
+    """Frames too wide for one shared-memory chunk of the M_1 kernel (the column-chunked layout)."""
+    cfg = scenes.with_size(scenes.SMALL_320x120, width=3000, height=96, n_disp=64)
+    disp, img, _ = scenes.make_batch(cfg, 2, first_frame=3)
+    for kw in ({}, {"box_nu": 2, "box_vs": 8}):
+        p = ld.default_params(n_disp=cfg.n_disp, **kw)
+        det = ld.Detector(cfg.width, cfg.height, 2, p)
+        res = _run(torch_cuda, det, disp, img)
+        for f in range(2):
             compare_frame(det, res[f], f, disp[f], img[f], p)
 
 
