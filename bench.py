@@ -132,6 +132,26 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------------------------------
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, or None when the
+    summary is missing or was taken on another version of the kernel source (its sha256 is recorded)."""
+    import hashlib
+    import re
+
+    md = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    src = os.path.join(ROOT, "paper_1807_02752_gb300", "csrc", f"{kernel}.cu")
+    if not (os.path.exists(md) and os.path.exists(src)):
+        return None
+    text = open(md).read()
+    sha = re.search(r"sha256 ([0-9a-f]{64})", text)
+    val = re.search(r"dram_bytes_per_launch: (\d+)", text)
+    if not sha or not val:
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != sha.group(1):
+        return None
+    return int(val.group(1))
+
+
 def bilateral_pixels(det, disp, W, H, n):
     """Pixels whose bilateral output the path needs: 3x3 dilation of the interior road pixels."""
     from paper_1807_02752_gb300 import ld
@@ -157,7 +177,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1807_02752_gb300 import ld, scenes
+    from paper_1807_02752_gb300 import ld, replicas, scenes
     from paper_1807_02752_gb300 import build as ldbuild
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -178,9 +198,16 @@ def run_ours(args):
     cfg, n = scenes.WORKLOADS[WORKLOAD]
     W, H = cfg.width, cfg.height
     # two input batches (frames of this rank), alternated so the inputs (2 x 149 MB) exceed the 129 MB L2
-    base = rank * 2 * n
-    d0, i0, _ = scenes.make_batch(cfg, n, first_frame=base)
-    d1, i1, _ = scenes.make_batch(cfg, n, first_frame=base + n)
+    # this rank's frames: its round-robin share of a sequence of world x 2 batches (replicas, no collective)
+    mine = replicas.frames_of_rank(world * 2 * n, rank, world)
+
+    def batch(frames):
+        fr = [scenes.make_frame(cfg, k) for k in frames]
+        return np.stack([x[0] for x in fr]), np.stack([x[1] for x in fr])
+
+    d0, i0 = batch(mine[:n])
+    d1, i1 = batch(mine[n:])
+    base = mine[0]
     disp = [torch.from_numpy(d0).cuda(), torch.from_numpy(d1).cuda()]
     img = [torch.from_numpy(i0).cuda(), torch.from_numpy(i1).cuda()]
     p = ld.default_params(n_disp=cfg.n_disp)
@@ -227,10 +254,7 @@ def run_ours(args):
         dist.barrier()
     total_ms = ev0.elapsed_time(ev1)
     step_ms = np.array([ev_start[s].elapsed_time(ev_end[s]) for s in range(args.steps)])
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(total_ms)
     clk = clocks.summary(t_wall0, t_wall1) if clocks else None
 
     # per-kernel durations: eager launches with an event around every kernel, same stream
@@ -274,10 +298,7 @@ def run_ours(args):
     for th in ths:
         th.join()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = replicas.max_over_ranks(e2e_s)
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -293,7 +314,7 @@ def run_ours(args):
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # INT32 lanes x SMs x clock
         roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom_name,
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(dom_name, WORKLOAD), "kernel": dom_name,
                 "units_per_launch": {"bilateral_pixels": npx, "taps_per_pixel": taps, "int_ops_per_tap": INT_OPS_PER_TAP},
                 "peak_source": f"152 SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz ({peak_src} clock)"}
     else:

@@ -12,6 +12,8 @@
 // the direction from the pixel to V_p(v); lines are undirected, so the angle is taken in [0, pi/2] through
 // s = sin^2(dtheta) = (t x r)^2 / (|t|^2 |r|^2) in float32.  w_g = 0 beyond pi/6 (s > 1/4); otherwise the
 // Q12 table entry at floor(sqrt(s) 2^15).  Eq. 23 is applied as printed: exp(-|dtheta| / sigma_g^2 * 36/pi).
+#include <type_traits>
+
 #include "ld_internal.cuh"
 
 namespace ld {
@@ -20,7 +22,7 @@ namespace {
 
 constexpr int kM1Threads = 512;
 constexpr int kEnThreads = 128;
-constexpr int kEnBatch = 16;   // track rows whose M_1 loads are in flight together
+constexpr int kEnBatch = 8;    // track rows whose M_1 loads are in flight together
 constexpr int kSelThreads = 256;
 
 // k_m1 works on D(u, v) = M_0(u+1, v) - M_0(u-1, v).  An edge pixel at (u_e, v_e) adds g = G_x w_g to the
@@ -91,8 +93,14 @@ __global__ void __launch_bounds__(kM1Threads, 2) k_m1(const KParams kp, const Wo
     const int rs = max(r0, vtop);
     for (int c0 = 0; c0 < W; c0 += Wc) {
         const int c1 = min(W, c0 + Wc), cw = c1 - c0;
-        for (int i = tid; i < ndr * cw; i += kM1Threads)
-            dd[i] = 0;
+        {
+            const int nz = ndr * cw;
+            int4 *dd4 = reinterpret_cast<int4 *>(dd);
+            for (int i = tid; i < (nz >> 2); i += kM1Threads)
+                dd4[i] = make_int4(0, 0, 0, 0);
+            for (int i = (nz & ~3) + tid; i < nz; i += kM1Threads)
+                dd[i] = 0;
+        }
         __syncthreads();
         const int total = eoff[ner];
         for (int q = tid; q < total; q += kM1Threads) {
@@ -183,35 +191,45 @@ __global__ void __launch_bounds__(kEnThreads, 8) k_energy(const KParams kp, cons
     const int32_t *M1 = w.M1 + (size_t)f * H * W;
     const float fW = (float)W;
     const bool lam = kp.lambda_g != 0;  // lambda_g is 0 or 1
-    // the track recursion does not depend on M_1: kEnBatch rows of track columns are computed and their
-    // M_1 loads issued before the energy recursion consumes them, so loads overlap instead of chaining
+    // The track recursion does not depend on M_1.  Each batch of kEnBatch rows first computes the track
+    // columns (no load in flight while the divisions run), then issues the batch's M_1 loads back to back,
+    // then adds them in row order.
     float u = (float)(i - kp.S0);
     long long E = 0;
-    for (int v0 = vmax; v0 >= vtop; v0 -= kEnBatch) {
-        int32_t m[kEnBatch];
+    auto batch = [&](int v0, int nb, auto full) {
+        int col[kEnBatch];
         float fv = (float)v0;  // (float)v, exact (v < 2^24)
 #pragma unroll
         for (int b = 0; b < kEnBatch; ++b) {
             const int v = v0 - b;
-            m[b] = 0;
-            if (v >= vtop) {
+            col[b] = -1;
+            if (decltype(full)::value || b < nb) {
                 if (v < vmax) {
                     const float vx = vrow[v + 1], vy = vrow[H + v + 1];
                     const float num = __fsub_rn(__fadd_rn(vx, __fmul_rn(fv, u)), __fmul_rn(vy, u));
                     const float den = __fsub_rn(__fadd_rn(fv, 1.0f), vy);
                     u = __fdiv_rn(num, den);
                 }
-                const float col = floorf(__fadd_rn(u, 0.5f));
-                if (col >= 0.0f && col < fW)
-                    m[b] = __ldg(M1 + (size_t)v * W + (int)col);
+                const float c = floorf(__fadd_rn(u, 0.5f));
+                if (c >= 0.0f && c < fW)
+                    col[b] = (int)c;
             }
             fv = __fsub_rn(fv, 1.0f);
         }
+        int32_t m[kEnBatch];
 #pragma unroll
         for (int b = 0; b < kEnBatch; ++b)
-            if (v0 - b >= vtop)
+            m[b] = col[b] >= 0 ? __ldg(M1 + (size_t)(v0 - b) * W + col[b]) : 0;
+#pragma unroll
+        for (int b = 0; b < kEnBatch; ++b)
+            if (decltype(full)::value || b < nb)
                 E = (long long)m[b] + (lam ? E : 0ll);
-    }
+    };
+    int v0 = vmax;
+    for (; v0 - kEnBatch + 1 >= vtop; v0 -= kEnBatch)
+        batch(v0, kEnBatch, std::true_type());
+    if (v0 >= vtop)
+        batch(v0, v0 - vtop + 1, std::false_type());
     w.HE[(size_t)f * kp.n_starts + i] = (int64_t)E;
 }
 

@@ -7,9 +7,9 @@
 // the CTA streams it as 16-byte loads of the aligned chunks inside it (several in flight per thread) plus
 // single loads of its head and tail; each warp streams one contiguous span.  Counts go to a shared-memory
 // histogram per row.  Disparity is locally smooth (a road row holds one or two bins, an obstacle one), so
-// each thread keeps a run of equal (row, bin) keys in registers and adds the run with one shared-memory
-// atomic when the key changes: far fewer atomics than pixels, and no 32-way conflicts on the dominant
-// bin.  The histogram is written transposed, [D][H] per frame, so that each step of the road DP (Eq. 12)
+// each thread counts a run of equal (row, bin) keys in registers and adds the run with one shared-memory
+// atomic when the key changes: fewer atomics than pixels, and few 32-way conflicts on the dominant bin.
+// The run update is branch-free (the flush is a predicated add), so warps do not diverge on the data.  The histogram is written transposed, [D][H] per frame, so that each step of the road DP (Eq. 12)
 // reads one contiguous row.
 #include "ld_internal.cuh"
 
@@ -19,6 +19,13 @@ namespace {
 constexpr int kRows = 8;
 constexpr int kThreads = 256;
 constexpr int kUnroll = 4;  // 16-byte loads in flight per thread
+
+// Shared-memory add of v at address a when p holds, as one predicated instruction (no branch).
+__device__ __forceinline__ void red_add_if(bool p, uint32_t a, int v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(a), "r"(v),
+                 "r"((int)p));
+}
 
 __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *__restrict__ myT,
                                                     const float *__restrict__ disp)
@@ -58,33 +65,30 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
     // row and column of the lane's first pixel, then advanced by 128 pixels per step (no division)
     int off0 = head + 4 * (w0 + lane);
     int row = off0 / W, col = off0 - row * W;
-    int run_key = -1, run_cnt = 0;
+    // one run per lane, updated without branches: a pixel whose key differs from the run flushes the run
+    // with a predicated shared-memory add, so the warp never diverges on the data
+    const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(hist);
+    int run_key = 0, run_cnt = 0;
     for (int base = w0; base < w1; base += 32 * kUnroll) {
         float4 x[kUnroll];
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             const int i = base + 32 * k + lane;
-            if (i < w1)
-                x[k] = __ldg(body + i);
+            x[k] = i < w1 ? __ldg(body + i) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // 0 does not count
         }
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
-            const int i = base + 32 * k + lane;
-            if (i < w1) {
-                const float l[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
-                const int rb = row * D;
+            const float l[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
+            const int rb = row * D;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int b = bin_of(l[e]);
-                    const int key = b < 0 ? -1 : (col + e < W ? rb : rb + D) + b;
-                    if (key >= 0 && key != run_key) {
-                        if (run_cnt)
-                            atomicAdd(&hist[run_key], run_cnt);
-                        run_key = key;
-                        run_cnt = 0;
-                    }
-                    run_cnt += key >= 0;
-                }
+            for (int e = 0; e < 4; ++e) {
+                const int b = __float2int_rd(__fadd_rn(l[e], 0.5f));
+                const bool ok = l[e] > 0.0f && b < D;
+                const int key = (col + e < W ? rb : rb + D) + b;
+                const bool nk = ok && key != run_key;
+                red_add_if(nk && run_cnt != 0, hbase + 4u * (uint32_t)run_key, run_cnt);
+                run_cnt = nk ? 1 : run_cnt + (int)ok;
+                run_key = nk ? key : run_key;
             }
             col += 128;
             while (col >= W) {
@@ -93,8 +97,7 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
             }
         }
     }
-    if (run_cnt)
-        atomicAdd(&hist[run_key], run_cnt);
+    red_add_if(run_cnt != 0, hbase + 4u * (uint32_t)run_key, run_cnt);
     __syncthreads();
     int32_t *dst = myT + (size_t)f * D * H;
     for (int i = tid; i < D * nr; i += kThreads) {

@@ -1,0 +1,41 @@
+"""Run the detector on one named synthetic workload a few times, with eager launches (no CUDA graph), so
+that a profiler attached to the process sees every kernel of every call as a separate launch.
+
+    python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4
+
+Each call launches the nine kernels of the path once, in order, on the handle's stream, and times each
+with CUDA events; the per-kernel times of the last call are printed.
+"""
+from __future__ import annotations
+
+import sys
+
+
+def main(argv=None):
+    import numpy as np
+    import torch
+
+    from . import ld, scenes
+
+    argv = sys.argv[1:] if argv is None else argv
+    name = argv[0] if argv else "batch64_1242x375"
+    calls = int(argv[1]) if len(argv) > 1 else 4
+    if name not in scenes.WORKLOADS:
+        raise SystemExit(f"unknown workload {name!r}; known: {', '.join(scenes.WORKLOADS)}")
+    cfg, n = scenes.WORKLOADS[name]
+    disp, img, _ = scenes.make_batch(cfg, n)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    det = ld.Detector(cfg.width, cfg.height, n, p)
+    d = torch.from_numpy(disp).cuda()
+    i = torch.from_numpy(img).cuda()
+    out = det.alloc_lanes(n)
+    ms = None
+    for _ in range(calls):
+        ms = det.detect_timed(d, i, out)
+    torch.cuda.synchronize()
+    print(name, n, "frames:", {k: round(float(x), 4) for k, x in zip(ld.launch_names(), np.asarray(ms))})
+    det.close()
+
+
+if __name__ == "__main__":
+    main()
