@@ -117,14 +117,6 @@ __device__ __forceinline__ int nib16(const uint16_t *row, int i) { return (row[i
 // Shared-memory accesses through 32-bit shared addresses (keeps the hot DP loop on the shared-memory path
 // whatever pointers the compiler can prove).
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ int lds(uint32_t a)
-{
-    int v;
-    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ void sts(uint32_t a, int v) { asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v)); }
-__device__ __forceinline__ void sts16(uint32_t a, uint32_t v) { asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"((uint16_t)v)); }
 __device__ __forceinline__ void atoms_add(uint32_t a, int v) { asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v)); }
 
 // ---------------------------------------------------------------------------------------------------

@@ -10,11 +10,14 @@
 // (2 sum(w I) + sum(w)) / (2 sum(w)), so the result does not depend on the order of the taps.
 //
 // GB300 mapping of the bilateral (the cost of the whole path sits here):
-//   - taps at equal distance share ws, so w depends only on (distance class, I(i,j) - I(u,v)); the CTA
-//     builds one 768-entry uint16 table per class in shared memory and a tap costs one table load, an
-//     address add and two 32-bit accumulations (sum(w) and sum(w 2 I) on separate pipes);
-//   - the tile stores 2 I (a byte offset into a table), so the table address is base_c + 2 I(i,j) + class
-//     offset, and sum(w 2 I) keeps the same exact arithmetic;
+//   - taps at equal distance share ws and the range weight depends on |I(i,j) - I(u,v)| only, so w depends
+//     on (distance class, |dI|); the CTA builds one 512-entry uint16 table per class in shared memory and
+//     a tap costs one absolute-difference-add (__usad), one table load and two 32-bit accumulations
+//     (sum(w) and sum(w 2 I) on separate pipes).  Indexing by |dI| halves the banks the common small
+//     differences occupy, which cuts the data-dependent bank conflicts of the lookups;
+//   - the tile stores 2 I (a byte offset into a table), so the table address is base_c + |2 I(i,j) - 2 I(u,v)|
+//     with a compile-time class offset, and sum(w 2 I) keeps the same exact arithmetic; the sentinel 2 x 511
+//     outside the frame lands in the zero half of every table;
 //   - a thread filters 4 horizontally adjacent pixels, sharing each window row it loads as 64-bit vectors;
 //   - pixel groups that need the filter are compacted first, so warps do not diverge on the road mask.
 // Staging: the image rows of a CTA (and its disparity rows) are one contiguous range of global memory,
@@ -32,9 +35,40 @@ namespace ld {
 namespace {
 
 constexpr int kThreads = 1024;
-constexpr int kTabBytes = kWrEntries * 2;  // one uint16 table per distance class
+constexpr int kTabEntries = 512;           // T_c[|dI|]: |dI| <= 255, zero from 256 on (where the sentinel lands)
+constexpr int kTabBytes = kTabEntries * 2;  // one uint16 table per distance class
+
+// Distance class of every tap (rank of dx^2 + dy^2 among the distinct values of the window), as byte
+// offsets of the class tables; a compile-time table, so an unrolled tap loop folds them into the loads.
+template <int RHO>
+__host__ __device__ constexpr int cls_rank(int d2)
+{
+    int r = 0;
+    for (int s = 0; s < d2; ++s) {
+        bool seen = false;
+        for (int dy = 0; dy <= RHO; ++dy)
+            for (int dx = 0; dx <= RHO; ++dx)
+                if (dx * dx + dy * dy == s)
+                    seen = true;
+        r += seen ? 1 : 0;
+    }
+    return r;
+}
+template <int RHO>
+struct ClsOffsets {
+    int v[(2 * RHO + 1) * (2 * RHO + 1)];
+};
+template <int RHO>
+__host__ __device__ constexpr ClsOffsets<RHO> make_cls_offsets()
+{
+    ClsOffsets<RHO> o{};
+    for (int dy = 0; dy <= 2 * RHO; ++dy)
+        for (int dx = 0; dx <= 2 * RHO; ++dx)
+            o.v[dy * (2 * RHO + 1) + dx] = cls_rank<RHO>((dy - RHO) * (dy - RHO) + (dx - RHO) * (dx - RHO)) * kTabBytes;
+    return o;
+}
 constexpr int kLoadsImg = 2, kLoadsDisp = 3;  // 16-byte staging loads per thread and pass
-static_assert(kThreads >= kWrEntries, "one thread per range-weight entry builds the class tables");
+static_assert(kThreads >= kTabEntries, "one thread per table entry builds the class tables");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -75,7 +109,7 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const uint32_t c2 = (u0 + p < W) ? crow[p] : 0u;  // pixels past the right edge: any valid index
-        base[p] = tab + 512u - c2;
+        base[p] = c2;
         sw[p] = 0u;
         swi[p] = 0u;
     }
@@ -96,7 +130,8 @@ __device__ __forceinline__ uint32_t bilateral4(const KParams &kp, const uint16_t
 #pragma unroll
             for (int dx = 0; dx < N; ++dx) {
                 const uint32_t qq = q[p + dx];
-                const uint32_t wq = lds_u16(base[p] + qq + kp.cls_off[dy * N + dx]);
+                constexpr ClsOffsets<RHO> kOff = make_cls_offsets<RHO>();
+                const uint32_t wq = lds_u16(__usad(qq, base[p], tab) + (uint32_t)kOff.v[dy * N + dx]);
                 sw[p] += wq;
                 swi[p] += wq * qq;
             }
@@ -137,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad(const KParams kp, const Wo
     const int TR = nr + 2 + 2 * RHO, BR = nr + 2;
 
     unsigned char *p = smem;
-    uint16_t *tabs = reinterpret_cast<uint16_t *>(p);           // [n_cls][768]
+    uint16_t *tabs = reinterpret_cast<uint16_t *>(p);           // [n_cls][512]
     p += (size_t)kTabBytes * kp.n_cls;
     int32_t *cnt = reinterpret_cast<int32_t *>(p);              // [2][R] edges, votes per row; [2R] groups
     p += sizeof(int32_t) * (2 * R + 4);
@@ -175,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad(const KParams kp, const Wo
     const int ooI = tid < headI ? tid : tailI + (tid - headI);
     const int ooD = tid < headD ? tid : tailD + (tid - headD);
 
-    const uint32_t wrk = tid < kWrEntries ? (uint32_t)__ldg(w.wr + tid) : 0u;
+    const uint32_t wrk = tid < 256 ? (uint32_t)__ldg(w.wr + 256 + tid) : 0u;  // Q15 wr(|dI|)
     const float fr = tid < nr ? __ldg(rows + r0 + tid) : 0.0f;
     const float vyr = tid < nr ? __ldg(rows + H + r0 + tid) : 0.0f;
     const uint32_t bI = tid < nsI ? (uint32_t)__ldg(gs + ooI) : 0u;
@@ -191,10 +226,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad(const KParams kp, const Wo
         if (k * kThreads + tid < nD)
             xd[k] = __ldg(bodyD + k * kThreads + tid);
 
-    // per-class weight tables T_c[k] = (ws_c * wr[k] + 2^14) >> 15, k = q - c + 256, one thread per k
-    if (tid < kWrEntries)
+    // per-class weight tables T_c[a] = (ws_c * wr(a) + 2^14) >> 15 for a = |I(i,j) - I(u,v)|, one thread per a
+    if (tid < kTabEntries)
         for (int c = 0; c < kp.n_cls; ++c)
-            tabs[c * kWrEntries + tid] = (uint16_t)(((uint32_t)kp.cls_ws[c] * wrk + 16384u) >> 15);
+            tabs[c * kTabEntries + tid] = (uint16_t)(((uint32_t)kp.cls_ws[c] * wrk + 16384u) >> 15);
     for (int i = tid; i < 2 * R + 4; i += kThreads)
         cnt[i] = 0;
     if (tid < nr) {
@@ -291,7 +326,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad(const KParams kp, const Wo
             const int j = j0 + lane;
             bool need = false;
             if (j < L.NG) {
-                const int u0 = 4 * j;
 #pragma unroll
                 for (int dr = -1; dr <= 1; ++dr) {
                     const int rr = br - 1 + dr;
@@ -404,12 +438,16 @@ size_t grad_smem(int W, int R, int n_cls)
     return s + 16;
 }
 
-// Rows per CTA: the most whose shared memory stays within 200 KB (one 1024-thread CTA per SM).
+// Rows per CTA: 28 when that fits the 220 KB shared-memory budget (fewer, taller tiles: less halo and
+// fewer waves over 152 SMs), else 16, else the most that fit (one 1024-thread CTA per SM either way).
 template <int RHO>
 int grad_rows(int W, int n_cls)
 {
+    constexpr size_t kBudget = 220 * 1024;
+    if (grad_smem<RHO>(W, 28, n_cls) <= kBudget)
+        return 28;
     int R = 16;
-    while (R > 1 && grad_smem<RHO>(W, R, n_cls) > 200 * 1024)
+    while (R > 1 && grad_smem<RHO>(W, R, n_cls) > kBudget)
         --R;
     return R;
 }

@@ -191,7 +191,6 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
         for (int dy = -rho; dy <= rho; ++dy)
             for (int dx = -rho; dx <= rho; ++dx) {
                 const int c = rank[dx * dx + dy * dy];
-                k.cls_off[(dy + rho) * nn + dx + rho] = (uint16_t)(c * ld::kWrEntries * 2);
                 k.cls_ws[c] = (uint16_t)h->ws_q[(dy + rho) * nn + dx + rho];
             }
     }

@@ -38,10 +38,10 @@ struct KParams {
     int32_t seg_rows;                  // rows of DP backtrack held in shared memory by the V_px kernel
     int32_t vote_cap;                  // votes per frame the V_px kernel stages in shared memory
     uint16_t ws[121];                  // Eq. 16 spatial weights, Q15 (up to 32768), (2 rho + 1)^2 used
-    // Taps at equal distance share one weight table (ws * wr rounded to Q15) in the gradient kernel:
-    // cls_off[tap] = byte offset of the tap's table, cls_ws[c] = the spatial weight of class c.
+    // Taps at equal distance share one weight table in the gradient kernel.  Classes are the ranks of
+    // dx^2 + dy^2 among the distinct values of the window (the kernel derives a tap's class at compile
+    // time in the same way); cls_ws[c] = the spatial weight of class c.
     int32_t n_cls;
-    uint16_t cls_off[121];
     uint16_t cls_ws[24];
 };
 
