@@ -34,50 +34,65 @@ constexpr int kNW = kFitThreads / 32;
 
 __device__ __forceinline__ double p2d(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
 
-// Normal equations of M unknowns from exact sums Sx[k] = sum t^k (k <= 2M-2), Sy[k] = sum y t^k.
+// Normal equations of M unknowns from exact sums S = (Sx[0 .. 2M-2], Sy[0 .. M-1]), Sx[k] = sum t^k,
+// Sy[k] = sum y t^k: A[r][c] = Sx[r + c] 2^-(r+c)e, b[r] = Sy[r] 2^-re (exact power-of-two column scaling),
+// Gaussian elimination with partial pivoting (first row of largest |pivot|; a pivot below 2^-40 is
+// singular), then back substitution; every product, difference and quotient rounded once, no FMA.  Solved
+// on one warp: lane j <= M holds column j of the augmented matrix, the pivot column is broadcast with
+// shuffles and every lane applies the elimination to its own column (the same operations, in the same
+// order, as the serial algorithm); lane 0 back-substitutes.  All lanes of the warp must call it.  Returns
+// 0 on every lane, or -1 if singular.
 template <int M>
-__device__ int solve_normal(const __int128 *Sx, const __int128 *Sy, int e, double *coef)
+__device__ int solve_normal_warp(const __int128 *S, int e, double *coef)
 {
-    double A[M][M + 1];
+    const int lane = threadIdx.x & 31;
+    const int c = lane <= M ? lane : M;  // lanes past M shadow column M and are never read
+    double col[M];
 #pragma unroll
-    for (int j = 0; j < M; ++j) {
-#pragma unroll
-        for (int k = 0; k < M; ++k)
-            A[j][k] = __dmul_rn(i128_to_f64(Sx[j + k]), p2d(-(j + k) * e));
-        A[j][M] = __dmul_rn(i128_to_f64(Sy[j]), p2d(-j * e));
-    }
+    for (int r = 0; r < M; ++r)
+        col[r] = c < M ? __dmul_rn(i128_to_f64(S[r + c]), p2d(-(r + c) * e))
+                       : __dmul_rn(i128_to_f64(S[2 * M - 1 + r]), p2d(-r * e));
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-        // partial pivoting: first row of largest |A[i][k]|, rows swapped by predicated moves
+        double pc[M];  // column k (after the previous steps), from lane k
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            pc[i] = __shfl_sync(0xffffffffu, col[i], k);
         int piv = k;
-        double pa = fabs(A[k][k]);
+        double pa = fabs(pc[k]);
 #pragma unroll
         for (int i = k + 1; i < M; ++i)
-            if (fabs(A[i][k]) > pa) {
-                pa = fabs(A[i][k]);
+            if (fabs(pc[i]) > pa) {
+                pa = fabs(pc[i]);
                 piv = i;
             }
         if (!(pa >= 0x1p-40))
             return -1;
 #pragma unroll
-        for (int i = k + 1; i < M; ++i) {
+        for (int i = k + 1; i < M; ++i)
             if (i == piv) {
+                double t = col[k];
+                col[k] = col[i];
+                col[i] = t;
+                t = pc[k];
+                pc[k] = pc[i];
+                pc[i] = t;
+            }
+        if (c > k) {
 #pragma unroll
-                for (int j = 0; j <= M; ++j) {
-                    const double t = A[k][j];
-                    A[k][j] = A[i][j];
-                    A[i][j] = t;
-                }
+            for (int i = k + 1; i < M; ++i) {
+                const double fct = __ddiv_rn(pc[i], pc[k]);
+                col[i] = __dsub_rn(col[i], __dmul_rn(fct, col[k]));
             }
         }
-#pragma unroll
-        for (int i = k + 1; i < M; ++i) {
-            const double fct = __ddiv_rn(A[i][k], A[k][k]);
-#pragma unroll
-            for (int j = k + 1; j <= M; ++j)
-                A[i][j] = __dsub_rn(A[i][j], __dmul_rn(fct, A[k][j]));
-        }
     }
+    // back substitution on lane 0, rows gathered from the column lanes
+    double A[M][M + 1];
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int j = 0; j <= M; ++j)
+            A[r][j] = __shfl_sync(0xffffffffu, col[r], j);
 #pragma unroll
     for (int k = M - 1; k >= 0; --k) {
         double s = A[k][M];
@@ -87,20 +102,6 @@ __device__ int solve_normal(const __int128 *Sx, const __int128 *Sy, int e, doubl
         coef[k] = __ddiv_rn(s, A[k][k]);
     }
     return 0;
-}
-
-template <int M>
-__device__ __forceinline__ void add_point(__int128 *Sx, __int128 *Sy, int x, int y, int centre)
-{
-    const __int128 t = (__int128)(x - centre);
-    __int128 pw = 1;
-#pragma unroll
-    for (int k = 0; k <= 2 * M - 2; ++k) {
-        Sx[k] += pw;
-        if (k < M)
-            Sy[k] += pw * (__int128)y;
-        pw *= t;
-    }
 }
 
 __device__ __forceinline__ __int128 shfl_down_i128(__int128 v, int d)
@@ -268,22 +269,58 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(const KParams kp, const Wor
             }
         }
         __syncthreads();
-        for (int h = warp; h < kp.hyps; h += kNW) {
-            int cnt = -1;
-            if (hyp_ok[h]) {
-                float cf[2 * M];
+        // inlier counts: consecutive lanes take consecutive hypotheses against the same point (broadcast
+        // point loads, independent iterations); a thread adds its count when its hypothesis changes
+        for (int h = tid; h < kp.hyps; h += kFitThreads)
+            hyp_cnt[h] = hyp_ok[h] ? 0 : -1;
+        __syncthreads();
+        {
+            const int nh = kp.hyps, dh = kFitThreads % nh, dq = kFitThreads / nh;
+            if (dh == 0) {
+                // the thread's hypothesis is fixed: a plain strided loop the compiler can overlap
+                const int h = tid % nh;
+                if (hyp_ok[h]) {
+                    float cf[2 * M];
 #pragma unroll
-                for (int k = 0; k < 2 * M; ++k)
-                    cf[k] = hyp_cf[h * 2 * M + k];
-                int c = 0;
-                for (int q = lane; q < ns; q += 32) {
-                    const int j = list[q];
-                    c += newton_inlier<M>(cf, cf + M, xs[j], ys[j], centre, sc, tr);
+                    for (int k = 0; k < 2 * M; ++k)
+                        cf[k] = hyp_cf[h * 2 * M + k];
+                    int c = 0;
+#pragma unroll 4
+                    for (int q = tid / nh; q < ns; q += dq) {
+                        const int j = list[q];
+                        c += newton_inlier<M>(cf, cf + M, xs[j], ys[j], centre, sc, tr);
+                    }
+                    if (c)
+                        atomicAdd(&hyp_cnt[h], c);
                 }
-                cnt = __reduce_add_sync(0xffffffffu, c);
+            } else {
+                int h = tid % nh, q = tid / nh, cur = -1, c = 0;
+                bool ok = false;
+                float cf[2 * M];
+                for (; q < ns; q += dq) {
+                    if (h != cur) {
+                        if (ok && c)
+                            atomicAdd(&hyp_cnt[cur], c);
+                        cur = h;
+                        c = 0;
+                        ok = hyp_ok[h] != 0;
+#pragma unroll
+                        for (int k = 0; k < 2 * M; ++k)
+                            cf[k] = hyp_cf[h * 2 * M + k];
+                    }
+                    if (ok) {
+                        const int j = list[q];
+                        c += newton_inlier<M>(cf, cf + M, xs[j], ys[j], centre, sc, tr);
+                    }
+                    h += dh;
+                    if (h >= nh) {
+                        h -= nh;
+                        ++q;
+                    }
+                }
+                if (ok && c)
+                    atomicAdd(&hyp_cnt[cur], c);
             }
-            if (lane == 0)
-                hyp_cnt[h] = cnt;
         }
         __syncthreads();
         if (warp == 0) {
@@ -324,48 +361,43 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(const KParams kp, const Wor
         if ((long long)kp.eps_den * bc >= (long long)kp.eps_num * ns)
             break;
     }
-    // final least squares over the remaining set: exact sums reduced over the block
+    // final least squares over the remaining set: exact sums, one warp per sum (sum t^k for k <= 2M-2, then
+    // sum y t^k for k < M), then the normal equations solved on one warp
     if (!(fl & 2)) {
-        __int128 S[3 * M - 1];
+        constexpr int NS = 3 * M - 1;
+        for (int sidx = warp; sidx < NS; sidx += kNW) {
+            const int pk = sidx < 2 * M - 1 ? sidx : sidx - (2 * M - 1);
+            __int128 acc = 0;
+            int cnt = 0;
+            for (int j = lane; j < n; j += 32)
+                if (member[j]) {
+                    const __int128 t = (__int128)(xs[j] - centre);
+                    __int128 pw = sidx < 2 * M - 1 ? (__int128)1 : (__int128)ys[j];
+                    for (int k = 0; k < pk; ++k)
+                        pw *= t;
+                    acc += pw;
+                    ++cnt;
+                }
 #pragma unroll
-        for (int k = 0; k < 3 * M - 1; ++k)
-            S[k] = 0;
-        int cnt = 0;
-        for (int j = tid; j < n; j += kFitThreads)
-            if (member[j]) {
-                add_point<M>(S, S + 2 * M - 1, xs[j], ys[j], centre);
-                ++cnt;
-            }
-        cnt = __reduce_add_sync(0xffffffffu, cnt);
-#pragma unroll
-        for (int k = 0; k < 3 * M - 1; ++k)
             for (int d = 16; d > 0; d >>= 1)
-                S[k] += shfl_down_i128(S[k], d);
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < 3 * M - 1; ++k)
-                red[warp * (3 * M - 1) + k] = S[k];
-            redc[warp] = cnt;
+                acc += shfl_down_i128(acc, d);
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if (lane == 0) {
+                red[sidx] = acc;
+                if (sidx == 0)
+                    redc[0] = cnt;
+            }
         }
         __syncthreads();
-        if (tid == 0) {
-            __int128 T[3 * M - 1];
-#pragma unroll
-            for (int k = 0; k < 3 * M - 1; ++k)
-                T[k] = 0;
-            int total = 0;
-            for (int wi = 0; wi < kNW; ++wi) {
-#pragma unroll
-                for (int k = 0; k < 3 * M - 1; ++k)
-                    T[k] += red[wi * (3 * M - 1) + k];
-                total += redc[wi];
-            }
+        if (warp == 0) {
             double cd[M];
-            int ok = total >= M && solve_normal<M>(T, T + 2 * M - 1, kp.e, cd) == 0;
-            if (ok)
-                for (int k = 0; k < M; ++k)
-                    coef_s[k] = cd[k];
-            sh[2] = ok;
+            int ok = redc[0] >= M ? solve_normal_warp<M>(red, kp.e, cd) == 0 : 0;
+            if (lane == 0) {
+                if (ok)
+                    for (int k = 0; k < M; ++k)
+                        coef_s[k] = cd[k];
+                sh[2] = ok;
+            }
         }
         __syncthreads();
         if (!sh[2])
