@@ -16,9 +16,8 @@
 // A path point whose cell holds no count carries no observation; the kernels hand the points with data to
 // the RANSAC fit (k_fit), in increasing index order.
 //
-// Each DP step is one row of the map.  In the road DP a thread owns four adjacent cells and writes their
-// four 4-bit backtrack entries as one 16-bit word; in the V_px DP a thread owns a pair of cells (more warps
-// per row, which is the latency-bound loop of the path) and writes one byte.  A thread loads the window of
+// Each DP step is one row of the map.  A thread owns a pair of adjacent cells (many warps per step: the
+// step loops are latency-bound) and writes their two 4-bit backtrack entries as one byte.  A thread loads the window of
 // the previous row its cells share once.  The CTA is sized to the row, so the per-row barriers involve few
 // warps.  Rows are padded with sentinels so the candidate loops have no bounds checks.  The V_px DP keeps
 // the backtrack rows of the top of the road in shared memory; the rows below go to a per-frame global
@@ -29,11 +28,9 @@ namespace ld {
 
 namespace {
 
-constexpr int kRoadThreads = 128;
-constexpr int kRoadQ = (LD_MAX_H / 4 + kRoadThreads - 1) / kRoadThreads;  // quads per thread (3)
 constexpr int kMaxChunks = (LD_MAX_H + 31) / 32 + 2;
 constexpr int kSent = 0x3fffffff;  // larger than any DP energy (checked when the handle is created)
-constexpr int kPadY = 20;          // >= 3 + tau_y
+constexpr int kPadY = 20;          // >= 2 + tau_y (rounded up to even)
 constexpr int kPadX = 16;          // >= tau_x rounded up to even, + 1
 
 template <typename T>
@@ -112,7 +109,6 @@ __device__ int block_compact(const uint8_t *flag, int n, int16_t *list, int *chu
     return cnt;
 }
 
-__device__ __forceinline__ int nib16(const uint16_t *row, int i) { return (row[i >> 2] >> (4 * (i & 3))) & 15; }
 
 // Shared-memory accesses through 32-bit shared addresses (keeps the hot DP loop on the shared-memory path
 // whatever pointers the compiler can prove).
@@ -123,39 +119,45 @@ __device__ __forceinline__ void atoms_add(uint32_t a, int v) { asm volatile("red
 // k_road_dp
 // ---------------------------------------------------------------------------------------------------
 template <int TMAX>
-__global__ void __launch_bounds__(kRoadThreads) k_road_dp(const KParams kp, const Work w)
+__global__ void __launch_bounds__(1024) k_road_dp(const KParams kp, const Work w)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int f = blockIdx.x, H = kp.H, D = kp.D, Hq = (H + 3) >> 2;
-    const int tid = threadIdx.x;
+    const int f = blockIdx.x, H = kp.H, D = kp.D, Hp = (H + 1) >> 1;  // Hp: pairs of rows
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int32_t *my = w.myT + (size_t)f * D * H;
 
     unsigned char *p = smem;
-    int *E0 = carve<int>(p, H + kPadY);
-    int *E1 = carve<int>(p, H + kPadY);
-    int *sh = carve<int>(p, kMaxChunks + 2 * (kRoadThreads / 32));
+    int *E0 = carve<int>(p, 2 * Hp + kPadY);
+    int *E1 = carve<int>(p, 2 * Hp + kPadY);
+    int *sh = carve<int>(p, kMaxChunks + 64);
     int16_t *path = carve<int16_t>(p, D);
     uint8_t *flag = carve<uint8_t>(p, D);
     int16_t *pid = carve<int16_t>(p, D);
-    uint16_t *bt = carve<uint16_t>(p, (size_t)D * Hq);
+    uint8_t *bt = carve<uint8_t>(p, (size_t)D * Hp);  // one byte per pair of rows: two 4-bit steps
 
     // E rows hold keys 16 E: a candidate's key 16 (E + lambda tau) + tau orders candidates by energy, then
     // by the smaller tau, so the tie-broken argmin is a plain integer minimum (|16 E| < 2^30 always holds
     // here: energies are bounded by (w + lambda_y tau_y) D).
-    for (int v = tid; v < H + kPadY; v += kRoadThreads) {
+    for (int v = tid; v < 2 * Hp + kPadY; v += nt) {
         E0[v] = v < H ? -16 * my[(size_t)(D - 1) * H + v] : kSent;
         E1[v] = kSent;
     }
-    // data terms of the next two steps are loaded a step ahead of their use
-    int cur[kRoadQ][4], nxt[kRoadQ][4];
+    // thread i owns rows v0 = 2i, v0 + 1.  The data terms of a step are loaded kSets steps ahead into one of
+    // kSets register sets (steps rotate over them), so no register copy waits for a load in flight.
+    const int i = tid, v0 = 2 * i;
+    const bool own = i < Hp;
+    auto load_row = [&](int d, int *dst) {
 #pragma unroll
-    for (int q = 0; q < kRoadQ; ++q)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int v = 4 * (tid + q * kRoadThreads) + c;
-            cur[q][c] = v < H ? my[(size_t)(D - 2) * H + v] : 0;
-            nxt[q][c] = (D - 3 >= 1 && v < H) ? my[(size_t)(D - 3) * H + v] : 0;
+        for (int c = 0; c < 2; ++c) {
+            const int v = v0 + c;
+            dst[c] = (own && d >= 1 && v < H) ? __ldg(my + (size_t)d * H + v) : 0;
         }
+    };
+    constexpr int kSets = 4;  // steps of load latency hidden: kSets - 1
+    int reg[kSets][2];
+#pragma unroll
+    for (int k = 0; k < kSets; ++k)
+        load_row(D - 2 - k, reg[k]);
     __syncthreads();
     int *Ep = E0, *Ec = E1;
     const int tau = kp.tau_y;
@@ -163,57 +165,50 @@ __global__ void __launch_bounds__(kRoadThreads) k_road_dp(const KParams kp, cons
 #pragma unroll
     for (int t = 0; t <= TMAX; ++t)
         ck[t] = t <= tau ? 16 * kp.lambda_y * t + t : kSent;
-    for (int d = D - 2; d >= 1; --d) {
-        int nn[kRoadQ][4];
+    constexpr int NL = (TMAX + 3) / 2;  // 8-byte loads: rows v0 .. v0 + 1 + TMAX
+    auto step = [&](int d, const int *cur) {
+        if (own) {
+            int e[2 * NL];
 #pragma unroll
-        for (int q = 0; q < kRoadQ; ++q)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int v = 4 * (tid + q * kRoadThreads) + c;
-                nn[q][c] = (d - 2 >= 1 && v < H) ? __ldg(my + (size_t)(d - 2) * H + v) : 0;
+            for (int j = 0; j < NL; ++j) {
+                const int2 v2 = *reinterpret_cast<const int2 *>(Ep + v0 + 2 * j);
+                e[2 * j] = v2.x;
+                e[2 * j + 1] = v2.y;
             }
+            uint32_t code = 0;
+            int out[2];
 #pragma unroll
-        for (int q = 0; q < kRoadQ; ++q) {
-            const int i = tid + q * kRoadThreads;
-            if (i < Hq) {
-                const int v0 = 4 * i;
-                int e[4 + TMAX];
+            for (int c = 0; c < 2; ++c) {
+                int kk[TMAX + 1];
 #pragma unroll
-                for (int j = 0; j < 4 + TMAX; ++j)
-                    e[j] = Ep[v0 + j];
-                uint32_t code = 0;
+                for (int t = 0; t <= TMAX; ++t)
+                    kk[t] = e[c + t] + ck[t];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    int kk[TMAX + 1];
+                for (int st = 1; st <= TMAX; st *= 2)
 #pragma unroll
-                    for (int t = 0; t <= TMAX; ++t)
-                        kk[t] = e[c + t] + ck[t];
-#pragma unroll
-                    for (int st = 1; st <= TMAX; st *= 2)
-#pragma unroll
-                        for (int j = 0; j + st <= TMAX; j += 2 * st)
-                            kk[j] = min(kk[j], kk[j + st]);
-                    if (v0 + c < H)
-                        Ec[v0 + c] = -16 * cur[q][c] + (kk[0] & ~15);
-                    code |= (uint32_t)(kk[0] & 15) << (4 * c);
-                }
-                bt[(size_t)d * Hq + i] = (uint16_t)code;
+                    for (int j = 0; j + st <= TMAX; j += 2 * st)
+                        kk[j] = min(kk[j], kk[j + st]);
+                out[c] = v0 + c < H ? -16 * cur[c] + (kk[0] & ~15) : kSent;
+                code |= (uint32_t)(kk[0] & 15) << (4 * c);
             }
+            *reinterpret_cast<int2 *>(Ec + v0) = make_int2(out[0], out[1]);
+            bt[(size_t)d * Hp + i] = (uint8_t)code;
         }
-#pragma unroll
-        for (int q = 0; q < kRoadQ; ++q)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                cur[q][c] = nxt[q][c];
-                nxt[q][c] = nn[q][c];
-            }
         __syncthreads();
         int *tmp = Ep;
         Ep = Ec;
         Ec = tmp;
+    };
+    for (int d = D - 2; d >= 1; d -= kSets) {
+#pragma unroll
+        for (int k = 0; k < kSets; ++k)
+            if (d - k >= 1) {
+                step(d - k, reg[k]);
+                load_row(d - k - kSets, reg[k]);
+            }
     }
     int bv = 0x7fffffff, bi = 0x7fffffff;
-    for (int v = tid; v < H; v += kRoadThreads)
+    for (int v = tid; v < H; v += nt)
         if (Ep[v] < bv) {
             bv = Ep[v];
             bi = v;
@@ -223,20 +218,21 @@ __global__ void __launch_bounds__(kRoadThreads) k_road_dp(const KParams kp, cons
         path[0] = -1;
         int v = vstar;
         path[1] = (int16_t)v;
-        for (int d = 1; d <= D - 2; ++d) {
-            v += nib16(bt + (size_t)d * Hq, v);
+        const uint8_t *row = bt + Hp;
+        for (int d = 1; d <= D - 2; ++d, row += Hp) {
+            v += (row[v >> 1] >> (4 * (v & 1))) & 15;
             path[d + 1] = (int16_t)v;
         }
     }
     __syncthreads();
-    for (int d = tid; d < D; d += kRoadThreads) {
+    for (int d = tid; d < D; d += nt) {
         flag[d] = d >= 1 && my[(size_t)d * H + path[d]] > 0;
         w.path_y[(size_t)f * D + d] = path[d];
     }
     __syncthreads();
     const int k = block_compact(flag, D, pid, sh);
     int16_t *gp = w.pts + (size_t)f * 2 * 3 * w.pmax;
-    for (int j = tid; j < k; j += kRoadThreads) {
+    for (int j = tid; j < k; j += nt) {
         gp[j] = path[pid[j]];
         gp[w.pmax + j] = pid[j];
         gp[2 * w.pmax + j] = pid[j];
@@ -297,19 +293,19 @@ __device__ __forceinline__ VoteRow vote_row(const KParams &kp, const Work &w, co
 }
 
 // Scatter the band change between row v+1 and row v (votes of row v - chi enter, of row v + chi + 1 leave)
-// into the delta array `delta` (shared address).
+// into the delta array `delta` (shared address), by the threads t0, t0 + stride, ...
 __device__ __forceinline__ void scatter_delta(const KParams &kp, const Work &w, const VpxMem &S, int f, int v, int vtop,
-                                              bool staged, uint32_t delta)
+                                              bool staged, uint32_t delta, int t0, int stride)
 {
     const int vmax = kp.H - 1, chi = kp.chi;
     if (v - chi >= vtop) {
         const VoteRow vr = vote_row(kp, w, S, f, v - chi, staged);
-        for (int q = threadIdx.x; q < vr.n; q += blockDim.x)
+        for (int q = t0; q < vr.n; q += stride)
             atoms_add(delta + 4u * (uint32_t)vr.p[q], 1);
     }
     if (v + chi + 1 <= vmax) {
         const VoteRow vr = vote_row(kp, w, S, f, v + chi + 1, staged);
-        for (int q = threadIdx.x; q < vr.n; q += blockDim.x)
+        for (int q = t0; q < vr.n; q += stride)
             atoms_add(delta + 4u * (uint32_t)vr.p[q], -1);
     }
 }
@@ -485,12 +481,12 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
     __syncthreads();
     int *Ep = S.E0, *Ec = S.E1;
     if (vmax - 1 >= vtop) {
-        scatter_delta(kp, w, S, f, vmax - 1, vtop, staged, ((vmax - 1) & 1) ? d1 : d0);
+        scatter_delta(kp, w, S, f, vmax - 1, vtop, staged, ((vmax - 1) & 1) ? d1 : d0, tid, nt);
         __syncthreads();
     }
     for (int v = vmax - 1; v >= vtop; --v) {
         if (v - 1 >= vtop)
-            scatter_delta(kp, w, S, f, v - 1, vtop, staged, ((v - 1) & 1) ? d1 : d0);
+            scatter_delta(kp, w, S, f, v - 1, vtop, staged, ((v - 1) & 1) ? d1 : d0, tid, nt);
         const uint32_t dv = (v & 1) ? d1 : d0;
         const int r = v - vtop;
 #pragma unroll
@@ -741,17 +737,24 @@ RoadKernel road_kernel(int tau) { return tau <= 6 ? k_road_dp<6> : k_road_dp<15>
 
 size_t road_smem_bytes(const KParams &kp)
 {
-    const size_t H = kp.H, D = kp.D, Hq = (H + 3) / 4;
+    const size_t H = kp.H, D = kp.D, Hp = (H + 1) / 2;
     size_t s = 0;
     auto add = [&](size_t bytes) { s = ((s + 15) & ~(size_t)15) + bytes; };
-    add(4 * (H + kPadY));
-    add(4 * (H + kPadY));
-    add(4 * (kMaxChunks + 2 * (kRoadThreads / 32)));
+    add(4 * (2 * Hp + kPadY));
+    add(4 * (2 * Hp + kPadY));
+    add(4 * (kMaxChunks + 64));
     add(2 * D);
     add(D);
     add(2 * D);
-    add(2 * D * Hq);
+    add(D * Hp);
     return s + 64;
+}
+
+// One thread per pair of rows (at least two warps).
+int road_threads(int H)
+{
+    const int nt = ((H + 1) / 2 + 31) / 32 * 32;
+    return nt < 64 ? 64 : nt;
 }
 
 size_t vpx_smem_bytes(const KParams &kp) { return vpx_fixed_bytes(kp) + vpx_dyn_bytes(kp); }
@@ -779,7 +782,7 @@ cudaError_t setup_dp(int smem_optin)
 
 cudaError_t launch_road(const KParams &kp, const Work &w, cudaStream_t s)
 {
-    road_kernel(kp.tau_y)<<<kp.n_frames, kRoadThreads, road_smem_bytes(kp), s>>>(kp, w);
+    road_kernel(kp.tau_y)<<<kp.n_frames, road_threads(kp.H), road_smem_bytes(kp), s>>>(kp, w);
     return cudaGetLastError();
 }
 
