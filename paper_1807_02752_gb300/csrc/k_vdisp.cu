@@ -9,14 +9,15 @@
 // histogram per row.  Disparity is locally smooth (a road row holds one or two bins, an obstacle one), so
 // each thread counts a run of equal (row, bin) keys in registers and adds the run with one shared-memory
 // atomic when the key changes: fewer atomics than pixels, and few 32-way conflicts on the dominant bin.
-// The run update is branch-free (the flush is a predicated add), so warps do not diverge on the data.  The histogram is written transposed, [D][H] per frame, so that each step of the road DP (Eq. 12)
+// The run update is branch-free (the flush is a predicated add; invalid pixels keep the run going), so
+// warps do not diverge on the data.  The histogram is written transposed, [D][H] per frame, so that each step of the road DP (Eq. 12)
 // reads one contiguous row.
 #include "ld_internal.cuh"
 
 namespace ld {
 
 namespace {
-constexpr int kRows = 8;
+constexpr int kRows = 16;
 constexpr int kThreads = 256;
 constexpr int kUnroll = 4;  // 16-byte loads in flight per thread
 
@@ -65,8 +66,8 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
     // row and column of the lane's first pixel, then advanced by 128 pixels per step (no division)
     int off0 = head + 4 * (w0 + lane);
     int row = off0 / W, col = off0 - row * W;
-    // one run per lane, updated without branches: a pixel whose key differs from the run flushes the run
-    // with a predicated shared-memory add, so the warp never diverges on the data
+    // one run per lane, updated without branches: an invalid pixel takes the run's key (it neither breaks nor
+    // extends the count); a new key flushes the run with a predicated shared-memory add (an empty run adds 0)
     const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(hist);
     int run_key = 0, run_cnt = 0;
     for (int base = w0; base < w1; base += 32 * kUnroll) {
@@ -79,16 +80,16 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             const float l[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
-            const int rb = row * D;
+            const int rb = row * D, rw = W - col;  // pixels e >= rw of this chunk are on the next row
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int b = __float2int_rd(__fadd_rn(l[e], 0.5f));
                 const bool ok = l[e] > 0.0f && b < D;
-                const int key = (col + e < W ? rb : rb + D) + b;
-                const bool nk = ok && key != run_key;
-                red_add_if(nk && run_cnt != 0, hbase + 4u * (uint32_t)run_key, run_cnt);
-                run_cnt = nk ? 1 : run_cnt + (int)ok;
-                run_key = nk ? key : run_key;
+                const int key = ok ? (e < rw ? rb : rb + D) + b : run_key;
+                const bool nk = key != run_key;
+                red_add_if(nk, hbase + 4u * (uint32_t)run_key, run_cnt);
+                run_cnt = (nk ? 0 : run_cnt) + (int)ok;
+                run_key = key;
             }
             col += 128;
             while (col >= W) {
