@@ -410,7 +410,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--streams", type=int, default=2, help="library handles on separate streams, batches alternate")
+    ap.add_argument("--streams", type=int, default=4, help="library handles on separate streams, batches rotate over them")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
