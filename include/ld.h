@@ -38,6 +38,7 @@ extern "C" {
 #define LD_E_CUDA (-2)     /* a CUDA runtime call failed; the message names it */
 #define LD_E_NOMEM (-3)    /* device or pinned-host allocation failed in ld_create */
 #define LD_E_STATE (-4)    /* call not valid in the handle's current state (e.g. no detect yet) */
+#define LD_E_BUSY (-5)     /* serving: no slot of the frame's size class can take it now (admission) */
 
 /* per-frame flags (ld_lanes.flags) */
 #define LD_F_NO_ROAD 1     /* no bottom run of rows with f(v) > 0 and f'(v) > 0 */
@@ -195,6 +196,79 @@ int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t
 #define LD_STATIC_SCRATCH_BYTES (8u << 20)
 int ld_road_path_static(const ld_params *p, const float *disp, int32_t w, int32_t h_px, int32_t n_frames,
                         int16_t *path_out, void *cuda_stream);
+
+/*
+ * Serving: frames of several sizes from several camera streams, batched continuously.  The paper runs one
+ * camera at a time and has no counterpart; its closing remarks suggest carrying the road profile and the
+ * vanishing point from frame to frame, for which the server keeps each stream's latest result in device
+ * memory (ld_server_stream_state).
+ *
+ * A server owns, for every size class, `slots_per_size` slots: a library handle, a CUDA stream, pinned
+ * staging for `max_batch` frames and their device buffers, all allocated in ld_server_create (the HBM a
+ * server may use is fixed there; admission is by free slot).  ld_server_submit copies a frame into the
+ * slot that is filling for its size class (opening a free one if needed); a full slot is launched at once
+ * and a partial one when its oldest frame has waited `max_wait_us` (a scheduler thread of the server).
+ * Each batch is one detection of its frames (the same kernels as ld_detect, launched without a graph),
+ * and every frame's result is the one it would get alone.  Results come back through ld_server_poll in
+ * completion order, each with the caller's tag, its stream, its per-stream sequence number and its
+ * latency from submit to the result being in host memory.  A server is thread-safe.
+ */
+#define LD_MAX_SIZE_CLASSES 8
+typedef struct ld_server ld_server;
+
+typedef struct ld_server_config {
+    int32_t n_sizes;                          /* size classes, 1 .. LD_MAX_SIZE_CLASSES */
+    int32_t sizes[LD_MAX_SIZE_CLASSES][2];    /* (w, h) of each class; a frame must match one exactly */
+    int32_t slots_per_size;                   /* batches of a class filling or in flight at once, >= 1 */
+    int32_t max_batch;                        /* frames per batch, >= 1 */
+    int32_t max_wait_us;                      /* a partial batch launches once its oldest frame waited this */
+    int32_t n_streams;                        /* camera streams: ids 0 .. n_streams-1 */
+} ld_server_config;
+
+typedef struct ld_result {
+    uint64_t tag;                             /* the caller's tag from ld_server_submit */
+    int32_t stream_id, w, h;
+    int64_t seq;                              /* 0, 1, 2 ... per stream, in submission order */
+    double latency_ms;                        /* submit -> result in host memory */
+    ld_lanes lanes;
+} ld_result;
+
+typedef struct ld_server_stats {
+    int64_t submitted, completed, rejected, batches;
+    double mean_batch;                        /* frames per launched batch */
+    double p50_ms, p99_ms;                    /* latency percentiles of the completed frames */
+} ld_server_stats;
+
+/* Create a server (all memory allocated here).  Errors: LD_E_ARG (bad config or params), LD_E_NOMEM,
+ * LD_E_CUDA; *out is NULL on error and ld_server_last_error(NULL) describes it. */
+int ld_server_create(const ld_params *p, const ld_server_config *cfg, ld_server **out);
+
+/* Submit one frame (HOST pointers, [h][w]; copied before the call returns, so the caller may reuse them).
+ * Errors: LD_E_ARG (unknown size or stream id, null pointer), LD_E_BUSY (every slot of the class is full
+ * or in flight: poll and retry), LD_E_CUDA. */
+int ld_server_submit(ld_server *s, int32_t stream_id, const float *disp, const uint8_t *img, int32_t w, int32_t h,
+                     uint64_t tag);
+
+/* Move up to max_out completed results into out (host array); waits up to timeout_ms for the first one.
+ * Returns the number moved (>= 0) or a negative LD_E_* code. */
+int ld_server_poll(ld_server *s, ld_result *out, int32_t max_out, int32_t timeout_ms);
+
+/* Launch every partial batch now and wait until all submitted frames have completed (results stay queued
+ * for ld_server_poll).  Errors: LD_E_CUDA. */
+int ld_server_drain(ld_server *s);
+
+/* The latest result of a stream (highest sequence number completed so far), read from the device copy the
+ * server keeps.  Errors: LD_E_ARG, LD_E_STATE (no frame of that stream completed yet), LD_E_CUDA. */
+int ld_server_stream_state(ld_server *s, int32_t stream_id, ld_lanes *out);
+
+/* Counters and latency percentiles since creation. */
+int ld_server_stats_get(ld_server *s, ld_server_stats *out);
+
+/* Message of the last error on s (or of the last failed ld_server_create when s is NULL). */
+const char *ld_server_last_error(const ld_server *s);
+
+/* Wait for the work in flight and release everything.  NULL is ignored. */
+void ld_server_destroy(ld_server *s);
 
 /* Message of the last error on h (or of the last failed ld_create when h is NULL). */
 const char *ld_last_error(const ld_handle *h);

@@ -644,3 +644,21 @@ void ld_destroy(ld_handle *h)
 }
 
 }  // extern "C"
+
+namespace ld {
+// ld_detect without the graph cache: the nine launches are enqueued directly on the handle's stream (the
+// serving path, whose batch sizes vary from call to call).
+int detect_eager(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+                 ld_lanes *out_lanes)
+{
+    int rc = check_call(h, disp, img, w, hh, n_frames, out_lanes);
+    if (rc != LD_OK)
+        return rc;
+    const ld::KParams kp = make_kparams(h, w, hh, n_frames);
+    h->last_w = w;
+    h->last_h = hh;
+    h->last_n = n_frames;
+    h->have_last = true;
+    return enqueue(h, kp, disp, img, out_lanes);
+}
+}  // namespace ld

@@ -151,4 +151,6 @@ cudaError_t setup_dp(int smem_optin);
 cudaError_t setup_ransac(int smem_optin);
 cudaError_t setup_grad(int smem_optin);
 cudaError_t setup_lpv(int smem_optin);
+int detect_eager(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+                 ld_lanes *out_lanes);
 }  // namespace ld

@@ -1,0 +1,463 @@
+// Serving runtime behind the ld_server_* entry points of include/ld.h: continuous batching of frames of
+// several sizes from several camera streams over a fixed set of slots.
+//
+// A slot is one library handle with its own CUDA stream, pinned host staging for max_batch frames and the
+// device buffers the batch runs from.  Slots cycle FREE -> FILLING (frames copied in by submit) ->
+// IN_FLIGHT (copies, the nine kernels, the result copy and a host callback enqueued on the slot's stream)
+// -> FREE (the callback has moved the results to the completion queue).  A scheduler thread launches a
+// filling slot whose oldest frame has waited max_wait_us.  After each batch the slot's stream also
+// updates the per-stream state in device memory (the latest result of each camera stream), ordered on one
+// state stream so that two batches never race on an entry.  Nothing here blocks on the GPU while holding
+// the server lock: the callback, which CUDA runs on its own thread, takes that lock.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ld_internal.cuh"
+
+static_assert(sizeof(ld_lanes) == 192 && sizeof(ld_result) == 232, "C-ABI result layouts");
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+std::string g_server_create_error;
+
+enum class SlotState { Free, Filling, InFlight };
+
+struct ReqInfo {
+    uint64_t tag;
+    int32_t stream_id;
+    int64_t seq;
+    Clock::time_point t_submit;
+};
+
+struct Slot {
+    ld_server *server = nullptr;
+    int cls = 0;
+    ld_handle *h = nullptr;
+    cudaStream_t stream = nullptr;
+    float *h_disp = nullptr;          // pinned [max_batch][h][w]
+    uint8_t *h_img = nullptr;
+    ld_lanes *h_lanes = nullptr;      // pinned [max_batch]
+    int32_t *h_meta = nullptr;        // pinned [max_batch][3]: stream id, seq low, seq high
+    float *d_disp = nullptr;
+    uint8_t *d_img = nullptr;
+    ld_lanes *d_lanes = nullptr;
+    int32_t *d_meta = nullptr;
+    cudaEvent_t done = nullptr;        // the batch's result copy has completed
+    cudaEvent_t state_done = nullptr;  // the state update that reads this slot's buffers has completed
+    SlotState state = SlotState::Free;
+    int n = 0;
+    std::vector<ReqInfo> reqs;
+};
+
+// Latest result per stream, applied in batch order by one thread: a frame replaces the entry when its
+// sequence number is higher than the entry's.
+__global__ void k_keep_state(const ld_lanes *lanes, const int32_t *meta, int n, ld_lanes *state, long long *state_seq)
+{
+    if (threadIdx.x != 0)
+        return;
+    for (int i = 0; i < n; ++i) {
+        const int sid = meta[3 * i];
+        const long long seq = (long long)(uint32_t)meta[3 * i + 1] | ((long long)meta[3 * i + 2] << 32);
+        if (seq > state_seq[sid]) {
+            state_seq[sid] = seq;
+            state[sid] = lanes[i];
+        }
+    }
+}
+
+void CUDART_CB on_batch_done(void *arg);
+
+}  // namespace
+
+struct ld_server {
+    ld_params p{};
+    ld_server_config cfg{};
+    std::vector<Slot> slots;
+    cudaStream_t state_stream = nullptr;
+    ld_lanes *d_state = nullptr;
+    long long *d_state_seq = nullptr;
+    std::vector<int64_t> next_seq;     // per stream
+    std::vector<int64_t> done_seq;     // highest completed sequence number per stream (-1: none)
+    std::mutex mu;
+    std::condition_variable cv_done;   // results queued / a slot freed
+    std::condition_variable cv_sched;  // the scheduler's wake-up
+    std::deque<ld_result> results;
+    std::vector<double> latencies;
+    int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched_frames = 0;
+    int in_flight = 0;
+    bool stop = false;
+    std::thread scheduler;
+    std::string err;
+};
+
+namespace {
+
+int sfail(ld_server *s, int code, const std::string &msg)
+{
+    if (s)
+        s->err = msg;
+    else
+        g_server_create_error = msg;
+    return code;
+}
+
+size_t frame_px(const ld_server *s, int cls) { return (size_t)s->cfg.sizes[cls][0] * s->cfg.sizes[cls][1]; }
+
+// Enqueue a filling slot's batch (called with the lock held; only asynchronous CUDA calls).
+int launch_slot(ld_server *s, Slot &sl)
+{
+    const int w = s->cfg.sizes[sl.cls][0], hh = s->cfg.sizes[sl.cls][1], n = sl.n;
+    const size_t px = (size_t)n * w * hh;
+    for (int i = 0; i < n; ++i) {
+        sl.h_meta[3 * i] = sl.reqs[i].stream_id;
+        sl.h_meta[3 * i + 1] = (int32_t)(uint32_t)(sl.reqs[i].seq & 0xffffffffu);
+        sl.h_meta[3 * i + 2] = (int32_t)(sl.reqs[i].seq >> 32);
+    }
+    // the previous batch's state update reads d_lanes and d_meta: wait for it before overwriting them
+    cudaError_t e = cudaStreamWaitEvent(sl.stream, sl.state_done, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sl.d_disp, sl.h_disp, px * sizeof(float), cudaMemcpyHostToDevice, sl.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sl.d_img, sl.h_img, px, cudaMemcpyHostToDevice, sl.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sl.d_meta, sl.h_meta, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, sl.stream);
+    if (e != cudaSuccess)
+        return sfail(s, LD_E_CUDA, std::string("batch input copy: ") + cudaGetErrorString(e));
+    int rc = ld::detect_eager(sl.h, sl.d_disp, sl.d_img, w, hh, n, sl.d_lanes);
+    if (rc != LD_OK)
+        return sfail(s, rc, std::string("batch detect: ") + ld_last_error(sl.h));
+    e = cudaMemcpyAsync(sl.h_lanes, sl.d_lanes, sizeof(ld_lanes) * n, cudaMemcpyDeviceToHost, sl.stream);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(sl.done, sl.stream);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(s->state_stream, sl.done, 0);
+    if (e == cudaSuccess) {
+        k_keep_state<<<1, 32, 0, s->state_stream>>>(sl.d_lanes, sl.d_meta, n, s->d_state, s->d_state_seq);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaEventRecord(sl.state_done, s->state_stream);
+    if (e == cudaSuccess)
+        e = cudaLaunchHostFunc(sl.stream, on_batch_done, &sl);
+    if (e != cudaSuccess)
+        return sfail(s, LD_E_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    sl.state = SlotState::InFlight;
+    ++s->in_flight;
+    ++s->batches;
+    s->batched_frames += n;
+    return LD_OK;
+}
+
+// Runs on a CUDA-owned thread once the slot's result copy has completed; host work only.
+void CUDART_CB on_batch_done(void *arg)
+{
+    Slot &sl = *static_cast<Slot *>(arg);
+    ld_server *s = sl.server;
+    const auto now = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const int w = s->cfg.sizes[sl.cls][0], hh = s->cfg.sizes[sl.cls][1];
+        for (int i = 0; i < sl.n; ++i) {
+            ld_result r;
+            r.tag = sl.reqs[i].tag;
+            r.stream_id = sl.reqs[i].stream_id;
+            r.w = w;
+            r.h = hh;
+            r.seq = sl.reqs[i].seq;
+            r.latency_ms = std::chrono::duration<double, std::milli>(now - sl.reqs[i].t_submit).count();
+            r.lanes = sl.h_lanes[i];
+            s->results.push_back(r);
+            s->latencies.push_back(r.latency_ms);
+            s->done_seq[r.stream_id] = std::max(s->done_seq[r.stream_id], r.seq);
+        }
+        s->completed += sl.n;
+        sl.n = 0;
+        sl.reqs.clear();
+        sl.state = SlotState::Free;
+        --s->in_flight;
+    }
+    s->cv_done.notify_all();
+}
+
+void scheduler_loop(ld_server *s)
+{
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto wait = std::chrono::microseconds(std::max(1, s->cfg.max_wait_us));
+    while (!s->stop) {
+        auto next = Clock::now() + std::chrono::milliseconds(50);
+        const auto now = Clock::now();
+        for (Slot &sl : s->slots)
+            if (sl.state == SlotState::Filling && !sl.reqs.empty()) {
+                const auto due = sl.reqs.front().t_submit + wait;
+                if (due <= now)
+                    launch_slot(s, sl);  // an error stays in s->err; the frames stay queued in the slot
+                else
+                    next = std::min(next, due);
+            }
+        s->cv_sched.wait_until(lk, next);
+    }
+}
+
+void free_slot(Slot &sl)
+{
+    if (sl.h)
+        ld_destroy(sl.h);
+    if (sl.stream)
+        cudaStreamDestroy(sl.stream);
+    if (sl.done)
+        cudaEventDestroy(sl.done);
+    if (sl.state_done)
+        cudaEventDestroy(sl.state_done);
+    cudaFreeHost(sl.h_disp);
+    cudaFreeHost(sl.h_img);
+    cudaFreeHost(sl.h_lanes);
+    cudaFreeHost(sl.h_meta);
+    cudaFree(sl.d_disp);
+    cudaFree(sl.d_img);
+    cudaFree(sl.d_lanes);
+    cudaFree(sl.d_meta);
+    sl = Slot();
+}
+
+void release(ld_server *s)
+{
+    for (Slot &sl : s->slots)
+        free_slot(sl);
+    if (s->state_stream)
+        cudaStreamDestroy(s->state_stream);
+    cudaFree(s->d_state);
+    cudaFree(s->d_state_seq);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ld_server_create(const ld_params *p, const ld_server_config *cfg, ld_server **out)
+{
+    if (!out)
+        return sfail(nullptr, LD_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || !cfg)
+        return sfail(nullptr, LD_E_ARG, "params or config is NULL");
+    if (cfg->n_sizes < 1 || cfg->n_sizes > LD_MAX_SIZE_CLASSES || cfg->slots_per_size < 1 || cfg->max_batch < 1 ||
+        cfg->n_streams < 1 || cfg->max_wait_us < 0)
+        return sfail(nullptr, LD_E_ARG, "n_sizes, slots_per_size, max_batch, n_streams or max_wait_us out of range");
+    for (int c = 0; c < cfg->n_sizes; ++c) {
+        const int w = cfg->sizes[c][0], hh = cfg->sizes[c][1];
+        if (w < 16 || hh < 16 || w > LD_MAX_W || hh > LD_MAX_H)
+            return sfail(nullptr, LD_E_ARG, "size class out of range");
+        for (int d = 0; d < c; ++d)
+            if (cfg->sizes[d][0] == w && cfg->sizes[d][1] == hh)
+                return sfail(nullptr, LD_E_ARG, "duplicate size class");
+    }
+    ld_server *s = new ld_server();
+    s->p = *p;
+    s->cfg = *cfg;
+    s->next_seq.assign(cfg->n_streams, 0);
+    s->done_seq.assign(cfg->n_streams, -1);
+    s->slots.resize((size_t)cfg->n_sizes * cfg->slots_per_size);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->state_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->d_state, sizeof(ld_lanes) * cfg->n_streams);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&s->d_state_seq, sizeof(long long) * cfg->n_streams);
+    if (e == cudaSuccess)
+        e = cudaMemset(s->d_state_seq, 0xff, sizeof(long long) * cfg->n_streams);  // -1: nothing yet
+    for (size_t k = 0; k < s->slots.size() && e == cudaSuccess; ++k) {
+        Slot &sl = s->slots[k];
+        sl.server = s;
+        sl.cls = (int)(k / cfg->slots_per_size);
+        const int w = cfg->sizes[sl.cls][0], hh = cfg->sizes[sl.cls][1], n = cfg->max_batch;
+        const size_t px = (size_t)n * w * hh;
+        e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&sl.state_done, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&sl.h_disp, px * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&sl.h_img, px);
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&sl.h_lanes, sizeof(ld_lanes) * n);
+        if (e == cudaSuccess)
+            e = cudaMallocHost(&sl.h_meta, sizeof(int32_t) * 3 * n);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&sl.d_disp, px * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&sl.d_img, px);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&sl.d_lanes, sizeof(ld_lanes) * n);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&sl.d_meta, sizeof(int32_t) * 3 * n);
+        if (e == cudaSuccess) {
+            const int rc = ld_create(p, w, hh, n, sl.stream, &sl.h);
+            if (rc != LD_OK) {
+                const std::string msg = std::string("slot handle: ") + ld_last_error(nullptr);
+                release(s);
+                delete s;
+                return sfail(nullptr, rc, msg);
+            }
+        }
+        sl.reqs.reserve(n);
+    }
+    if (e != cudaSuccess) {
+        const std::string msg = std::string("server allocation: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        release(s);
+        delete s;
+        return sfail(nullptr, e == cudaErrorMemoryAllocation ? LD_E_NOMEM : LD_E_CUDA, msg);
+    }
+    s->scheduler = std::thread(scheduler_loop, s);
+    *out = s;
+    return LD_OK;
+}
+
+int ld_server_submit(ld_server *s, int32_t stream_id, const float *disp, const uint8_t *img, int32_t w, int32_t h,
+                     uint64_t tag)
+{
+    if (!s)
+        return LD_E_ARG;
+    if (!disp || !img || stream_id < 0 || stream_id >= s->cfg.n_streams)
+        return sfail(s, LD_E_ARG, "null frame or stream id out of range");
+    int cls = -1;
+    for (int c = 0; c < s->cfg.n_sizes; ++c)
+        if (s->cfg.sizes[c][0] == w && s->cfg.sizes[c][1] == h)
+            cls = c;
+    if (cls < 0)
+        return sfail(s, LD_E_ARG, "frame size matches no size class");
+    std::unique_lock<std::mutex> lk(s->mu);
+    Slot *target = nullptr;
+    for (Slot &sl : s->slots)
+        if (sl.cls == cls && sl.state == SlotState::Filling && sl.n < s->cfg.max_batch) {
+            target = &sl;
+            break;
+        }
+    if (!target)
+        for (Slot &sl : s->slots)
+            if (sl.cls == cls && sl.state == SlotState::Free) {
+                target = &sl;
+                target->state = SlotState::Filling;
+                break;
+            }
+    if (!target) {
+        ++s->rejected;
+        return sfail(s, LD_E_BUSY, "every slot of the size class is full or in flight");
+    }
+    const size_t px = frame_px(s, cls);
+    std::memcpy(target->h_disp + (size_t)target->n * px, disp, px * sizeof(float));
+    std::memcpy(target->h_img + (size_t)target->n * px, img, px);
+    target->reqs.push_back(ReqInfo{tag, stream_id, s->next_seq[stream_id]++, Clock::now()});
+    ++target->n;
+    ++s->submitted;
+    int rc = LD_OK;
+    if (target->n == s->cfg.max_batch)
+        rc = launch_slot(s, *target);
+    else if (target->n == 1)
+        s->cv_sched.notify_one();  // a new deadline
+    return rc;
+}
+
+int ld_server_poll(ld_server *s, ld_result *out, int32_t max_out, int32_t timeout_ms)
+{
+    if (!s || (!out && max_out > 0) || max_out < 0)
+        return LD_E_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->results.empty() && timeout_ms > 0)
+        s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return !s->results.empty(); });
+    int k = 0;
+    while (k < max_out && !s->results.empty()) {
+        out[k++] = s->results.front();
+        s->results.pop_front();
+    }
+    return k;
+}
+
+int ld_server_drain(ld_server *s)
+{
+    if (!s)
+        return LD_E_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (Slot &sl : s->slots)
+        if (sl.state == SlotState::Filling) {
+            const int rc = launch_slot(s, sl);
+            if (rc != LD_OK)
+                return rc;
+        }
+    // bounded wait: a batch that has not finished after a minute is reported, not waited for forever
+    const bool ok = s->cv_done.wait_for(lk, std::chrono::seconds(60), [&] { return s->in_flight == 0; });
+    return ok ? LD_OK : sfail(s, LD_E_CUDA, "batches still in flight after 60 s");
+}
+
+int ld_server_stream_state(ld_server *s, int32_t stream_id, ld_lanes *out)
+{
+    if (!s || !out || stream_id < 0 || stream_id >= s->cfg.n_streams)
+        return s ? sfail(s, LD_E_ARG, "stream id out of range or null output") : LD_E_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->done_seq[stream_id] < 0)
+            return sfail(s, LD_E_STATE, "no frame of this stream has completed");
+    }
+    cudaError_t e = cudaStreamSynchronize(s->state_stream);  // without the lock: callbacks may need it
+    if (e == cudaSuccess)
+        e = cudaMemcpy(out, s->d_state + stream_id, sizeof(ld_lanes), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LD_OK : sfail(s, LD_E_CUDA, std::string("state copy: ") + cudaGetErrorString(e));
+}
+
+int ld_server_stats_get(ld_server *s, ld_server_stats *out)
+{
+    if (!s || !out)
+        return LD_E_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->rejected = s->rejected;
+    out->batches = s->batches;
+    out->mean_batch = s->batches ? (double)s->batched_frames / (double)s->batches : 0.0;
+    out->p50_ms = out->p99_ms = 0.0;
+    if (!s->latencies.empty()) {
+        std::vector<double> v = s->latencies;
+        auto pct = [&](double q) {
+            const size_t k = (size_t)std::min<double>((double)v.size() - 1, q * (double)(v.size() - 1) + 0.5);
+            std::nth_element(v.begin(), v.begin() + k, v.end());
+            return v[k];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+    }
+    return LD_OK;
+}
+
+const char *ld_server_last_error(const ld_server *s) { return s ? s->err.c_str() : g_server_create_error.c_str(); }
+
+void ld_server_destroy(ld_server *s)
+{
+    if (!s)
+        return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_sched.notify_all();
+    if (s->scheduler.joinable())
+        s->scheduler.join();
+    for (Slot &sl : s->slots)
+        if (sl.stream)
+            cudaStreamSynchronize(sl.stream);  // runs the last callbacks (they take the lock, now free)
+    if (s->state_stream)
+        cudaStreamSynchronize(s->state_stream);
+    release(s);
+    delete s;
+}
+
+}  // extern "C"

@@ -45,6 +45,24 @@ LANES_DTYPE = np.dtype([
 ])
 assert LANES_DTYPE.itemsize == 192
 
+MAX_SIZE_CLASSES = 8
+E_BUSY = -5
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("n_sizes", C.c_int32), ("sizes", (C.c_int32 * 2) * MAX_SIZE_CLASSES), ("slots_per_size", C.c_int32),
+                ("max_batch", C.c_int32), ("max_wait_us", C.c_int32), ("n_streams", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64), ("batches", C.c_int64),
+                ("mean_batch", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
+
+
+RESULT_DTYPE = np.dtype([("tag", "<u8"), ("stream_id", "<i4"), ("w", "<i4"), ("h", "<i4"), ("pad", "<i4"),
+                         ("seq", "<i8"), ("latency_ms", "<f8"), ("lanes", LANES_DTYPE)])
+assert RESULT_DTYPE.itemsize == 232
+
 _lib = None
 
 
@@ -85,13 +103,31 @@ def load():
     L.ld_destroy.restype = None
     L.ld_road_path_static.argtypes = [P, p, i32, i32, i32, p, p]
     L.ld_road_path_static.restype = C.c_int
+    L.ld_server_create.argtypes = [P, C.POINTER(ServerConfig), C.POINTER(p)]
+    L.ld_server_create.restype = C.c_int
+    L.ld_server_submit.argtypes = [p, i32, p, p, i32, i32, C.c_uint64]
+    L.ld_server_submit.restype = C.c_int
+    L.ld_server_poll.argtypes = [p, p, i32, i32]
+    L.ld_server_poll.restype = C.c_int
+    L.ld_server_drain.argtypes = [p]
+    L.ld_server_drain.restype = C.c_int
+    L.ld_server_stream_state.argtypes = [p, i32, p]
+    L.ld_server_stream_state.restype = C.c_int
+    L.ld_server_stats_get.argtypes = [p, C.POINTER(ServerStats)]
+    L.ld_server_stats_get.restype = C.c_int
+    L.ld_server_last_error.argtypes = [p]
+    L.ld_server_last_error.restype = C.c_char_p
+    L.ld_server_destroy.argtypes = [p]
+    L.ld_server_destroy.restype = None
     _lib = L
     return L
 
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
             "ld_debug_get", "ld_debug_size", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
-            "ld_destroy", "ld_road_path_static"]
+            "ld_destroy", "ld_road_path_static", "ld_server_create", "ld_server_submit", "ld_server_poll",
+            "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
+            "ld_server_destroy"]
 
 
 def launch_names():
@@ -234,6 +270,76 @@ class Detector:
         if getattr(self, "h", None):
             self.L.ld_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching of frames of several sizes from several camera streams (ld_server_* of ld.h)."""
+
+    def __init__(self, sizes, params: Params | None = None, slots_per_size: int = 2, max_batch: int = 16,
+                 max_wait_us: int = 500, n_streams: int = 8):
+        self.L = load()
+        self.params = params or default_params()
+        cfg = ServerConfig()
+        cfg.n_sizes = len(sizes)
+        for k, (w, h) in enumerate(sizes):
+            cfg.sizes[k][0] = w
+            cfg.sizes[k][1] = h
+        cfg.slots_per_size, cfg.max_batch, cfg.max_wait_us, cfg.n_streams = slots_per_size, max_batch, max_wait_us, n_streams
+        self.cfg = cfg
+        s = C.c_void_p()
+        rc = self.L.ld_server_create(C.byref(self.params), C.byref(cfg), C.byref(s))
+        if rc != 0:
+            raise LDError(rc, self.L.ld_server_last_error(None).decode())
+        self.s = s
+
+    def submit(self, stream_id: int, disp: np.ndarray, img: np.ndarray, tag: int = 0) -> bool:
+        """Copy one frame in; False when every slot of its size class is busy (poll and retry)."""
+        d = np.ascontiguousarray(disp, np.float32)
+        i = np.ascontiguousarray(img, np.uint8)
+        H, W = d.shape
+        rc = self.L.ld_server_submit(self.s, stream_id, d.ctypes.data, i.ctypes.data, W, H, tag)
+        if rc == E_BUSY:
+            return False
+        if rc != 0:
+            raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
+        return True
+
+    def poll(self, max_out: int = 256, timeout_ms: int = 0) -> np.ndarray:
+        out = np.zeros(max_out, RESULT_DTYPE)
+        k = self.L.ld_server_poll(self.s, out.ctypes.data, max_out, timeout_ms)
+        if k < 0:
+            raise LDError(k, self.L.ld_server_last_error(self.s).decode())
+        return out[:k]
+
+    def drain(self):
+        rc = self.L.ld_server_drain(self.s)
+        if rc != 0:
+            raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
+
+    def stream_state(self, stream_id: int) -> np.ndarray:
+        out = np.zeros(1, LANES_DTYPE)
+        rc = self.L.ld_server_stream_state(self.s, stream_id, out.ctypes.data)
+        if rc != 0:
+            raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
+        return out[0]
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        rc = self.L.ld_server_stats_get(self.s, C.byref(st))
+        if rc != 0:
+            raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.L.ld_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

@@ -1,0 +1,126 @@
+"""Serving measurement: camera streams with Poisson frame arrivals at mixed sizes through one server.
+
+    python -m paper_1807_02752_gb300.serve --streams 8 --fps 60 --seconds 10
+    python -m paper_1807_02752_gb300.serve --streams 8 --saturate --seconds 5
+
+Each camera stream has a fixed resolution (stream k takes size k mod the number of sizes) and submits
+frames at exponential inter-arrival times of mean 1/fps (or back to back with --saturate, a closed loop
+that resubmits as soon as the server admits a frame).  Frames are seeded synthetic scenes of the size's
+workload, generated before the clock starts and reused round-robin.  One JSON line reports the frames/s
+completed, p50/p99 latency from submit to result in host memory (overall and per size), the mean batch
+size and the admissions refused (a refused frame is retried after the next poll).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+
+def scene_config(w: int, h: int, n_disp: int):
+    from . import scenes
+
+    if (w, h) == (1920, 1080):
+        return scenes.with_size(scenes.HD_1920x1080, n_disp=n_disp)
+    if h >= 600:
+        return scenes.with_size(scenes.HD_1920x1080, width=w, height=h, n_disp=n_disp)
+    return scenes.with_size(scenes.BATCH64_1242x375, width=w, height=h, n_disp=n_disp)
+
+
+def main(argv=None):
+    import numpy as np
+
+    from . import ld, scenes
+
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--streams", type=int, default=8)
+    ap.add_argument("--fps", type=float, default=60.0, help="mean frames/s per stream (Poisson arrivals)")
+    ap.add_argument("--saturate", action="store_true", help="closed loop: submit as fast as admission allows")
+    ap.add_argument("--seconds", type=float, default=10.0)
+    ap.add_argument("--sizes", default="1242x375,1280x720,1920x1080")
+    ap.add_argument("--n-disp", type=int, default=256)
+    ap.add_argument("--max-batch", type=int, default=8)
+    ap.add_argument("--slots", type=int, default=2, help="slots per size class")
+    ap.add_argument("--max-wait-us", type=int, default=2000)
+    ap.add_argument("--frames-per-size", type=int, default=8)
+    ap.add_argument("--seed", type=int, default=7)
+    args = ap.parse_args(argv)
+
+    sizes = [tuple(int(x) for x in s.split("x")) for s in args.sizes.split(",")]
+    frames = {}
+    for (w, h) in sizes:
+        cfg = scene_config(w, h, args.n_disp)
+        frames[(w, h)] = [scenes.make_frame(cfg, 1000 + k)[:2] for k in range(args.frames_per_size)]
+    p = ld.default_params(n_disp=args.n_disp)
+    srv = ld.Server(sizes, p, slots_per_size=args.slots, max_batch=args.max_batch, max_wait_us=args.max_wait_us,
+                    n_streams=args.streams)
+    size_of = [sizes[k % len(sizes)] for k in range(args.streams)]
+    rng = np.random.default_rng(args.seed)
+    results = []
+    refused = 0
+    sent = [0] * args.streams
+    t0 = time.perf_counter()
+    t_end = t0 + args.seconds
+    if args.saturate:
+        k = 0
+        while time.perf_counter() < t_end:
+            sid = k % args.streams
+            d, i = frames[size_of[sid]][sent[sid] % args.frames_per_size]
+            if srv.submit(sid, d, i, k):
+                sent[sid] += 1
+                k += 1
+            else:
+                refused += 1
+                results.extend(srv.poll(timeout_ms=1))
+            results.extend(srv.poll())
+    else:
+        due = [t0 + rng.exponential(1.0 / args.fps) for _ in range(args.streams)]
+        k = 0
+        while True:
+            now = time.perf_counter()
+            sid = int(np.argmin(due))
+            if due[sid] >= t_end:
+                break
+            if due[sid] > now:
+                results.extend(srv.poll(timeout_ms=max(0, int((due[sid] - now) * 1e3) - 1)))
+                continue
+            d, i = frames[size_of[sid]][sent[sid] % args.frames_per_size]
+            if srv.submit(sid, d, i, k):
+                sent[sid] += 1
+                k += 1
+                due[sid] += rng.exponential(1.0 / args.fps)
+            else:
+                refused += 1
+                results.extend(srv.poll(timeout_ms=1))
+            results.extend(srv.poll())
+    srv.drain()
+    while True:
+        r = srv.poll()
+        if len(r) == 0:
+            break
+        results.extend(r)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([float(r["latency_ms"]) for r in results])
+    per_size = {}
+    for (w, h) in sizes:
+        m = np.array([int(r["w"]) == w and int(r["h"]) == h for r in results], bool)
+        if m.any():
+            per_size[f"{w}x{h}"] = {"frames": int(m.sum()), "p50_ms": round(float(np.percentile(lat[m], 50)), 3),
+                                    "p99_ms": round(float(np.percentile(lat[m], 99)), 3)}
+    line = {
+        "mode": "saturate" if args.saturate else "poisson", "streams": args.streams,
+        "offered_fps": None if args.saturate else args.fps * args.streams,
+        "frames": len(results), "seconds": round(wall, 3), "fps": round(len(results) / wall, 1),
+        "p50_ms": round(float(np.percentile(lat, 50)), 3) if len(lat) else None,
+        "p99_ms": round(float(np.percentile(lat, 99)), 3) if len(lat) else None,
+        "mean_batch": round(st["mean_batch"], 2), "batches": st["batches"], "refused_submits": refused,
+        "sizes": per_size, "n_disp": args.n_disp, "max_batch": args.max_batch, "slots_per_size": args.slots,
+        "max_wait_us": args.max_wait_us,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,105 @@
+"""Serving: frames of two sizes from three camera streams through one server (continuous batching over
+slots).  Every result must be the one the frame gets alone, byte for byte; results carry the caller's tag
+and per-stream sequence numbers; the device-kept stream state is each stream's latest result.
+"""
+import numpy as np
+import pytest
+
+from paper_1807_02752_gb300 import ld, scenes
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(320, 120), (256, 96)]
+N_STREAMS, PER_STREAM = 3, 6
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_02752_gb300 import build
+    build.build()
+    return torch
+
+
+def _frames():
+    """(stream, frame index in stream, size class, disp, img) in an interleaved submission order."""
+    out = []
+    for k in range(PER_STREAM):
+        for sid in range(N_STREAMS):
+            w, h = SIZES[(sid + k) % len(SIZES)]
+            cfg = scenes.with_size(scenes.SMALL_320x120, width=w, height=h, n_disp=48)
+            d, i, _ = scenes.make_frame(cfg, 100 + 10 * sid + k)
+            out.append((sid, k, (w, h), d, i))
+    return out
+
+
+def _alone(frames, p):
+    dets = {wh: ld.Detector(wh[0], wh[1], 1, p) for wh in SIZES}
+    res = []
+    for sid, k, wh, d, i in frames:
+        res.append(dets[wh].detect_host(d[None], i[None])[0])
+    for det in dets.values():
+        det.close()
+    return res
+
+
+def _serve(frames, p, **kw):
+    srv = ld.Server(SIZES, p, n_streams=N_STREAMS, **kw)
+    got = []
+    for tag, (sid, k, wh, d, i) in enumerate(frames):
+        while not srv.submit(sid, d, i, tag):
+            got.extend(srv.poll(timeout_ms=100))
+    srv.drain()
+    while True:
+        r = srv.poll()
+        if len(r) == 0:
+            break
+        got.extend(r)
+    return srv, got
+
+
+@pytest.mark.parametrize("kw", [dict(slots_per_size=2, max_batch=4, max_wait_us=200),
+                                dict(slots_per_size=1, max_batch=3, max_wait_us=100000),
+                                dict(slots_per_size=3, max_batch=1, max_wait_us=0)])
+def test_results_match_alone(torch_cuda, kw):
+    p = ld.default_params(n_disp=48)
+    frames = _frames()
+    alone = _alone(frames, p)
+    srv, got = _serve(frames, p, **kw)
+    try:
+        assert sorted(int(r["tag"]) for r in got) == list(range(len(frames)))
+        for r in got:
+            tag = int(r["tag"])
+            sid, k, wh, _, _ = frames[tag]
+            assert (int(r["stream_id"]), int(r["seq"]), int(r["w"]), int(r["h"])) == (sid, k, wh[0], wh[1])
+            assert r["lanes"].tobytes() == alone[tag].tobytes(), f"frame {tag} differs from its result alone"
+            assert r["latency_ms"] > 0
+        for sid in range(N_STREAMS):
+            last = max(t for t, f in enumerate(frames) if f[0] == sid)
+            assert srv.stream_state(sid).tobytes() == alone[last].tobytes()
+        st = srv.stats()
+        assert st["submitted"] == st["completed"] == len(frames)
+        assert st["batches"] >= len(frames) / kw["max_batch"]
+        assert 0 < st["p50_ms"] <= st["p99_ms"]
+    finally:
+        srv.close()
+
+
+def test_rejects_unknown_size_and_stream(torch_cuda):
+    p = ld.default_params(n_disp=48)
+    srv = ld.Server(SIZES, p, n_streams=2, slots_per_size=1, max_batch=2)
+    try:
+        d = np.zeros((50, 60), np.float32)
+        i = np.zeros((50, 60), np.uint8)
+        with pytest.raises(ld.LDError):
+            srv.submit(0, d, i)
+        d2 = np.zeros((120, 320), np.float32)
+        i2 = np.zeros((120, 320), np.uint8)
+        with pytest.raises(ld.LDError):
+            srv.submit(5, d2, i2)
+        with pytest.raises(ld.LDError):
+            srv.stream_state(0)  # nothing completed yet
+    finally:
+        srv.close()
