@@ -103,3 +103,49 @@ def test_rejects_unknown_size_and_stream(torch_cuda):
             srv.stream_state(0)  # nothing completed yet
     finally:
         srv.close()
+
+
+def test_concurrent_submitters(torch_cuda):
+    """Three host threads submit their streams at once (the server is thread-safe); nothing is lost or
+    mixed up, and each result is still the frame's result alone."""
+    import threading
+
+    p = ld.default_params(n_disp=48)
+    frames = _frames()
+    alone = _alone(frames, p)
+    srv = ld.Server(SIZES, p, n_streams=N_STREAMS, slots_per_size=2, max_batch=3, max_wait_us=300)
+    errors = []
+
+    def producer(sid):
+        try:
+            for tag, f in enumerate(frames):
+                if f[0] != sid:
+                    continue
+                while not srv.submit(sid, f[3], f[4], tag):
+                    threading.Event().wait(0.0005)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    try:
+        ths = [threading.Thread(target=producer, args=(sid,)) for sid in range(N_STREAMS)]
+        for t in ths:
+            t.start()
+        got = []
+        while any(t.is_alive() for t in ths):
+            got.extend(srv.poll(timeout_ms=5))
+        for t in ths:
+            t.join()
+        srv.drain()
+        while True:
+            r = srv.poll()
+            if len(r) == 0:
+                break
+            got.extend(r)
+        assert not errors, errors
+        assert sorted(int(r["tag"]) for r in got) == list(range(len(frames)))
+        for r in got:
+            tag = int(r["tag"])
+            assert int(r["stream_id"]) == frames[tag][0] and int(r["seq"]) == frames[tag][1]
+            assert r["lanes"].tobytes() == alone[tag].tobytes()
+    finally:
+        srv.close()
