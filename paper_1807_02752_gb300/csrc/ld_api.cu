@@ -1,6 +1,7 @@
 // Host runtime behind include/ld.h: parameter checks, lookup tables, workspace, the launch sequence of
-// one ld_detect call (replayed from a captured CUDA graph when the same buffers come back), the
-// host-buffer path and the debug getters.
+// one ld_detect call (replayed from a captured CUDA graph when the same buffers come back; a call of at
+// least kSplitMin frames is captured as two concurrent half-batches, so one half's per-frame serial kernels
+// overlap the other half's dense kernels), the host-buffer path and the debug getters.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -15,6 +16,7 @@ constexpr int kLaunches = 9;
 const char *const kLaunchNames[kLaunches] = {"k_vdisp", "k_road_dp", "k_fit_y", "k_grad", "k_vpx_dp",
                                              "k_fit_x", "k_m1", "k_energy", "k_select"};
 constexpr int kGraphSlots = 4;
+constexpr int kSplitMin = 16;  // captured calls of at least this many frames run as two concurrent halves
 constexpr int kVoteCap = 12288;
 
 std::string g_create_error;
@@ -47,6 +49,9 @@ struct ld_handle {
     GraphSlot graphs[kGraphSlots];
     int next_slot = 0;
     cudaEvent_t ev[kLaunches + 1] = {};
+    // two half-batches forked onto their own streams inside a captured call (joined before it ends)
+    cudaStream_t sub[2] = {};
+    cudaEvent_t fork = nullptr, join[2] = {};
     std::string err;
 };
 
@@ -201,24 +206,24 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // The launch sequence of one call; with `timed`, an event is recorded before and after every kernel.
-int enqueue(ld_handle *h, const ld::KParams &kp, const float *disp, const uint8_t *img, ld_lanes *out,
-            bool timed = false)
+// The nine launches of one detection of kp.n_frames frames on stream s, on the workspace view w.
+int enqueue_on(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const float *disp, const uint8_t *img,
+               ld_lanes *out, cudaStream_t s, bool timed)
 {
-    cudaStream_t s = h->stream;
     cudaError_t e = cudaSuccess;
     if (timed && (e = cudaEventRecord(h->ev[0], s)) != cudaSuccess)
         return cuda_fail(h, e, "event record");
     for (int k = 0; k < kLaunches; ++k) {
         switch (k) {
-        case 0: e = ld::launch_vdisp(kp, h->w, disp, s); break;
-        case 1: e = ld::launch_road(kp, h->w, s); break;
-        case 2: e = ld::launch_fit_y(kp, h->w, s); break;
-        case 3: e = ld::launch_grad(kp, h->w, disp, img, s); break;
-        case 4: e = ld::launch_vpx(kp, h->w, s); break;
-        case 5: e = ld::launch_fit_x(kp, h->w, s); break;
-        case 6: e = ld::launch_m1(kp, h->w, s); break;
-        case 7: e = ld::launch_energy(kp, h->w, s); break;
-        default: e = ld::launch_select(kp, h->w, out, s); break;
+        case 0: e = ld::launch_vdisp(kp, w, disp, s); break;
+        case 1: e = ld::launch_road(kp, w, s); break;
+        case 2: e = ld::launch_fit_y(kp, w, s); break;
+        case 3: e = ld::launch_grad(kp, w, disp, img, s); break;
+        case 4: e = ld::launch_vpx(kp, w, s); break;
+        case 5: e = ld::launch_fit_x(kp, w, s); break;
+        case 6: e = ld::launch_m1(kp, w, s); break;
+        case 7: e = ld::launch_energy(kp, w, s); break;
+        default: e = ld::launch_select(kp, w, out, s); break;
         }
         if (e != cudaSuccess)
             return cuda_fail(h, e, kLaunchNames[k]);
@@ -226,6 +231,79 @@ int enqueue(ld_handle *h, const ld::KParams &kp, const float *disp, const uint8_
             return cuda_fail(h, e, "event record");
     }
     return LD_OK;
+}
+
+int enqueue(ld_handle *h, const ld::KParams &kp, const float *disp, const uint8_t *img, ld_lanes *out,
+            bool timed = false)
+{
+    return enqueue_on(h, kp, h->w, disp, img, out, h->stream, timed);
+}
+
+// The workspace seen from frame f0 on: every per-frame array advanced by f0 frames of this call's size.
+ld::Work work_from(const ld::Work &w, const ld::KParams &kp, int f0)
+{
+    const size_t f = f0, W = kp.W, H = kp.H, D = kp.D;
+    ld::Work v = w;
+    v.myT += f * D * H;
+    v.fs += f;
+    v.rows += f * 3 * H;
+    v.path_y += f * D;
+    v.inl_y += f * D;
+    v.ecount += f * H;
+    v.edges += f * H * W * 4;
+    v.vcount += f * H;
+    v.vbins += f * H * W;
+    v.path_x += f * H;
+    v.inl_x += f * H;
+    v.pts += f * 2 * 3 * (size_t)w.pmax;
+    v.npts += f * 2;
+    v.gbt += f * (size_t)w.max_h * ld::vpx_row_bytes(w.max_w);
+    v.M1 += f * H * W;
+    v.HE += f * (size_t)kp.n_starts;
+    return v;
+}
+
+// Two half-batches on the handle's two sub-streams, forked from and joined back to the handle's stream
+// (inside a capture, two concurrent branches of the graph that the GPU interleaves).  Staggering the
+// halves (the second half's gradient kernel after the first's) was slower: a gradient CTA holds 213 KB of
+// shared memory, so the first half's serial kernels waited for SMs.
+int enqueue_split(ld_handle *h, int w, int hh, int n, const float *disp, const uint8_t *img, ld_lanes *out)
+{
+    cudaError_t e = cudaEventRecord(h->fork, h->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "fork");
+    const int n0 = (n + 1) / 2;
+    for (int k = 0; k < 2; ++k) {
+        const int f0 = k ? n0 : 0, nk = k ? n - n0 : n0;
+        const ld::KParams kp = make_kparams(h, w, hh, nk);
+        const ld::KParams kfull = make_kparams(h, w, hh, n);
+        if ((e = cudaStreamWaitEvent(h->sub[k], h->fork, 0)) != cudaSuccess)
+            return cuda_fail(h, e, "fork wait");
+        const size_t px = (size_t)f0 * w * hh;
+        const int rc = enqueue_on(h, kp, work_from(h->w, kfull, f0), disp + px, img + px, out + f0, h->sub[k], false);
+        if (rc != LD_OK)
+            return rc;
+        if ((e = cudaEventRecord(h->join[k], h->sub[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(h->stream, h->join[k], 0)) != cudaSuccess)
+            return cuda_fail(h, e, "join");
+    }
+    return LD_OK;
+}
+
+void release_sync_objects(ld_handle *h)
+{
+    for (int k = 0; k <= kLaunches; ++k)
+        if (h->ev[k])
+            cudaEventDestroy(h->ev[k]);
+    if (h->fork)
+        cudaEventDestroy(h->fork);
+
+    for (int k = 0; k < 2; ++k) {
+        if (h->join[k])
+            cudaEventDestroy(h->join[k]);
+        if (h->sub[k])
+            cudaStreamDestroy(h->sub[k]);
+    }
 }
 
 int check_call(ld_handle *h, const void *disp, const void *img, int w, int hh, int n, const void *out)
@@ -419,11 +497,17 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     }
     for (int k = 0; k <= kLaunches && e == cudaSuccess; ++k)
         e = cudaEventCreate(&h->ev[k]);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&h->sub[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&h->join[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
-        cuda_fail(nullptr, e, "event creation");
-        for (int k = 0; k <= kLaunches; ++k)
-            if (h->ev[k])
-                cudaEventDestroy(h->ev[k]);
+        cuda_fail(nullptr, e, "stream and event creation");
+        release_sync_objects(h);
         cudaFree(h->ws);
         delete h;
         return LD_E_CUDA;
@@ -459,7 +543,8 @@ int ld_detect(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, in
     e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess)
         return cuda_fail(h, e, "begin capture");
-    rc = enqueue(h, kp, disp, img, out_lanes);
+    rc = n_frames >= kSplitMin ? enqueue_split(h, w, hh, n_frames, disp, img, out_lanes)
+                               : enqueue(h, kp, disp, img, out_lanes);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(h->stream, &graph);
     if (rc != LD_OK) {
@@ -636,9 +721,7 @@ void ld_destroy(ld_handle *h)
     for (GraphSlot &g : h->graphs)
         if (g.exec)
             cudaGraphExecDestroy(g.exec);
-    for (int k = 0; k <= kLaunches; ++k)
-        if (h->ev[k])
-            cudaEventDestroy(h->ev[k]);
+    release_sync_objects(h);
     cudaFree(h->ws);
     delete h;
 }
