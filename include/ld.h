@@ -122,6 +122,17 @@ int ld_detect(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, in
               ld_lanes *out_lanes);
 
 /*
+ * Tune the launch shapes for frames of w x h_px: rows per CTA of the v-disparity, gradient and M_1 kernels
+ * (the tiled, shared-memory-bound ones), each chosen among a few candidates by timing eager detections of
+ * the caller's frames (DEVICE pointers, as ld_detect; out_lanes receives their results).  The choice is
+ * kept in the handle and used by every later call with the same w and h_px; results never depend on it
+ * (tiles only partition the same work).  The paper has no counterpart.  chosen (may be NULL) receives the
+ * three row counts.  The call synchronises the handle's stream.  Errors as ld_detect.
+ */
+int ld_tune(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t h_px, int32_t n_frames,
+            ld_lanes *out_lanes, int32_t *chosen);
+
+/*
  * Same as ld_detect with HOST buffers: copies the inputs to device staging owned by the handle, runs the
  * path, copies the results to out_lanes (host, n_frames entries) and waits for the stream.  Page-locked
  * (pinned) inputs give the fastest copies.  Errors as ld_detect.

@@ -438,16 +438,15 @@ size_t grad_smem(int W, int R, int n_cls)
     return s + 16;
 }
 
-// Rows per CTA: 28 when that fits the 220 KB shared-memory budget (fewer, taller tiles: less halo and
-// fewer waves over 152 SMs), else 16, else the most that fit (one 1024-thread CTA per SM either way).
+// Rows per CTA: the tuned value when set, else 28 when that fits the 220 KB shared-memory budget (fewer,
+// taller tiles: less halo and fewer waves over 152 SMs), else 16; in every case reduced until it fits (one
+// 1024-thread CTA per SM).
+constexpr size_t kGradBudget = 220 * 1024;
 template <int RHO>
-int grad_rows(int W, int n_cls)
+int grad_rows(int W, int n_cls, int tuned)
 {
-    constexpr size_t kBudget = 220 * 1024;
-    if (grad_smem<RHO>(W, 28, n_cls) <= kBudget)
-        return 28;
-    int R = 16;
-    while (R > 1 && grad_smem<RHO>(W, R, n_cls) > kBudget)
+    int R = tuned > 0 ? tuned : grad_smem<RHO>(W, 28, n_cls) <= kGradBudget ? 28 : 16;
+    while (R > 1 && grad_smem<RHO>(W, R, n_cls) > kGradBudget)
         --R;
     return R;
 }
@@ -455,7 +454,7 @@ int grad_rows(int W, int n_cls)
 template <int RHO>
 cudaError_t launch_grad_t(const KParams &kp, const Work &w, const float *disp, const uint8_t *img, cudaStream_t s)
 {
-    const int R = grad_rows<RHO>(kp.W, kp.n_cls);
+    const int R = grad_rows<RHO>(kp.W, kp.n_cls, kp.tile_grad);
     const size_t smem = grad_smem<RHO>(kp.W, R, kp.n_cls);
     dim3 grid((kp.H + R - 1) / R, kp.n_frames);
     k_grad<RHO><<<grid, kThreads, smem, s>>>(kp, w, disp, img, R);

@@ -38,17 +38,23 @@ struct M1Layout {
     int R, Wc;  // M_1 rows per CTA, columns of D per shared-memory chunk
 };
 
-inline M1Layout m1_layout(int W, int vs)
+// Rows per CTA: the tuned value (1 .. 16) when set, else the most of 16 .. 8 that fit one 110 KB chunk of
+// the full width (two CTAs per SM), else 16 with the columns split into chunks.
+inline M1Layout m1_layout(int W, int vs, int tuned)
 {
-    const size_t budget = 110 * 1024;  // two CTAs per SM
+    const size_t budget = 110 * 1024;
     M1Layout L;
-    for (L.R = 16; L.R >= 8; --L.R)
-        if ((size_t)(L.R + 2 + 2 * vs) * W * sizeof(int32_t) <= budget) {
-            L.Wc = W;
-            return L;
-        }
-    L.R = 16;
-    L.Wc = (int)(budget / ((size_t)(L.R + 2 + 2 * vs) * sizeof(int32_t))) & ~31;
+    if (tuned > 0) {
+        L.R = tuned < 16 ? tuned : 16;
+    } else {
+        for (L.R = 16; L.R >= 8; --L.R)
+            if ((size_t)(L.R + 2 + 2 * vs) * W * sizeof(int32_t) <= budget)
+                break;
+        if (L.R < 8)
+            L.R = 16;
+    }
+    const size_t row_bytes = (size_t)(L.R + 2 + 2 * vs) * sizeof(int32_t);
+    L.Wc = (size_t)W * row_bytes <= budget ? W : (int)(budget / row_bytes) & ~31;
     return L;
 }
 
@@ -352,7 +358,7 @@ cudaError_t setup_lpv(int smem_optin)
 
 cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s)
 {
-    const M1Layout L = m1_layout(kp.W, kp.box_vs);
+    const M1Layout L = m1_layout(kp.W, kp.box_vs, kp.tile_m1);
     const size_t smem = sizeof(int32_t) * (size_t)(L.R + 2 + 2 * kp.box_vs) * L.Wc;
     dim3 grid((kp.H + L.R - 1) / L.R, kp.n_frames);
     k_m1<<<grid, kM1Threads, smem, s>>>(kp, w, L.R, L.Wc);

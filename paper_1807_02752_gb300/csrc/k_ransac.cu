@@ -22,7 +22,9 @@
 //     singular).
 //
 // GB300 mapping: every THREAD fits one hypothesis in float32 (GB300's FP64 pipe is narrow, so float64 is
-// kept to the one final solve per round loop), then every WARP counts the inliers of one hypothesis at a time.
+// kept to the final solve); inlier counts put consecutive hypotheses on consecutive lanes against the same
+// point (broadcast loads, independent iterations); the final fit reduces each exact int128 sum on its own
+// warp and solves the normal equations on one warp, one column per lane.
 #include "ld_internal.cuh"
 
 namespace ld {

@@ -3,7 +3,7 @@
 // A pixel counts when its disparity l is finite and > 0 (0 marks pixels invalidated by the left-right
 // check, Eq. 10); its bin is floor(l + 0.5) in float32 and bins >= D are dropped.
 //
-// One CTA covers kRows consecutive rows of one frame.  Those rows are one contiguous range of memory, so
+// One CTA covers kRows consecutive rows of one frame (16 unless ld_tune chose another count).  Those rows are one contiguous range of memory, so
 // the CTA streams it as 16-byte loads of the aligned chunks inside it (several in flight per thread) plus
 // single loads of its head and tail; each warp streams one contiguous span.  Counts go to a shared-memory
 // histogram per row.  Disparity is locally smooth (a road row holds one or two bins, an obstacle one), so
@@ -17,7 +17,7 @@
 namespace ld {
 
 namespace {
-constexpr int kRows = 16;
+constexpr int kRowsDefault = 16;  // rows per CTA unless tuned
 constexpr int kThreads = 256;
 constexpr int kUnroll = 4;  // 16-byte loads in flight per thread
 
@@ -29,7 +29,7 @@ __device__ __forceinline__ void red_add_if(bool p, uint32_t a, int v)
 }
 
 __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *__restrict__ myT,
-                                                    const float *__restrict__ disp)
+                                                    const float *__restrict__ disp, int kRows)
 {
     extern __shared__ int32_t hist[];  // [kRows][D]
     const int W = kp.W, H = kp.H, D = kp.D;
@@ -108,11 +108,21 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
 }
 }  // namespace
 
+// Rows per CTA: the tuned value when set, kept within 48 KB of histogram shared memory.
+int vdisp_rows(const KParams &kp)
+{
+    int r = kp.tile_vdisp > 0 ? kp.tile_vdisp : kRowsDefault;
+    while (r > 1 && sizeof(int32_t) * (size_t)r * kp.D > 48 * 1024)
+        r >>= 1;
+    return r;
+}
+
 cudaError_t launch_vdisp(const KParams &kp, const Work &w, const float *disp, cudaStream_t s)
 {
+    const int kRows = vdisp_rows(kp);
     dim3 grid((kp.H + kRows - 1) / kRows, kp.n_frames);
     const size_t smem = sizeof(int32_t) * kRows * kp.D;
-    k_vdisp<<<grid, kThreads, smem, s>>>(kp, w.myT, disp);
+    k_vdisp<<<grid, kThreads, smem, s>>>(kp, w.myT, disp, kRows);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ struct ld_handle {
     // two half-batches forked onto their own streams inside a captured call (joined before it ends)
     cudaStream_t sub[2] = {};
     cudaEvent_t fork = nullptr, join[2] = {};
+    // tile sizes chosen by ld_tune for frames of tile_w x tile_h (0: the built-in rules)
+    int tile_w = 0, tile_h = 0, tile[3] = {0, 0, 0};
     std::string err;
 };
 
@@ -200,6 +202,10 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
             }
     }
     k.seg_rows = ld::vpx_seg_rows(k, (size_t)h->smem_optin - 1024);
+    const bool tuned = W == h->tile_w && H == h->tile_h;
+    k.tile_vdisp = tuned ? h->tile[0] : 0;
+    k.tile_grad = tuned ? h->tile[1] : 0;
+    k.tile_m1 = tuned ? h->tile[2] : 0;
     return k;
 }
 
@@ -594,6 +600,56 @@ int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t
     for (int k = 0; k < kLaunches && e == cudaSuccess; ++k)
         e = cudaEventElapsedTime(&ms_out[k], h->ev[k], h->ev[k + 1]);
     return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "event timing");
+}
+
+int ld_tune(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+            ld_lanes *out_lanes, int32_t *chosen)
+{
+    int rc = check_call(h, disp, img, w, hh, n_frames, out_lanes);
+    if (rc != LD_OK)
+        return rc;
+    // candidates per tuned kernel (launch index in the sequence, rows per CTA); the launchers reduce a
+    // value that does not fit their shared-memory budget
+    static const int kTuned[3] = {0, 3, 6};  // k_vdisp, k_grad, k_m1
+    static const std::vector<int> kCand[3] = {{8, 16, 32}, {12, 16, 20, 24, 28}, {8, 12, 14, 16}};
+    constexpr int kReps = 3;
+    h->tile_w = w;
+    h->tile_h = hh;
+    for (int t = 0; t < 3; ++t)
+        h->tile[t] = 0;
+    float ms[kLaunches];
+    for (int t = 0; t < 3; ++t) {
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int c : kCand[t]) {
+            h->tile[t] = c;
+            float m = 1e30f;
+            for (int r = 0; r < kReps; ++r) {
+                rc = ld_detect_timed(h, disp, img, w, hh, n_frames, out_lanes, ms);
+                if (rc != LD_OK) {
+                    h->tile_w = h->tile_h = 0;
+                    return rc;
+                }
+                m = ms[kTuned[t]] < m ? ms[kTuned[t]] : m;
+            }
+            if (m < best_ms) {
+                best_ms = m;
+                best = c;
+            }
+        }
+        h->tile[t] = best;
+    }
+    // launch shapes changed: drop the captured graphs
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    for (GraphSlot &g : h->graphs)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g = GraphSlot();
+        }
+    if (chosen)
+        for (int t = 0; t < 3; ++t)
+            chosen[t] = h->tile[t];
+    return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "tune sync");
 }
 
 int ld_detect_host(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,

@@ -15,7 +15,7 @@ namespace ld {
 
 constexpr int kMaxHyps = 256;
 constexpr int kWgEntries = 16385;     // Eq. 23 table: sin(dtheta) in [0, 1/2] in steps of 2^-15
-constexpr int kWrEntries = 768;       // range-weight table indexed by q - c + 256 (entries >= 512 are 0)
+constexpr int kWrEntries = 768;       // Q15 range weight of dI at index 256 + dI (symmetric; entries >= 512 are 0)
 constexpr int kSentinel = 511;        // image value marking taps outside the frame
 
 // Per-launch constants, passed by value (they live in the kernel-parameter constant bank).
@@ -36,6 +36,7 @@ struct KParams {
     uint32_t key0, key1;
     int32_t centre, e;                 // polynomial basis tau = (v - centre) / 2^e
     int32_t seg_rows;                  // rows of DP backtrack held in shared memory by the V_px kernel
+    int32_t tile_vdisp, tile_grad, tile_m1;  // rows per CTA chosen by ld_tune (0: the built-in rule)
     int32_t vote_cap;                  // votes per frame the V_px kernel stages in shared memory
     uint16_t ws[121];                  // Eq. 16 spatial weights, Q15 (up to 32768), (2 rho + 1)^2 used
     // Taps at equal distance share one weight table in the gradient kernel.  Classes are the ranks of

@@ -103,6 +103,8 @@ def load():
     L.ld_destroy.restype = None
     L.ld_road_path_static.argtypes = [P, p, i32, i32, i32, p, p]
     L.ld_road_path_static.restype = C.c_int
+    L.ld_tune.argtypes = [p, p, p, i32, i32, i32, p, p]
+    L.ld_tune.restype = C.c_int
     L.ld_server_create.argtypes = [P, C.POINTER(ServerConfig), C.POINTER(p)]
     L.ld_server_create.restype = C.c_int
     L.ld_server_submit.argtypes = [p, i32, p, p, i32, i32, C.c_uint64]
@@ -125,7 +127,7 @@ def load():
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
             "ld_debug_get", "ld_debug_size", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
-            "ld_destroy", "ld_road_path_static", "ld_server_create", "ld_server_submit", "ld_server_poll",
+            "ld_destroy", "ld_road_path_static", "ld_tune", "ld_server_create", "ld_server_submit", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy"]
 
@@ -237,6 +239,16 @@ class Detector:
         self._check(self.L.ld_detect_timed(self.h, disp.data_ptr(), img.data_ptr(), W, H, n, out.data_ptr(),
                                            ms.ctypes.data))
         return ms
+
+    def tune(self, disp, img, out=None):
+        """Time candidate tile shapes on these frames (device tensors) and keep the fastest for their size.
+        Returns the chosen rows per CTA of the v-disparity, gradient and M_1 kernels."""
+        n, H, W = disp.shape
+        out = self.alloc_lanes(n) if out is None else out
+        chosen = np.zeros(3, np.int32)
+        self._check(self.L.ld_tune(self.h, disp.data_ptr(), img.data_ptr(), W, H, n, out.data_ptr(),
+                                   chosen.ctypes.data))
+        return {"vdisp_rows": int(chosen[0]), "grad_rows": int(chosen[1]), "m1_rows": int(chosen[2])}
 
     def detect_host_ptr(self, disp_ptr: int, img_ptr: int, W: int, H: int, n: int, res: np.ndarray):
         self._check(self.L.ld_detect_host(self.h, disp_ptr, img_ptr, W, H, n, res.ctypes.data))

@@ -177,3 +177,32 @@ def test_argument_errors(torch_cuda):
     assert L.ld_debug_get(det.h, 5, ld.STAGE_HE, buf.ctypes.data, 16) == ld.E_ARG
     assert L.ld_debug_get(det.h, 0, 99, buf.ctypes.data, 16) == ld.E_ARG
     assert L.ld_debug_get(det.h, 0, ld.STAGE_HE, buf.ctypes.data, 16) == ld.E_ARG  # wrong size
+
+
+def test_tuning_keeps_results(torch_cuda):
+    """ld_tune only changes launch shapes: lanes and intermediate stages stay identical, before and after
+    (the latter through a newly captured graph)."""
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS["single_1242x375"]
+    disp, img, _ = scenes.make_batch(cfg, 3, first_frame=40)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    det = ld.Detector(cfg.width, cfg.height, 3, p)
+    d = torch.from_numpy(disp).cuda()
+    i = torch.from_numpy(img).cuda()
+    stages = (ld.STAGE_VDISP, ld.STAGE_ROWS, ld.STAGE_M1, ld.STAGE_HE)
+
+    def run():
+        out = det.detect(d, i)
+        torch.cuda.synchronize()
+        res = det.lanes(out).tobytes()
+        dumps = [det.debug(f, st, cfg.width, cfg.height) for f in range(3) for st in stages]
+        return res, dumps
+
+    before = run()
+    chosen = det.tune(d, i)
+    assert chosen["vdisp_rows"] in (8, 16, 32) and chosen["grad_rows"] in (12, 16, 20, 24, 28)
+    assert chosen["m1_rows"] in (8, 12, 14, 16)
+    after = run()
+    assert before[0] == after[0]
+    for a, b in zip(before[1], after[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
