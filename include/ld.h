@@ -47,6 +47,7 @@ extern "C" {
 #define LD_F_CAP_X 8       /* V_px RANSAC stopped at its round cap */
 #define LD_F_DEGEN_X 16    /* V_px fit impossible */
 #define LD_F_NO_LANES 32   /* no lane passed validation */
+#define LD_F_FALLBACK 64   /* learned proposal: no lane among the proposed starts; the exhaustive search ran */
 
 /*
  * Parameters: every constant of the method, named after the paper's symbols.  ld_params_default() fills
@@ -280,6 +281,75 @@ const char *ld_server_last_error(const ld_server *s);
 
 /* Wait for the work in flight and release everything.  NULL is ignored. */
 void ld_server_destroy(ld_server *s);
+
+/*
+ * Learned lane-position proposal.  The paper evaluates the energy (Eq. 24-25) of the track started at
+ * every bottom-row position and selects lanes among its minima (Alg. 7); it has no learned component.
+ * This form ranks the starts first with a small convolutional network and evaluates exact energies only
+ * on the best-ranked ones; the exhaustive search remains the fallback.
+ *
+ *   input    x(i, j) = sum of |G_x w_g| (the Q12 weighted gradient of Eq. 23) over the 4x4 pixel block at
+ *            rows 4i.., columns 4j.. (mh = ceil(h/4) by mw = ceil(w/4) cells), fed as bf16(x 2^-22);
+ *   network  four 3x3 convolutions (zero padding, channels 1-16-32-32-16, bias, ReLU) and a 1x1 head
+ *            16 -> 1 giving a logit z per cell: sigmoid(z) is the chance that a lane crosses the cell, its
+ *            rows the per-row lane-position heatmap.  Products in bf16, sums in FP32, activations stored
+ *            as bf16; trained with a weighted logistic loss (positive weight 10) and Adam;
+ *   ranking  coarse start c covers the starts 4c .. 4c+3; its score sums z along the Eq. 25 track taken
+ *            in steps of four rows from u = (4c - S0) + 1.5 on the bottom row;
+ *   search   the top_k coarse starts give candidate starts; each candidate and its neighbours get the
+ *            exact energy; lanes are the Alg. 7 minima among the candidates (threshold from the smallest
+ *            evaluated energy).  A frame where that finds no lane runs the exhaustive search and is
+ *            flagged LD_F_FALLBACK.
+ *
+ * Parameters are a flat float32 vector of LD_NET_PARAMS values: for each convolution W[co][ci][3][3] then
+ * b[co]; then the head's w[16] and b.  A network is created for a detector handle and uses its stream and
+ * its largest frame and batch; it owns its activations (about 5 KB per cell of the largest batch while
+ * training, 2.5 KB otherwise), its master weights and Adam state.  All buffer arguments are DEVICE
+ * pointers owned by the caller; calls enqueue on the handle's stream and return without waiting.
+ * Errors: LD_E_ARG, LD_E_NOMEM, LD_E_STATE (training call on an inference network), LD_E_CUDA.
+ */
+#define LD_NET_PARAMS 18689
+#define LD_NET_TOPK_MAX 256
+typedef struct ld_net ld_net;
+
+enum {
+    LD_NET_STAGE_XSUM = 1,     /* int32 [mh][mw]  block sums x of the last learned detection */
+    LD_NET_STAGE_LOGITS = 2,   /* float [mh][mw]  logits z used by the last learned detection */
+    LD_NET_STAGE_SCORES = 3,   /* float [ceil(n_starts / 4)] coarse-start scores */
+    LD_NET_STAGE_CFLAG = 4,    /* uint8 [n_starts] bit 0 candidate, bit 1 energy evaluated */
+};
+
+int32_t ld_net_param_count(void);
+/* training != 0 also allocates what the backward pass needs. */
+int ld_net_create(ld_handle *h, int32_t training, ld_net **out);
+/* Copy LD_NET_PARAMS floats in as the master weights; resets the Adam moments and step count. */
+int ld_net_set_params(ld_net *net, const float *params);
+int ld_net_get_params(ld_net *net, float *params);
+/* logits[n][mh][mw] of the block sums xsum[n][mh][mw] of frames of w x h pixels. */
+int ld_net_forward(ld_net *net, const int32_t *xsum, int32_t w, int32_t h_px, int32_t n_frames, float *logits);
+/* Gradient of the mean loss over n frames (grad: LD_NET_PARAMS floats) and the loss (1 float); labels are
+ * uint8 [n][mh][mw] (nonzero = lane cell).  Training networks only. */
+int ld_net_grad(ld_net *net, const int32_t *xsum, const uint8_t *labels, int32_t w, int32_t h_px, int32_t n_frames,
+                float *grad, float *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) with the given gradient. */
+int ld_net_apply_grad(ld_net *net, const float *grad, float lr);
+/* ld_net_grad followed by ld_net_apply_grad; loss may be NULL. */
+int ld_net_train_step(ld_net *net, const int32_t *xsum, const uint8_t *labels, int32_t w, int32_t h_px,
+                      int32_t n_frames, float lr, float *loss);
+/* Training pairs from frames: the plain method's lanes (lanes_out, may be NULL), the block sums
+ * (xsum_out [n][mh][mw]) and the labels (labels_out [n][mh][mw]: cells crossed by the Eq. 25 tracks of the
+ * selected lanes on the road rows). */
+int ld_make_training_pairs(ld_net *net, const float *disp, const uint8_t *img, int32_t w, int32_t h_px,
+                           int32_t n_frames, int32_t *xsum_out, uint8_t *labels_out, ld_lanes *lanes_out);
+/* The learned form of ld_detect.  logits == NULL runs the network; otherwise logits[n][mh][mw] are used
+ * as given.  top_k in [1, LD_NET_TOPK_MAX]. */
+int ld_detect_learned(ld_net *net, const float *logits, const float *disp, const uint8_t *img, int32_t w,
+                      int32_t h_px, int32_t n_frames, int32_t top_k, ld_lanes *out_lanes);
+/* Intermediate results of the last learned detection (synchronises the stream), as ld_debug_get. */
+size_t ld_net_debug_size(ld_net *net, int32_t stage);
+int ld_net_debug_get(ld_net *net, int32_t frame, int32_t stage, void *host_dst, size_t bytes);
+const char *ld_net_last_error(const ld_net *net);
+void ld_net_destroy(ld_net *net);
 
 /* Message of the last error on h (or of the last failed ld_create when h is NULL). */
 const char *ld_last_error(const ld_handle *h);

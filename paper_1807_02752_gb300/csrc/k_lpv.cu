@@ -7,6 +7,8 @@
 //             row up to v_top and its energy E = M_1(round(u_v), v) + lambda_g E (Eq. 24).
 //   k_select  strict interior local minima of H below t = ceil(thr min H), then suppression of nearby
 //             minima in increasing (energy, position) order; fills ld_lanes.
+//   Both also serve the learned proposal (k_net.cu): energies of listed starts only, selection among
+//   candidate starts, and the exhaustive fallback for the frames where that selected nothing.
 //
 // w_g reading: theta_e is the direction of the edge (the Sobel gradient turned by 90 degrees), theta_Vp
 // the direction from the pixel to V_p(v); lines are undirected, so the angle is taken in [0, pi/2] through
@@ -140,6 +142,10 @@ __global__ void __launch_bounds__(kM1Threads, 2) k_m1(const KParams kp, const Wo
             const int g = gx * wg;
             if (g == 0)
                 continue;
+            // input map of the learned proposal: the CTA that owns row v and the chunk that holds column u
+            // add |g| to the edge's 4x4 block (integer: the sum does not depend on the order)
+            if (w.xsum && v >= r0 && v < r0 + nr && u >= c0 && u < c1)
+                atomicAdd(w.xsum + ((size_t)f * ((H + 3) >> 2) + (v >> 2)) * ((W + 3) >> 2) + (u >> 2), abs(g));
             int32_t *drow = dd + (size_t)(v - d0) * cw;  // column t of the frame at drow[t - c0]
             const int tgt[4] = {u - nu - 1, u - nu, u + nu, u + nu + 1};
 #pragma unroll
@@ -176,13 +182,21 @@ __global__ void __launch_bounds__(kM1Threads, 2) k_m1(const KParams kp, const Wo
     }
 }
 
-__global__ void __launch_bounds__(kEnThreads, 8) k_energy(const KParams kp, const Work w)
+// MODE 0: every start of every frame; 1: the starts listed per frame (learned proposal); 2: every start of
+// the frames flagged LD_F_FALLBACK (the proposal selected no lane there).
+template <int MODE>
+__global__ void __launch_bounds__(kEnThreads, 8) k_energy(const KParams kp, const Work w, const int32_t *elist,
+                                                          const int32_t *ecnt, int ecap)
 {
     extern __shared__ float vrow[];   // [2][H]: V_px, V_py
     const int W = kp.W, H = kp.H;
     const int f = blockIdx.y;
     const FrameState &fs = w.fs[f];
     if (fs.flags & LD_F_NO_LANES)
+        return;
+    if (MODE == 2 && !(fs.flags & LD_F_FALLBACK))
+        return;
+    if (MODE == 1 && blockIdx.x * kEnThreads >= ecnt[f])
         return;
     const int vtop = fs.v_top, vmax = H - 1;
     const float *rows = w.rows + (size_t)f * 3 * H;
@@ -191,7 +205,12 @@ __global__ void __launch_bounds__(kEnThreads, 8) k_energy(const KParams kp, cons
         vrow[H + v] = rows[H + v];
     }
     __syncthreads();
-    const int i = blockIdx.x * kEnThreads + threadIdx.x;
+    int i = blockIdx.x * kEnThreads + threadIdx.x;
+    if (MODE == 1) {
+        if (i >= ecnt[f])
+            return;
+        i = elist[(size_t)f * ecap + i];
+    }
     if (i >= kp.n_starts)
         return;
     const int32_t *M1 = w.M1 + (size_t)f * H * W;
@@ -239,7 +258,10 @@ __global__ void __launch_bounds__(kEnThreads, 8) k_energy(const KParams kp, cons
     w.HE[(size_t)f * kp.n_starts + i] = (int64_t)E;
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const Work w, ld_lanes *out)
+// mode 0: every start; 1: minima only at candidate starts (cflag bit 0), minimum over the evaluated ones
+// (bit 1), and a frame without a lane is flagged LD_F_FALLBACK; 2: the flagged frames only, every start.
+__global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const Work w, ld_lanes *out,
+                                                        const uint8_t *cflag, int mode)
 {
     extern __shared__ int cand[];     // [n_starts / 2 + 2] candidate positions, then their sorted order
     __shared__ long long red[kSelThreads / 32];
@@ -249,8 +271,11 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const 
     const int f = blockIdx.x, ns = kp.n_starts;
     const int tid = threadIdx.x;
     const FrameState fs = w.fs[f];
+    if (mode == 2 && !(fs.flags & LD_F_FALLBACK))
+        return;
     int flags = fs.flags;
     const int64_t *he = w.HE + (size_t)f * ns;
+    const uint8_t *cf = mode == 1 ? cflag + (size_t)f * ns : nullptr;
     if (tid == 0) {
         ncand = 0;
         nacc = 0;
@@ -259,7 +284,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const 
     if (!(flags & LD_F_NO_LANES)) {
         long long m = 0x7fffffffffffffffLL;
         for (int i = tid; i < ns; i += kSelThreads)
-            m = he[i] < m ? (long long)he[i] : m;
+            if (!cf || (cf[i] & 2))
+                m = he[i] < m ? (long long)he[i] : m;
         for (int d = 16; d > 0; d >>= 1) {
             const long long o = __shfl_down_sync(0xffffffffu, m, d);
             m = o < m ? o : m;
@@ -276,6 +302,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const 
             const long long t = -(((-mn) * (long long)kp.thr_num) / (long long)kp.thr_den);
             int *pos = cand;
             for (int i = 1 + tid; i < ns - 1; i += kSelThreads) {
+                if (cf && !(cf[i] & 1))
+                    continue;
                 const long long h = he[i];
                 if (h < he[i - 1] && h < he[i + 1] && h < t)
                     pos[atomicAdd(&ncand, 1)] = i;
@@ -323,6 +351,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const 
         }
     }
     __syncthreads();
+    if (mode == 1 && tid == 0 && nacc == 0 && !(fs.flags & LD_F_NO_LANES))
+        w.fs[f].flags = fs.flags | LD_F_FALLBACK;
     if (tid == 0) {
         ld_lanes L;
         const int na = nacc;
@@ -368,15 +398,46 @@ cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s)
 cudaError_t launch_energy(const KParams &kp, const Work &w, cudaStream_t s)
 {
     dim3 grid((kp.n_starts + kEnThreads - 1) / kEnThreads, kp.n_frames);
-    k_energy<<<grid, kEnThreads, sizeof(float) * 2 * kp.H, s>>>(kp, w);
+    k_energy<0><<<grid, kEnThreads, sizeof(float) * 2 * kp.H, s>>>(kp, w, nullptr, nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_list(const KParams &kp, const Work &w, const int32_t *elist, const int32_t *ecnt, int ecap,
+                               cudaStream_t s)
+{
+    dim3 grid((ecap + kEnThreads - 1) / kEnThreads, kp.n_frames);
+    k_energy<1><<<grid, kEnThreads, sizeof(float) * 2 * kp.H, s>>>(kp, w, elist, ecnt, ecap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_fallback(const KParams &kp, const Work &w, cudaStream_t s)
+{
+    dim3 grid((kp.n_starts + kEnThreads - 1) / kEnThreads, kp.n_frames);
+    k_energy<2><<<grid, kEnThreads, sizeof(float) * 2 * kp.H, s>>>(kp, w, nullptr, nullptr, 0);
+    return cudaGetLastError();
+}
+
+static cudaError_t select_mode(const KParams &kp, const Work &w, ld_lanes *out, const uint8_t *cflag, int mode,
+                               cudaStream_t s)
+{
+    const size_t smem = sizeof(int) * (size_t)(kp.n_starts + 4);
+    k_select<<<kp.n_frames, kSelThreads, smem, s>>>(kp, w, out, cflag, mode);
     return cudaGetLastError();
 }
 
 cudaError_t launch_select(const KParams &kp, const Work &w, ld_lanes *out, cudaStream_t s)
 {
-    const size_t smem = sizeof(int) * (size_t)(kp.n_starts + 4);
-    k_select<<<kp.n_frames, kSelThreads, smem, s>>>(kp, w, out);
-    return cudaGetLastError();
+    return select_mode(kp, w, out, nullptr, 0, s);
+}
+
+cudaError_t launch_select_set(const KParams &kp, const Work &w, const uint8_t *cflag, ld_lanes *out, cudaStream_t s)
+{
+    return select_mode(kp, w, out, cflag, 1, s);
+}
+
+cudaError_t launch_select_fallback(const KParams &kp, const Work &w, ld_lanes *out, cudaStream_t s)
+{
+    return select_mode(kp, w, out, nullptr, 2, s);
 }
 
 }  // namespace ld

@@ -1,0 +1,845 @@
+// Learned lane-position proposal: a small BF16 convolutional network on the 4x-downsampled map of
+// |G_x w_g| (Eq. 23) ranks the bottom-row starts of Eq. 24-25, and exact energies are evaluated only on
+// the best-ranked ones (the exhaustive search of Alg. 7 stays as the fallback).  The paper has no such
+// network; the form follows a stated configuration: 3x3 convolutions with 1-16-32-32-16 channels, BF16
+// operands with FP32 accumulation, a per-cell logit z (the per-row heatmap is sigmoid(z)), top-k = 32.
+//
+//   k_conv1     layer 1 (one input channel) from the integer block sums; writes the bf16 input and A1
+//   k_conv      layers 2-4 as implicit GEMMs on the tensor cores (mma.sync m16n8k16, bf16 -> f32):
+//               an 8 x 16-cell output tile per CTA, its 10 x 18 halo in shared memory, one m16 tile per
+//               tile row, K = 9 taps x C_in; epilogues: bias + ReLU (+ the 1x1 head), or the backward
+//               data pass (transposed, flipped weights) times the ReLU mask of the layer below
+//   k_wgrad     weight and bias gradients of a layer: M = C_out, N = 9 C_in + 1 (a column of ones gives
+//               the bias), K = cells; per-CTA partial sums, then k_wreduce adds them in a fixed order
+//   k_loss      head, weighted logistic loss, dz, dS_4 and the head's gradient partials
+//   k_adam      Adam (Kingma & Ba, Algorithm 1) on the FP32 master weights, then the bf16 operand copies
+//   k_labels    training targets: cells crossed by the Eq. 25 tracks of the selected lanes
+//   k_score     coarse-start scores: z summed along the Eq. 25 track taken in steps of four rows
+//   k_topk      the k best coarse starts of a frame -> candidate and evaluated starts
+//
+// Data layout: cell maps are [n][mh][mw] with mh = ceil(H/4), mw = ceil(W/4); activations are bf16
+// [n][mh][mw][C] (channels innermost, 32 or 64 bytes per cell).  Weights: W_l[co][tap][ci] (k = tap C_in
+// + ci) for the forward pass and W_l^T[ci][8 - tap][co] for the backward data pass.
+#include <cuda_bf16.h>
+
+#include "ld_internal.cuh"
+#include "ld_net.cuh"
+
+namespace ld {
+
+namespace {
+
+constexpr int kTileR = 8, kTileC = 16;              // output cells per CTA tile
+constexpr int kHaloR = kTileR + 2, kHaloC = kTileC + 2;
+constexpr int kConvThreads = 128;                   // 4 warps, two tile rows (two m16 tiles) each
+constexpr int kCellThreads = 256;
+constexpr float kInScale = 2.384185791015625e-07f;  // 2^-22
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_raw(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// network input of one cell: bf16(f32(sum) 2^-22), as a float
+__device__ __forceinline__ float cell_input(int32_t s)
+{
+    return __bfloat162float(__float2bfloat16_rn(__fmul_rn(__int2float_rn(s), kInScale)));
+}
+
+// ---------------------------------------------------------------------------------------------------
+// layer 1: one input channel, K = 9, direct FMA per cell
+// ---------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCellThreads) k_conv1(const NetArgs a, const int32_t *xsum, int n)
+{
+    __shared__ float wsm[16 * 9 + 16];
+    for (int i = threadIdx.x; i < 16 * 9; i += kCellThreads)
+        wsm[i] = __bfloat162float(a.wf[0][i]);   // [co][tap]
+    for (int i = threadIdx.x; i < 16; i += kCellThreads)
+        wsm[144 + i] = a.bias[0][i];
+    __syncthreads();
+    const int mh = a.mh, mw = a.mw;
+    const long long cells = (long long)n * mh * mw;
+    for (long long p = blockIdx.x * (long long)kCellThreads + threadIdx.x; p < cells;
+         p += (long long)gridDim.x * kCellThreads) {
+        const int x = (int)(p % mw);
+        const int y = (int)((p / mw) % mh);
+        const long long fb = p - (long long)y * mw - x;   // first cell of the frame
+        float in[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+            in[t] = (yy >= 0 && yy < mh && xx >= 0 && xx < mw) ? cell_input(__ldg(xsum + fb + (long long)yy * mw + xx)) : 0.0f;
+        }
+        if (a.X)
+            a.X[p] = __float2bfloat16_rn(in[4]);
+        uint32_t o[8];
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+            float s0 = wsm[144 + c], s1 = wsm[144 + c + 1];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                s0 = __fmaf_rn(wsm[c * 9 + t], in[t], s0);
+                s1 = __fmaf_rn(wsm[(c + 1) * 9 + t], in[t], s1);
+            }
+            o[c >> 1] = pack2(fmaxf(s0, 0.0f), fmaxf(s1, 0.0f));
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(a.act[0] + p * 16);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// layers 2-4 (and the backward data pass) on the tensor cores
+// ---------------------------------------------------------------------------------------------------
+enum Epi { kEpiRelu = 0, kEpiHead = 1, kEpiMask = 2 };
+
+struct ConvIO {
+    const __nv_bfloat16 *in;     // [n][mh][mw][CIN]
+    const __nv_bfloat16 *wt;     // [COUT][9 CIN]
+    const float *bias;           // [COUT] (kEpiRelu, kEpiHead)
+    __nv_bfloat16 *out;          // [n][mh][mw][COUT] (kEpiHead: may be null)
+    const __nv_bfloat16 *mask;   // [n][mh][mw][COUT] activations whose sign gates the result (kEpiMask)
+    const __nv_bfloat16 *wh;     // [16] head weights (kEpiHead)
+    const float *bh;             // [1]
+    float *z;                    // [n][mh][mw] logits (kEpiHead)
+    int n, mh, mw, tiles_r, tiles_c;
+};
+
+template <int CIN, int COUT>
+struct ConvSmem {
+    static constexpr int CINP = CIN + 8;           // padded cell stride (bank-conflict-free fragment loads)
+    static constexpr int KP = 9 * CIN + 8;         // padded weight row
+    static constexpr int in_elems = kHaloR * kHaloC * CINP;
+    static constexpr int w_elems = COUT * KP;
+    static constexpr size_t bytes = sizeof(__nv_bfloat16) * (size_t)(in_elems + w_elems);
+};
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(kConvThreads) k_conv(const ConvIO io)
+{
+    using S = ConvSmem<CIN, COUT>;
+    constexpr int NT = COUT / 8;
+    extern __shared__ __align__(16) __nv_bfloat16 csm[];
+    __nv_bfloat16 *sin = csm;
+    __nv_bfloat16 *sw = csm + S::in_elems;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    // weights once per CTA: row co holds 9 CIN values (a multiple of 8: 16-byte chunks)
+    for (int i = tid; i < COUT * (9 * CIN / 8); i += kConvThreads) {
+        const int co = i / (9 * CIN / 8), ch = i % (9 * CIN / 8);
+        *reinterpret_cast<uint4 *>(sw + co * S::KP + ch * 8) =
+            __ldg(reinterpret_cast<const uint4 *>(io.wt + (size_t)co * 9 * CIN + ch * 8));
+    }
+    const int mh = io.mh, mw = io.mw;
+    const int per_frame = io.tiles_r * io.tiles_c;
+    const int total = io.n * per_frame;
+    float hw[NT][2];
+    if (EPI == kEpiHead) {
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            hw[nt][0] = __bfloat162float(io.wh[nt * 8 + 2 * t]);
+            hw[nt][1] = __bfloat162float(io.wh[nt * 8 + 2 * t + 1]);
+        }
+    }
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int f = tile / per_frame, rem = tile % per_frame;
+        const int y0 = (rem / io.tiles_c) * kTileR, x0 = (rem % io.tiles_c) * kTileC;
+        __syncthreads();   // previous tile's reads of sin are done (and the weights are in place)
+        constexpr int kChunks = CIN / 8;    // 16-byte chunks per cell
+        for (int i = tid; i < kHaloR * kHaloC * kChunks; i += kConvThreads) {
+            const int cell = i / kChunks, ch = i % kChunks;
+            const int yy = y0 - 1 + cell / kHaloC, xx = x0 - 1 + cell % kHaloC;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (yy >= 0 && yy < mh && xx >= 0 && xx < mw)
+                v = __ldg(reinterpret_cast<const uint4 *>(io.in + (((size_t)f * mh + yy) * mw + xx) * CIN) + ch);
+            *reinterpret_cast<uint4 *>(sin + cell * S::CINP + ch * 8) = v;
+        }
+        __syncthreads();
+        float acc[2][NT][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    acc[mt][nt][q] = 0.0f;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+            for (int kc = 0; kc < CIN / 16; ++kc) {
+                uint32_t af[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const int hp = (2 * warp + mt + dy) * kHaloC + dx;   // halo cell of output column 0
+                    const __nv_bfloat16 *r0 = sin + (hp + g) * S::CINP + kc * 16 + 2 * t;
+                    const __nv_bfloat16 *r1 = sin + (hp + g + 8) * S::CINP + kc * 16 + 2 * t;
+                    af[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
+                    af[mt][1] = *reinterpret_cast<const uint32_t *>(r1);
+                    af[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+                    af[mt][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+                }
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const __nv_bfloat16 *wr = sw + (nt * 8 + g) * S::KP + tap * CIN + kc * 16 + 2 * t;
+                    const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wr);
+                    const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wr + 8);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+                        mma16816(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b0, b1);
+                }
+            }
+        }
+        // epilogue: thread holds, for tile row 2 warp + mt, cells x0 + g (+8) and channels nt 8 + 2t (+1)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int y = y0 + 2 * warp + mt;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int x = x0 + g + 8 * half;
+                const bool in_map = y < mh && x < mw;
+                const size_t cell = ((size_t)f * mh + (y < mh ? y : 0)) * mw + (x < mw ? x : 0);
+                float zpart = 0.0f;
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const int co = nt * 8 + 2 * t;
+                    float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                    if (EPI == kEpiMask) {
+                        if (in_map) {
+                            const uint32_t m = *reinterpret_cast<const uint32_t *>(io.mask + cell * COUT + co);
+                            v0 = bf_lo(m) > 0.0f ? v0 : 0.0f;
+                            v1 = bf_hi(m) > 0.0f ? v1 : 0.0f;
+                            *reinterpret_cast<uint32_t *>(io.out + cell * COUT + co) = pack2(v0, v1);
+                        }
+                    } else {
+                        v0 = fmaxf(__fadd_rn(v0, io.bias[co]), 0.0f);
+                        v1 = fmaxf(__fadd_rn(v1, io.bias[co + 1]), 0.0f);
+                        const uint32_t pk = pack2(v0, v1);
+                        if (in_map && io.out)
+                            *reinterpret_cast<uint32_t *>(io.out + cell * COUT + co) = pk;
+                        if (EPI == kEpiHead)
+                            zpart = __fmaf_rn(hw[nt][1], bf_hi(pk), __fmaf_rn(hw[nt][0], bf_lo(pk), zpart));
+                    }
+                }
+                if (EPI == kEpiHead) {
+                    zpart += __shfl_xor_sync(0xffffffffu, zpart, 1);
+                    zpart += __shfl_xor_sync(0xffffffffu, zpart, 2);
+                    if (t == 0 && in_map)
+                        io.z[cell] = __fadd_rn(zpart, io.bh[0]);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// weight gradients: dW[co][tap][ci] = sum_cells dS[co] A[cell + (tap)][ci]; column 9 CIN holds the bias
+// ---------------------------------------------------------------------------------------------------
+struct WgradIO {
+    const __nv_bfloat16 *dS;     // [n][mh][mw][COUT]
+    const __nv_bfloat16 *A;      // [n][mh][mw][CIN]
+    float *part;                 // [gridDim.x][COUT][9 CIN + 1]
+    int n, mh, mw, tiles_r, tiles_c;
+};
+
+template <int CIN, int COUT>
+struct WgradShape {
+    static constexpr int NCOL = 9 * CIN + 1;
+    static constexpr int NTT = (NCOL + 7) / 8;          // n8 tiles
+    static constexpr int NPW = (NTT + 3) / 4;           // per warp
+    static constexpr int MT = COUT / 16;
+    static constexpr int CINP = CIN == 1 ? 2 : CIN + 8; // halo cell stride (elements)
+    static constexpr int PXP = kTileR * kTileC + 8;     // dS^T row stride (elements)
+    static constexpr size_t bytes = sizeof(__nv_bfloat16) * (size_t)(kHaloR * kHaloC * CINP + COUT * PXP);
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kConvThreads) k_wgrad(const WgradIO io)
+{
+    using S = WgradShape<CIN, COUT>;
+    extern __shared__ __align__(16) __nv_bfloat16 gsm[];
+    __nv_bfloat16 *sA = gsm;                                   // [10 x 18][CINP]
+    __nv_bfloat16 *sD = gsm + kHaloR * kHaloC * S::CINP;        // [COUT][PXP]: dS transposed
+    const uint16_t *sA16 = reinterpret_cast<const uint16_t *>(sA);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int mh = io.mh, mw = io.mw;
+    const int per_frame = io.tiles_r * io.tiles_c;
+    const int total = io.n * per_frame;
+    // this lane's B column in each of the warp's n-tiles: (tap, ci), the bias column, or nothing
+    int coff[S::NPW];    // element offset of (dy, dx, ci) in the halo tile, -1 = zero column, -2 = ones
+#pragma unroll
+    for (int j = 0; j < S::NPW; ++j) {
+        const int col = (warp * S::NPW + j) * 8 + g;
+        if (col < 9 * CIN) {
+            const int tap = col / CIN, ci = col % CIN;
+            coff[j] = ((tap / 3) * kHaloC + tap % 3) * S::CINP + ci;
+        } else {
+            coff[j] = col == 9 * CIN ? -2 : -1;
+        }
+    }
+    float acc[S::MT][S::NPW][4];
+#pragma unroll
+    for (int mt = 0; mt < S::MT; ++mt)
+#pragma unroll
+        for (int j = 0; j < S::NPW; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                acc[mt][j][q] = 0.0f;
+    const uint16_t one = 0x3f80;   // bf16 1.0
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int f = tile / per_frame, rem = tile % per_frame;
+        const int y0 = (rem / io.tiles_c) * kTileR, x0 = (rem % io.tiles_c) * kTileC;
+        __syncthreads();
+        if constexpr (CIN == 1) {
+            for (int i = tid; i < kHaloR * kHaloC; i += kConvThreads) {
+                const int yy = y0 - 1 + i / kHaloC, xx = x0 - 1 + i % kHaloC;
+                __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+                if (yy >= 0 && yy < mh && xx >= 0 && xx < mw)
+                    v = io.A[((size_t)f * mh + yy) * mw + xx];
+                sA[i * S::CINP] = v;
+            }
+        } else {
+            for (int i = tid; i < kHaloR * kHaloC * (CIN / 8); i += kConvThreads) {
+                const int cell = i / (CIN / 8), ch = i % (CIN / 8);
+                const int yy = y0 - 1 + cell / kHaloC, xx = x0 - 1 + cell % kHaloC;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (yy >= 0 && yy < mh && xx >= 0 && xx < mw)
+                    v = __ldg(reinterpret_cast<const uint4 *>(io.A + (((size_t)f * mh + yy) * mw + xx) * CIN) + ch);
+                *reinterpret_cast<uint4 *>(sA + cell * S::CINP + ch * 8) = v;
+            }
+        }
+        // dS of the tile's 128 cells, transposed to [co][cell]; cells outside the map are 0
+        for (int i = tid; i < kTileR * kTileC * (COUT / 8); i += kConvThreads) {
+            const int cell = i / (COUT / 8), ch = i % (COUT / 8);
+            const int yy = y0 + cell / kTileC, xx = x0 + cell % kTileC;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (yy < mh && xx < mw)
+                v = __ldg(reinterpret_cast<const uint4 *>(io.dS + (((size_t)f * mh + yy) * mw + xx) * COUT) + ch);
+            const uint16_t *e = reinterpret_cast<const uint16_t *>(&v);
+            uint16_t *col = reinterpret_cast<uint16_t *>(sD) + (ch * 8) * S::PXP + cell;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                col[k * S::PXP] = e[k];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int r = 0; r < kTileR; ++r) {           // one k16 step per tile row (16 cells)
+            uint32_t af[S::MT][4];
+#pragma unroll
+            for (int mt = 0; mt < S::MT; ++mt) {
+                const __nv_bfloat16 *r0 = sD + (mt * 16 + g) * S::PXP + r * kTileC + 2 * t;
+                const __nv_bfloat16 *r1 = r0 + 8 * S::PXP;
+                af[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
+                af[mt][1] = *reinterpret_cast<const uint32_t *>(r1);
+                af[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
+                af[mt][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
+            }
+            const int rowoff = r * kHaloC * S::CINP;
+#pragma unroll
+            for (int j = 0; j < S::NPW; ++j) {
+                if ((warp * S::NPW + j) * 8 >= S::NCOL)
+                    break;
+                uint32_t b0, b1;
+                if (coff[j] >= 0) {
+                    const uint16_t *p = sA16 + rowoff + coff[j] + (2 * t) * S::CINP;
+                    b0 = pack_raw(p[0], p[S::CINP]);
+                    b1 = pack_raw(p[8 * S::CINP], p[9 * S::CINP]);
+                } else {
+                    b0 = coff[j] == -2 ? pack_raw(one, one) : 0u;
+                    b1 = b0;
+                }
+#pragma unroll
+                for (int mt = 0; mt < S::MT; ++mt)
+                    mma16816(acc[mt][j], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b0, b1);
+            }
+        }
+    }
+    float *part = io.part + (size_t)blockIdx.x * COUT * S::NCOL;
+#pragma unroll
+    for (int mt = 0; mt < S::MT; ++mt)
+#pragma unroll
+        for (int j = 0; j < S::NPW; ++j) {
+            const int c0 = (warp * S::NPW + j) * 8 + 2 * t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int co = mt * 16 + g + (q >> 1) * 8, col = c0 + (q & 1);
+                if (col < S::NCOL)
+                    part[co * S::NCOL + col] = acc[mt][j][q];
+            }
+        }
+}
+
+// Sum the per-CTA partials in CTA order and scatter into the flat gradient (layout [co][ci][3][3], b[co]).
+__global__ void k_wreduce(const float *part, int nparts, int cin, int cout, float *grad_w, float *grad_b)
+{
+    const int ncol = 9 * cin + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cout * ncol)
+        return;
+    float s = 0.0f;
+    for (int k = 0; k < nparts; ++k)
+        s = __fadd_rn(s, part[(size_t)k * cout * ncol + i]);
+    const int co = i / ncol, col = i % ncol;
+    if (col == 9 * cin)
+        grad_b[co] = s;
+    else
+        grad_w[(co * cin + col % cin) * 9 + col / cin] = s;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// head + loss: z, loss term, dz, dS_4 = bf16(w_h dz [A_4 > 0]); partials (loss, dw_h[16], db_h)
+// ---------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCellThreads) k_loss(const NetArgs a, const uint8_t *labels, int n, float inv_n,
+                                                       float pw, float *part)
+{
+    __shared__ float red[kCellThreads / 32][18];
+    const int mh = a.mh, mw = a.mw;
+    const long long cells = (long long)n * mh * mw;
+    float whv[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+        whv[c] = __bfloat162float(a.whb[c]);
+    const float bh = a.bh[0];
+    float acc[18];
+#pragma unroll
+    for (int k = 0; k < 18; ++k)
+        acc[k] = 0.0f;
+    for (long long p = blockIdx.x * (long long)kCellThreads + threadIdx.x; p < cells;
+         p += (long long)gridDim.x * kCellThreads) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.act[3] + p * 16);
+        const uint4 q0 = src[0], q1 = src[1];
+        const uint32_t w32[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        float av[16];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            av[2 * k] = bf_lo(w32[k]);
+            av[2 * k + 1] = bf_hi(w32[k]);
+        }
+        float z = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            z = __fmaf_rn(whv[c], av[c], z);
+        z = __fadd_rn(z, bh);
+        const float y = labels[p] ? 1.0f : 0.0f;
+        const float sp = 1.0f / (1.0f + expf(-z));          // sigmoid(z)
+        const float sn = 1.0f / (1.0f + expf(z));           // sigmoid(-z)
+        const float spz = fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));     // softplus(z)
+        const float spn = fmaxf(-z, 0.0f) + log1pf(expf(-fabsf(z)));    // softplus(-z)
+        acc[0] += pw * y * spn + (1.0f - y) * spz;
+        const float dz = ((1.0f - y) * sp - pw * y * sn) * inv_n;
+        uint32_t o[8];
+#pragma unroll
+        for (int c = 0; c < 16; c += 2) {
+            const float d0 = av[c] > 0.0f ? whv[c] * dz : 0.0f;
+            const float d1 = av[c + 1] > 0.0f ? whv[c + 1] * dz : 0.0f;
+            o[c >> 1] = pack2(d0, d1);
+            acc[1 + c] = __fmaf_rn(dz, av[c], acc[1 + c]);
+            acc[2 + c] = __fmaf_rn(dz, av[c + 1], acc[2 + c]);
+        }
+        acc[17] += dz;
+        uint4 *dst = reinterpret_cast<uint4 *>(a.dS[0] + p * 16);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+        float v = acc[k];
+        for (int d = 16; d > 0; d >>= 1)
+            v += __shfl_down_sync(0xffffffffu, v, d);
+        if (lane == 0)
+            red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 18) {
+        float v = 0.0f;
+        for (int w = 0; w < kCellThreads / 32; ++w)
+            v += red[w][threadIdx.x];
+        part[(size_t)blockIdx.x * 18 + threadIdx.x] = v;
+    }
+}
+
+// loss and the head's gradient from the k_loss partials (fixed order)
+__global__ void k_loss_reduce(const float *part, int nparts, float inv_n, float *grad_head, float *loss_out)
+{
+    const int k = threadIdx.x;
+    if (k >= 18)
+        return;
+    float s = 0.0f;
+    for (int i = 0; i < nparts; ++i)
+        s = __fadd_rn(s, part[(size_t)i * 18 + k]);
+    if (k == 0) {
+        if (loss_out)
+            *loss_out = s * inv_n;
+    } else {
+        grad_head[k - 1] = s;   // wh[0..15], then bh
+    }
+}
+
+// ---------------------------------------------------------------------------------------------------
+// parameters: Adam step and the bf16 operand copies
+// ---------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void store_operand(const NetArgs &a, int i, float v)
+{
+    // flat layout: per layer W[co][ci][3][3] then b[co]; then wh[16], bh
+    int base = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const int ci_n = net_ch(l), co_n = net_ch(l + 1);
+        const int nw = co_n * ci_n * 9;
+        if (i < base + nw) {
+            const int r = i - base, co = r / (ci_n * 9), ci = (r / 9) % ci_n, tap = r % 9;
+            const __nv_bfloat16 b = __float2bfloat16_rn(v);
+            a.wf[l][(co * 9 + tap) * ci_n + ci] = b;
+            if (l > 0)
+                a.wb[l][(ci * 9 + (8 - tap)) * co_n + co] = b;
+            return;
+        }
+        base += nw + co_n;
+        if (i < base)
+            return;   // bias: read from the master copy
+    }
+    if (i < base + 16)
+        a.whb[i - base] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_pack(const NetArgs a)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kNetParams)
+        store_operand(a, i, a.theta[i]);
+}
+
+__global__ void k_adam(const NetArgs a, const float *grad, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNetParams)
+        return;
+    const float gi = grad[i];
+    const float m = b1 * a.m[i] + (1.0f - b1) * gi;
+    const float v = b2 * a.v[i] + (1.0f - b2) * gi * gi;
+    a.m[i] = m;
+    a.v[i] = v;
+    const float th = a.theta[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);   // c1 = 1 - b1^t, c2 = 1 - b2^t
+    a.theta[i] = th;
+    store_operand(a, i, th);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// labels, scores, top-k
+// ---------------------------------------------------------------------------------------------------
+// one thread per (frame, lane): the Eq. 25 track of the lane's start, row by row as in the energy kernel
+__global__ void k_labels(const KParams kp, const Work w, const ld_lanes *lanes, uint8_t *labels, int mh, int mw)
+{
+    const int f = blockIdx.x, l = threadIdx.x;
+    if (l >= LD_MAX_LANES)
+        return;
+    const ld_lanes &L = lanes[f];
+    const FrameState &fs = w.fs[f];
+    if (l >= L.n_lanes || (fs.flags & (LD_F_NO_ROAD | LD_F_DEGEN_Y | LD_F_DEGEN_X)))
+        return;
+    const int W = kp.W, H = kp.H, vtop = fs.v_top;
+    const float *Vpy = w.rows + (size_t)f * 3 * H + H;
+    const float *Vpx = Vpy + H;
+    uint8_t *Y = labels + (size_t)f * mh * mw;
+    float u = (float)L.start_u[l];
+    for (int v = H - 1; v >= vtop; --v) {
+        if (v < H - 1) {
+            const float vx = Vpx[v + 1], vy = Vpy[v + 1];
+            const float num = __fsub_rn(__fadd_rn(vx, __fmul_rn((float)v, u)), __fmul_rn(vy, u));
+            const float den = __fsub_rn((float)(v + 1), vy);
+            u = __fdiv_rn(num, den);
+        }
+        const float c = floorf(__fadd_rn(u, 0.5f));
+        if (c >= 0.0f && c < (float)W)
+            Y[(v >> 2) * mw + ((int)c >> 2)] = 1;
+    }
+}
+
+// one thread per (frame, coarse start c): z summed along the track in steps of four rows
+__global__ void __launch_bounds__(128) k_score(const KParams kp, const Work w, const float *z, float *scores,
+                                               int mh, int mw)
+{
+    const int f = blockIdx.y, c = blockIdx.x * 128 + threadIdx.x;
+    const int nc = (kp.n_starts + 3) >> 2;
+    if (c >= nc)
+        return;
+    const FrameState &fs = w.fs[f];
+    float acc = 0.0f;
+    if (!(fs.flags & LD_F_NO_LANES)) {
+        const int W = kp.W, H = kp.H;
+        const float *Vpy = w.rows + (size_t)f * 3 * H + H;
+        const float *Vpx = Vpy + H;
+        const float *zf = z + (size_t)f * mh * mw;
+        float u = __fadd_rn((float)(4 * c - kp.S0), 1.5f);
+        for (int v = H - 1; v >= fs.v_top; v -= 4) {
+            const float col = floorf(__fadd_rn(u, 0.5f));
+            if (col >= 0.0f && col < (float)W)
+                acc = __fadd_rn(acc, __ldg(zf + (v >> 2) * mw + ((int)col >> 2)));
+            const float step = __fdiv_rn(__fmul_rn(4.0f, __fsub_rn(Vpx[v], u)), __fsub_rn((float)v, Vpy[v]));
+            u = __fadd_rn(u, step);
+        }
+    }
+    scores[(size_t)f * nc + c] = acc;
+}
+
+// one CTA per frame: ranks of the coarse scores (ties to the smaller index), flags of candidate (bit 0)
+// and evaluated (bit 1) starts, and the ascending list of evaluated starts
+constexpr int kTopThreads = 256;
+
+__global__ void __launch_bounds__(kTopThreads) k_topk(const KParams kp, const Work w, const float *scores, int top_k,
+                                                      uint8_t *cflag, int32_t *elist, int32_t *ecnt, int ecap)
+{
+    extern __shared__ __align__(16) unsigned char tsm[];
+    const int f = blockIdx.x, ns = kp.n_starts, nc = (ns + 3) >> 2;
+    float *sc = reinterpret_cast<float *>(tsm);               // [nc]
+    uint8_t *fl = tsm + sizeof(float) * ((nc + 3) & ~3);       // [ns]
+    __shared__ int wsum[kTopThreads / 32];
+    __shared__ int base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool skip = w.fs[f].flags & LD_F_NO_LANES;
+    for (int i = tid; i < nc; i += kTopThreads)
+        sc[i] = scores[(size_t)f * nc + i];
+    for (int i = tid; i < ns; i += kTopThreads)
+        fl[i] = 0;
+    if (tid == 0)
+        base = 0;
+    __syncthreads();
+    if (!skip) {
+        for (int c = tid; c < nc; c += kTopThreads) {
+            const float s = sc[c];
+            int rank = 0;
+            for (int o = 0; o < nc && rank < top_k; ++o) {
+                const float so = sc[o];
+                rank += (so > s) || (so == s && o < c);
+            }
+            if (rank < top_k)
+                for (int r = 0; r < 4; ++r)
+                    if (4 * c + r < ns)
+                        fl[4 * c + r] = 1;
+        }
+    }
+    __syncthreads();
+    // evaluated = candidate or next to one; per chunk a read phase, then the writes and an ordered compaction
+    for (int i0 = 0; i0 < ns; i0 += kTopThreads) {
+        const int i = i0 + tid;
+        bool ev = false;
+        if (i < ns)
+            ev = (fl[i] & 1) || (i > 0 && (fl[i - 1] & 1)) || (i + 1 < ns && (fl[i + 1] & 1));
+        __syncthreads();
+        if (i < ns && ev)
+            fl[i] |= 2;
+        // ordered compaction of this chunk
+        const unsigned bal = __ballot_sync(0xffffffffu, ev);
+        if (lane == 0)
+            wsum[warp] = __popc(bal);
+        __syncthreads();
+        int off = base;
+        for (int k = 0; k < warp; ++k)
+            off += wsum[k];
+        off += __popc(bal & ((1u << lane) - 1u));
+        if (ev && off < ecap)
+            elist[(size_t)f * ecap + off] = i;
+        __syncthreads();
+        if (tid == 0) {
+            int s = 0;
+            for (int k = 0; k < kTopThreads / 32; ++k)
+                s += wsum[k];
+            base += s;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < ns; i += kTopThreads)
+        cflag[(size_t)f * ns + i] = fl[i];
+    if (tid == 0)
+        ecnt[f] = base < ecap ? base : ecap;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------------
+// Every kernel here stays under the default 48 KB of dynamic shared memory (k_topk: 2.5 bytes per start,
+// at most 30 KB for the widest frame), so no opt-in is needed.
+
+static int grid_for(int tiles, int per_sm)
+{
+    const int g = 152 * per_sm;
+    return tiles < g ? tiles : g;
+}
+
+template <int CIN, int COUT, int EPI>
+static cudaError_t conv(const ConvIO &io, cudaStream_t s)
+{
+    const int tiles = io.n * io.tiles_r * io.tiles_c;
+    k_conv<CIN, COUT, EPI><<<grid_for(tiles, 8), kConvThreads, ConvSmem<CIN, COUT>::bytes, s>>>(io);
+    return cudaGetLastError();
+}
+
+cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, bool keep_a4, cudaStream_t s)
+{
+    const long long cells = (long long)n * a.mh * a.mw;
+    const int g1 = (int)((cells + kCellThreads - 1) / kCellThreads);
+    k_conv1<<<g1 < 152 * 8 ? g1 : 152 * 8, kCellThreads, 0, s>>>(a, xsum, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    ConvIO io{};
+    io.n = n;
+    io.mh = a.mh;
+    io.mw = a.mw;
+    io.tiles_r = (a.mh + kTileR - 1) / kTileR;
+    io.tiles_c = (a.mw + kTileC - 1) / kTileC;
+    io.in = a.act[0];
+    io.wt = a.wf[1];
+    io.bias = a.bias[1];
+    io.out = a.act[1];
+    if ((e = conv<16, 32, kEpiRelu>(io, s)) != cudaSuccess)
+        return e;
+    io.in = a.act[1];
+    io.wt = a.wf[2];
+    io.bias = a.bias[2];
+    io.out = a.act[2];
+    if ((e = conv<32, 32, kEpiRelu>(io, s)) != cudaSuccess)
+        return e;
+    io.in = a.act[2];
+    io.wt = a.wf[3];
+    io.bias = a.bias[3];
+    io.out = keep_a4 ? a.act[3] : nullptr;
+    io.wh = a.whb;
+    io.bh = a.bh;
+    io.z = z;
+    return conv<32, 16, kEpiHead>(io, s);
+}
+
+template <int CIN, int COUT>
+static cudaError_t wgrad(const NetArgs &a, const __nv_bfloat16 *dS, const __nv_bfloat16 *A, int n, float *gw,
+                         float *gb, cudaStream_t s)
+{
+    WgradIO io{};
+    io.dS = dS;
+    io.A = A;
+    io.part = a.part;
+    io.n = n;
+    io.mh = a.mh;
+    io.mw = a.mw;
+    io.tiles_r = (a.mh + kTileR - 1) / kTileR;
+    io.tiles_c = (a.mw + kTileC - 1) / kTileC;
+    const int G = grid_for(n * io.tiles_r * io.tiles_c, kWgradCtasPerSm);
+    k_wgrad<CIN, COUT><<<G, kConvThreads, WgradShape<CIN, COUT>::bytes, s>>>(io);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const int outs = COUT * (9 * CIN + 1);
+    k_wreduce<<<(outs + 255) / 256, 256, 0, s>>>(a.part, G, CIN, COUT, gw, gb);
+    return cudaGetLastError();
+}
+
+cudaError_t net_backward(const NetArgs &a, const uint8_t *labels, int n, float pw, float *grad, float *loss,
+                         cudaStream_t s)
+{
+    const long long cells = (long long)n * a.mh * a.mw;
+    const float inv_n = 1.0f / (float)cells;
+    const int gl = (int)((cells + kCellThreads - 1) / kCellThreads);
+    const int GL = gl < 152 * 4 ? gl : 152 * 4;
+    k_loss<<<GL, kCellThreads, 0, s>>>(a, labels, n, inv_n, pw, a.part_head);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    k_loss_reduce<<<1, 32, 0, s>>>(a.part_head, GL, inv_n, grad + kNetParams - 17, loss);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    // parameter offsets
+    int off[4], cur = 0;
+    for (int l = 0; l < 4; ++l) {
+        off[l] = cur;
+        cur += net_ch(l + 1) * net_ch(l) * 9 + net_ch(l + 1);
+    }
+    auto gw = [&](int l) { return grad + off[l]; };
+    auto gb = [&](int l) { return grad + off[l] + net_ch(l + 1) * net_ch(l) * 9; };
+    ConvIO io{};
+    io.n = n;
+    io.mh = a.mh;
+    io.mw = a.mw;
+    io.tiles_r = (a.mh + kTileR - 1) / kTileR;
+    io.tiles_c = (a.mw + kTileC - 1) / kTileC;
+    // layer 4: dS_4 in dS[0] (16 channels), A_3 (32)
+    if ((e = wgrad<32, 16>(a, a.dS[0], a.act[2], n, gw(3), gb(3), s)) != cudaSuccess)
+        return e;
+    io.in = a.dS[0];
+    io.wt = a.wb[3];
+    io.mask = a.act[2];
+    io.out = a.dS[1];
+    if ((e = conv<16, 32, kEpiMask>(io, s)) != cudaSuccess)    // dS_3 (32)
+        return e;
+    if ((e = wgrad<32, 32>(a, a.dS[1], a.act[1], n, gw(2), gb(2), s)) != cudaSuccess)
+        return e;
+    io.in = a.dS[1];
+    io.wt = a.wb[2];
+    io.mask = a.act[1];
+    io.out = a.dS[0];
+    if ((e = conv<32, 32, kEpiMask>(io, s)) != cudaSuccess)    // dS_2 (32)
+        return e;
+    if ((e = wgrad<16, 32>(a, a.dS[0], a.act[0], n, gw(1), gb(1), s)) != cudaSuccess)
+        return e;
+    io.in = a.dS[0];
+    io.wt = a.wb[1];
+    io.mask = a.act[0];
+    io.out = a.dS[1];
+    if ((e = conv<32, 16, kEpiMask>(io, s)) != cudaSuccess)    // dS_1 (16)
+        return e;
+    return wgrad<1, 16>(a, a.dS[1], a.X, n, gw(0), gb(0), s);
+}
+
+cudaError_t net_pack(const NetArgs &a, cudaStream_t s)
+{
+    k_pack<<<(kNetParams + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t net_adam(const NetArgs &a, const float *grad, float lr, float b1, float b2, float eps, float c1, float c2,
+                     cudaStream_t s)
+{
+    k_adam<<<(kNetParams + 255) / 256, 256, 0, s>>>(a, grad, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t net_labels(const KParams &kp, const Work &w, const ld_lanes *lanes, uint8_t *labels, int mh, int mw,
+                       cudaStream_t s)
+{
+    k_labels<<<kp.n_frames, 32, 0, s>>>(kp, w, lanes, labels, mh, mw);
+    return cudaGetLastError();
+}
+
+cudaError_t net_propose(const KParams &kp, const Work &w, const float *z, int mh, int mw, int top_k, float *scores,
+                        uint8_t *cflag, int32_t *elist, int32_t *ecnt, int ecap, cudaStream_t s)
+{
+    const int nc = (kp.n_starts + 3) >> 2;
+    dim3 g1((nc + 127) / 128, kp.n_frames);
+    k_score<<<g1, 128, 0, s>>>(kp, w, z, scores, mh, mw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const size_t smem = sizeof(float) * (size_t)((nc + 3) & ~3) + (size_t)kp.n_starts;
+    k_topk<<<kp.n_frames, kTopThreads, smem, s>>>(kp, w, scores, top_k, cflag, elist, ecnt, ecap);
+    return cudaGetLastError();
+}
+
+}  // namespace ld

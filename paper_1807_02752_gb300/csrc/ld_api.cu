@@ -211,15 +211,15 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// The launch sequence of one call; with `timed`, an event is recorded before and after every kernel.
-// The nine launches of one detection of kp.n_frames frames on stream s, on the workspace view w.
-int enqueue_on(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const float *disp, const uint8_t *img,
-               ld_lanes *out, cudaStream_t s, bool timed)
+// Launches [first, last) of the sequence of one detection of kp.n_frames frames on stream s, on the
+// workspace view w; with `timed`, an event is recorded before and after every kernel.
+int enqueue_range(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const float *disp, const uint8_t *img,
+                  ld_lanes *out, cudaStream_t s, bool timed, int first, int last)
 {
     cudaError_t e = cudaSuccess;
-    if (timed && (e = cudaEventRecord(h->ev[0], s)) != cudaSuccess)
+    if (timed && (e = cudaEventRecord(h->ev[first], s)) != cudaSuccess)
         return cuda_fail(h, e, "event record");
-    for (int k = 0; k < kLaunches; ++k) {
+    for (int k = first; k < last; ++k) {
         switch (k) {
         case 0: e = ld::launch_vdisp(kp, w, disp, s); break;
         case 1: e = ld::launch_road(kp, w, s); break;
@@ -237,6 +237,13 @@ int enqueue_on(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const flo
             return cuda_fail(h, e, "event record");
     }
     return LD_OK;
+}
+
+// The nine launches of one detection.
+int enqueue_on(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const float *disp, const uint8_t *img,
+               ld_lanes *out, cudaStream_t s, bool timed)
+{
+    return enqueue_range(h, kp, w, disp, img, out, s, timed, 0, kLaunches);
 }
 
 int enqueue(ld_handle *h, const ld::KParams &kp, const float *disp, const uint8_t *img, ld_lanes *out,
@@ -265,6 +272,8 @@ ld::Work work_from(const ld::Work &w, const ld::KParams &kp, int f0)
     v.npts += f * 2;
     v.gbt += f * (size_t)w.max_h * ld::vpx_row_bytes(w.max_w);
     v.M1 += f * H * W;
+    if (v.xsum)
+        v.xsum += f * (size_t)((H + 3) / 4) * ((W + 3) / 4);
     v.HE += f * (size_t)kp.n_starts;
     return v;
 }
@@ -329,6 +338,38 @@ int check_call(ld_handle *h, const void *disp, const void *img, int w, int hh, i
 
 namespace ld {
 void set_global_error(const char *msg) { g_create_error = msg; }
+
+// Access for the learned proposal's runtime (ld_net.cu), which drives a handle's plain stages.
+int handle_fail(ld_handle *h, int code, const char *msg) { return fail(h, code, msg); }
+int handle_cuda_fail(ld_handle *h, cudaError_t e, const char *what) { return cuda_fail(h, e, what); }
+int handle_check(ld_handle *h, const void *disp, const void *img, int w, int hh, int n, const void *out)
+{
+    return check_call(h, disp, img, w, hh, n, out);
+}
+void handle_dims(const ld_handle *h, int *max_w, int *max_h, int *max_batch)
+{
+    *max_w = h->max_w;
+    *max_h = h->max_h;
+    *max_batch = h->max_batch;
+}
+const ld_params &handle_params(const ld_handle *h) { return h->p; }
+cudaStream_t handle_stream(const ld_handle *h) { return h->stream; }
+Work handle_work(const ld_handle *h) { return h->w; }
+// parameters of a call on w x hh x n frames; the call becomes the one ld_debug_get reports on
+KParams handle_call(ld_handle *h, int w, int hh, int n)
+{
+    h->last_w = w;
+    h->last_h = hh;
+    h->last_n = n;
+    h->have_last = true;
+    return make_kparams(h, w, hh, n);
+}
+// launches [first, last) of the plain sequence (0 k_vdisp ... 6 k_m1, 7 k_energy, 8 k_select), eager
+int handle_enqueue(ld_handle *h, const KParams &kp, const Work &w, const float *disp, const uint8_t *img,
+                   ld_lanes *out, int first, int last)
+{
+    return enqueue_range(h, kp, w, disp, img, out, h->stream, false, first, last);
+}
 }  // namespace ld
 
 extern "C" {

@@ -70,6 +70,7 @@ struct Work {
     int32_t *npts;       // [n][2]
     uint8_t *gbt;        // [n][max_h][vpx_row_bytes(max_w)] V_px backtrack rows below the shared-memory block
     int32_t *M1;         // [n][H][W]
+    int32_t *xsum;       // [n][ceil(H/4)][ceil(W/4)] block sums of |G_x w_g| for the learned proposal, or null
     int64_t *HE;         // [n][n_starts]
     const int32_t *wr;   // [kWrEntries] Q15
     const int32_t *wg;   // [kWgEntries] Q12
@@ -145,6 +146,13 @@ cudaError_t launch_vpx(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_energy(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_select(const KParams &kp, const Work &w, ld_lanes *out, cudaStream_t s);
+// learned proposal: energies of the listed starts / selection among the candidates (frames without a lane
+// are flagged LD_F_FALLBACK), then the exhaustive energies and selection of the flagged frames only
+cudaError_t launch_energy_list(const KParams &kp, const Work &w, const int32_t *elist, const int32_t *ecnt, int ecap,
+                               cudaStream_t s);
+cudaError_t launch_select_set(const KParams &kp, const Work &w, const uint8_t *cflag, ld_lanes *out, cudaStream_t s);
+cudaError_t launch_energy_fallback(const KParams &kp, const Work &w, cudaStream_t s);
+cudaError_t launch_select_fallback(const KParams &kp, const Work &w, ld_lanes *out, cudaStream_t s);
 size_t road_smem_bytes(const KParams &kp);
 size_t vpx_smem_bytes(const KParams &kp);
 int vpx_seg_rows(const KParams &kp, size_t budget);

@@ -16,7 +16,9 @@ LIB_PATH = os.path.join(HERE, "lib", "libld.so")
 MAX_LANES = 8
 LD_STATIC_SCRATCH_BYTES = 8 << 20
 OK, E_ARG, E_CUDA, E_NOMEM, E_STATE = 0, -1, -2, -3, -4
-F_NO_ROAD, F_CAP_Y, F_DEGEN_Y, F_CAP_X, F_DEGEN_X, F_NO_LANES = 1, 2, 4, 8, 16, 32
+F_NO_ROAD, F_CAP_Y, F_DEGEN_Y, F_CAP_X, F_DEGEN_X, F_NO_LANES, F_FALLBACK = 1, 2, 4, 8, 16, 32, 64
+NET_PARAMS, NET_TOPK_MAX = 18689, 256
+NET_STAGE_XSUM, NET_STAGE_LOGITS, NET_STAGE_SCORES, NET_STAGE_CFLAG = 1, 2, 3, 4
 STAGE_VDISP, STAGE_PATH_Y, STAGE_INL_Y, STAGE_ROWS, STAGE_EDGES, STAGE_PATH_X, STAGE_INL_X, STAGE_M1, STAGE_HE = range(1, 10)
 
 
@@ -121,6 +123,28 @@ def load():
     L.ld_server_last_error.restype = C.c_char_p
     L.ld_server_destroy.argtypes = [p]
     L.ld_server_destroy.restype = None
+    L.ld_net_param_count.argtypes = []
+    L.ld_net_param_count.restype = i32
+    L.ld_net_create.argtypes = [p, i32, C.POINTER(p)]
+    L.ld_net_set_params.argtypes = [p, p]
+    L.ld_net_get_params.argtypes = [p, p]
+    L.ld_net_forward.argtypes = [p, p, i32, i32, i32, p]
+    L.ld_net_grad.argtypes = [p, p, p, i32, i32, i32, p, p]
+    L.ld_net_apply_grad.argtypes = [p, p, C.c_float]
+    L.ld_net_train_step.argtypes = [p, p, p, i32, i32, i32, C.c_float, p]
+    L.ld_make_training_pairs.argtypes = [p, p, p, i32, i32, i32, p, p, p]
+    L.ld_detect_learned.argtypes = [p, p, p, p, i32, i32, i32, i32, p]
+    L.ld_net_debug_get.argtypes = [p, i32, i32, p, C.c_size_t]
+    L.ld_net_debug_size.argtypes = [p, i32]
+    L.ld_net_debug_size.restype = C.c_size_t
+    L.ld_net_last_error.argtypes = [p]
+    L.ld_net_last_error.restype = C.c_char_p
+    L.ld_net_destroy.argtypes = [p]
+    L.ld_net_destroy.restype = None
+    for name in ("ld_net_create", "ld_net_set_params", "ld_net_get_params", "ld_net_forward", "ld_net_grad",
+                 "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs", "ld_detect_learned",
+                 "ld_net_debug_get"):
+        getattr(L, name).restype = C.c_int
     _lib = L
     return L
 
@@ -129,7 +153,9 @@ EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_de
             "ld_debug_get", "ld_debug_size", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
             "ld_destroy", "ld_road_path_static", "ld_tune", "ld_server_create", "ld_server_submit", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
-            "ld_server_destroy"]
+            "ld_server_destroy", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
+            "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
+            "ld_detect_learned", "ld_net_debug_size", "ld_net_debug_get", "ld_net_last_error", "ld_net_destroy"]
 
 
 def launch_names():
@@ -352,6 +378,108 @@ class Server:
         if getattr(self, "s", None):
             self.L.ld_server_destroy(self.s)
             self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """The learned lane-position proposal of a Detector (ld_net_*): device tensors in, device tensors out."""
+
+    def __init__(self, det: "Detector", training: bool = False):
+        self.L = load()
+        self.det = det
+        h = C.c_void_p()
+        rc = self.L.ld_net_create(det.h, 1 if training else 0, C.byref(h))
+        if rc != OK:
+            raise LDError(rc, self.L.ld_net_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LDError(rc, self.L.ld_net_last_error(self.h).decode())
+
+    @staticmethod
+    def map_shape(W: int, H: int):
+        return (H + 3) // 4, (W + 3) // 4
+
+    def set_params(self, theta):
+        """theta: float32 device tensor of NET_PARAMS values (resets the optimiser state)."""
+        assert theta.is_cuda and theta.numel() == NET_PARAMS and theta.dtype.itemsize == 4 and theta.is_contiguous()
+        self._check(self.L.ld_net_set_params(self.h, theta.data_ptr()))
+
+    def get_params(self):
+        import torch
+
+        out = torch.empty(NET_PARAMS, dtype=torch.float32, device="cuda")
+        self._check(self.L.ld_net_get_params(self.h, out.data_ptr()))
+        return out
+
+    def forward(self, xsum, W: int, H: int):
+        import torch
+
+        n = xsum.shape[0]
+        mh, mw = self.map_shape(W, H)
+        z = torch.empty((n, mh, mw), dtype=torch.float32, device="cuda")
+        self._check(self.L.ld_net_forward(self.h, xsum.data_ptr(), W, H, n, z.data_ptr()))
+        return z
+
+    def grad(self, xsum, labels, W: int, H: int):
+        import torch
+
+        n = xsum.shape[0]
+        g = torch.empty(NET_PARAMS, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        self._check(self.L.ld_net_grad(self.h, xsum.data_ptr(), labels.data_ptr(), W, H, n, g.data_ptr(),
+                                       loss.data_ptr()))
+        return g, loss
+
+    def apply_grad(self, g, lr: float):
+        self._check(self.L.ld_net_apply_grad(self.h, g.data_ptr(), lr))
+
+    def train_step(self, xsum, labels, W: int, H: int, lr: float, loss=None):
+        n = xsum.shape[0]
+        self._check(self.L.ld_net_train_step(self.h, xsum.data_ptr(), labels.data_ptr(), W, H, n, lr,
+                                             None if loss is None else loss.data_ptr()))
+
+    def training_pairs(self, disp, img, xsum_out=None, labels_out=None, lanes_out=None):
+        """The plain method's lanes, block sums and labels of frames disp/img [n][H][W] (device tensors)."""
+        import torch
+
+        n, H, W = disp.shape
+        mh, mw = self.map_shape(W, H)
+        xs = xsum_out if xsum_out is not None else torch.empty((n, mh, mw), dtype=torch.int32, device="cuda")
+        lb = labels_out if labels_out is not None else torch.empty((n, mh, mw), dtype=torch.uint8, device="cuda")
+        ln = lanes_out if lanes_out is not None else self.det.alloc_lanes(n)
+        self._check(self.L.ld_make_training_pairs(self.h, disp.data_ptr(), img.data_ptr(), W, H, n, xs.data_ptr(),
+                                                  lb.data_ptr(), ln.data_ptr()))
+        return xs, lb, ln
+
+    def detect(self, disp, img, top_k: int = 32, logits=None, out=None):
+        """Learned form of Detector.detect (device tensors); logits [n][mh][mw] replace the network's."""
+        n, H, W = disp.shape
+        out = self.det.alloc_lanes(n) if out is None else out
+        self._check(self.L.ld_detect_learned(self.h, None if logits is None else logits.data_ptr(), disp.data_ptr(),
+                                             img.data_ptr(), W, H, n, top_k, out.data_ptr()))
+        return out
+
+    def debug(self, frame: int, stage: int):
+        size = int(self.L.ld_net_debug_size(self.h, stage))
+        buf = np.zeros(size, np.uint8)
+        self._check(self.L.ld_net_debug_get(self.h, frame, stage, buf.ctypes.data, size))
+        if stage in (NET_STAGE_XSUM,):
+            return buf.view(np.int32)
+        if stage in (NET_STAGE_LOGITS, NET_STAGE_SCORES):
+            return buf.view(np.float32)
+        return buf
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ld_net_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

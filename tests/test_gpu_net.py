@@ -1,0 +1,256 @@
+"""GPU parity of the learned lane-position proposal (ld_net_*, ld_detect_learned) against oracle/proposal.py.
+
+Exact: the block sums of |G_x w_g|, the training labels, the coarse-start scores (one float32 expression
+order on both sides), the candidate and evaluated sets, and the lanes chosen from given logits.
+Tolerances (network arithmetic): the kernels sum bf16 products in float32 in another order than the
+oracle's float64 sums.  The two sums of a 288-term dot product differ by about 2e-5 relative, against a
+bf16 spacing of 2^-8, so about one stored activation in a hundred rounds to the neighbouring bf16 value
+(0.4 % of itself).  Logits are compared within 2^-7 of their largest magnitude everywhere and within 1e-4
+of it for 99 % of cells, gradients within 1 % per parameter group (relative norm), Adam steps within
+1e-6 relative plus 1e-4 of the step size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import proposal as P
+from paper_1807_02752_gb300 import ld, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_02752_gb300 import build
+    build.build()
+    return torch
+
+
+def init_params(seed: int) -> np.ndarray:
+    """He-normal weights, small positive biases (seeded)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in P.param_shapes():
+        if name.startswith("W"):
+            fan_in = shape[1] * 9
+            parts.append(rng.standard_normal(shape) * np.sqrt(2.0 / fan_in))
+        elif name == "wh":
+            parts.append(rng.standard_normal(shape) * np.sqrt(1.0 / 16))
+        elif name == "bh":
+            parts.append(np.full(shape, -2.0))
+        else:
+            parts.append(np.full(shape, 0.01))
+    return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+
+
+def _frames(cfg, n, first=0):
+    disp, img, truths = scenes.make_batch(cfg, n, first_frame=first)
+    return disp, img, truths
+
+
+def _oracle_frames(disp, img, p):
+    return [oracle.detect(disp[f], img[f], p) for f in range(len(disp))]
+
+
+FIT_FAILED = oracle.F_NO_ROAD | oracle.F_DEGEN_Y | oracle.F_DEGEN_X
+
+
+@pytest.mark.parametrize("name,n", [("small_320x120", 6), ("single_1242x375", 2)])
+def test_block_sums_and_labels_match_oracle(torch_cuda, name, n):
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS[name]
+    disp, img, _ = _frames(cfg, n, first=3)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    op = oracle.default_params(n_disp=cfg.n_disp)
+    det = ld.Detector(cfg.width, cfg.height, n, p)
+    net = ld.Net(det, training=True)
+    xs, lb, ln = net.training_pairs(torch.from_numpy(disp).cuda(), torch.from_numpy(img).cuda())
+    torch.cuda.synchronize()
+    xs, lb, lanes = xs.cpu().numpy(), lb.cpu().numpy(), ld.Detector.lanes(ln)
+    for f, r in enumerate(_oracle_frames(disp, img, op)):
+        assert np.array_equal(xs[f].astype(np.int64), P.xmap_sums(r["Gw"])), f
+        assert list(lanes[f]["start_u"][:lanes[f]["n_lanes"]]) == r["start_u"]
+        want = np.zeros_like(lb[f])
+        if not (r["flags"] & FIT_FAILED):
+            want = P.lane_labels(r["start_u"], r["Vpx"], r["Vpy"], r["v_top"], cfg.height, cfg.width)
+        assert np.array_equal(lb[f], want), f
+    net.close()
+    det.close()
+
+
+def _gpu_pairs(torch, cfg, n, first):
+    disp, img, truths = _frames(cfg, n, first)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    det = ld.Detector(cfg.width, cfg.height, n, p)
+    net = ld.Net(det, training=True)
+    xs, lb, _ = net.training_pairs(torch.from_numpy(disp).cuda(), torch.from_numpy(img).cuda())
+    return disp, img, truths, det, net, xs, lb
+
+
+@pytest.mark.parametrize("name,n", [("small_320x120", 3), ("single_1242x375", 1)])
+def test_forward_matches_oracle(torch_cuda, name, n):
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS[name]
+    disp, img, _, det, net, xs, _ = _gpu_pairs(torch, cfg, n, first=11)
+    theta = init_params(5)
+    net.set_params(torch.from_numpy(theta).cuda())
+    z = net.forward(xs, cfg.width, cfg.height).cpu().numpy()
+    params = P.unpack(theta.astype(np.float64))
+    op = oracle.default_params(n_disp=cfg.n_disp)
+    for f, r in enumerate(_oracle_frames(disp, img, op)):
+        X = P.xmap_input(P.xmap_sums(r["Gw"]))
+        want = P.forward(params, X)["z"]
+        scale = float(np.abs(want).max())
+        d = np.abs(z[f].astype(np.float64) - want)
+        assert d.max() <= 2.0 ** -7 * scale, (f, d.max(), scale)
+        assert np.mean(d <= 1e-4 * scale) >= 0.99, (f, np.mean(d <= 1e-4 * scale))
+    net.close()
+    det.close()
+
+
+@pytest.mark.parametrize("name,n", [("small_320x120", 2), ("single_1242x375", 1)])
+def test_gradient_matches_oracle(torch_cuda, name, n):
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS[name]
+    disp, img, _, det, net, xs, lb = _gpu_pairs(torch, cfg, n, first=21)
+    theta = init_params(6)
+    net.set_params(torch.from_numpy(theta).cuda())
+    # labels: the plain method's lane cells plus seeded random cells, so both loss terms are present
+    rng = np.random.default_rng(7)
+    labels = lb.cpu().numpy() | (rng.random(lb.shape) < 0.02).astype(np.uint8)
+    g, loss = net.grad(xs, torch.from_numpy(labels).cuda(), cfg.width, cfg.height)
+    g, loss = g.cpu().numpy().astype(np.float64), float(loss.cpu().numpy()[0])
+    op = oracle.default_params(n_disp=cfg.n_disp)
+    X = np.stack([P.xmap_input(P.xmap_sums(r["Gw"])) for r in _oracle_frames(disp, img, op)])
+    want_loss, want = P.loss_and_grad(P.unpack(theta.astype(np.float64)), X, labels)
+    assert abs(loss - want_loss) <= 1e-4 * abs(want_loss)
+    gd = P.unpack(g)
+    for name_, _ in P.param_shapes():
+        a, b = gd[name_].ravel(), want[name_].ravel()
+        assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b) + 1e-12, (name_, np.linalg.norm(a - b), np.linalg.norm(b))
+    net.close()
+    det.close()
+
+
+def test_adam_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    cfg = scenes.SMALL_320x120
+    det = ld.Detector(cfg.width, cfg.height, 1, ld.default_params(n_disp=cfg.n_disp))
+    net = ld.Net(det, training=True)
+    rng = np.random.default_rng(8)
+    theta = rng.standard_normal(ld.NET_PARAMS).astype(np.float32) * np.float32(0.1)
+    net.set_params(torch.from_numpy(theta).cuda())
+    th, m, v = theta.astype(np.float64), np.zeros(ld.NET_PARAMS), np.zeros(ld.NET_PARAMS)
+    lr = 3e-3
+    for t in range(1, 4):
+        g = (rng.standard_normal(ld.NET_PARAMS) * 10.0 ** rng.uniform(-4, 0, ld.NET_PARAMS)).astype(np.float32)
+        net.apply_grad(torch.from_numpy(g).cuda(), lr)
+        th, m, v = P.adam(th, g.astype(np.float64), m, v, t, lr)
+    got = net.get_params().cpu().numpy().astype(np.float64)
+    assert np.allclose(got, th, rtol=1e-6, atol=lr * 1e-4)
+    net.close()
+    det.close()
+
+
+def _truth_logits(truths, cfg, S0):
+    """Seeded input logits that favour the generator's planted lanes: +3 on cells crossed by the planted
+    markings' tracks toward the planted vanishing points, -3 elsewhere."""
+    H, W = cfg.height, cfg.width
+    mh, mw = P.map_shape(H, W)
+    out = np.full((len(truths), mh, mw), -3.0, np.float32)
+    for f, t in enumerate(truths):
+        for s in t.lane_starts:
+            u = float(s)
+            for v in range(H - 1, 0, -1):
+                if not np.isfinite(t.vpx[v]) or v - t.vpy[v] <= 1.0:
+                    break
+                c = int(np.floor(u + 0.5))
+                if 0 <= c < W:
+                    out[f, v >> 2, c >> 2] = 3.0
+                u = u + (t.vpx[v] - u) / (v - t.vpy[v])
+    return out
+
+
+def _oracle_learned(r, z, cfg, op, top_k):
+    """Expected (n_lanes, start_u, energy, flags, scores, cflag) of the learned form from the oracle's frame r."""
+    H, W = cfg.height, cfg.width
+    ns = oracle.n_starts(W, op)
+    S0 = (ns - W) // 2
+    if r["flags"] & FIT_FAILED:
+        return r["start_u"], r["energy"], r["flags"], None, None
+    sc = P.coarse_scores(z, r["Vpx"], r["Vpy"], r["v_top"], H, W, S0, ns)
+    top = P.top_k(sc, top_k)
+    cand, ev = P.candidate_sets(top, ns)
+    starts, energies = P.select_on_set(r["HE"], cand, ev, S0, op.thr_num, op.thr_den, op.near_px, op.max_lanes)
+    base = r["flags"] & ~oracle.F_NO_LANES
+    if starts:
+        return starts, energies, base, sc, cand.astype(np.uint8) | (ev.astype(np.uint8) << 1)
+    flags = base | P.F_FALLBACK | (r["flags"] & oracle.F_NO_LANES)
+    return r["start_u"], r["energy"], flags, sc, cand.astype(np.uint8) | (ev.astype(np.uint8) << 1)
+
+
+@pytest.mark.parametrize("name,n,top_k", [("small_320x120", 6, 4), ("small_320x120", 6, 32),
+                                          ("single_1242x375", 2, 32), ("single_1242x375", 2, 3)])
+def test_proposal_from_given_logits_matches_oracle(torch_cuda, name, n, top_k):
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS[name]
+    disp, img, truths = _frames(cfg, n, first=31)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    op = oracle.default_params(n_disp=cfg.n_disp)
+    det = ld.Detector(cfg.width, cfg.height, n, p)
+    net = ld.Net(det)
+    ns = det.n_starts(cfg.width)
+    rng = np.random.default_rng(9)
+    mh, mw = P.map_shape(cfg.height, cfg.width)
+    cases = [_truth_logits(truths, cfg, (ns - cfg.width) // 2),                   # informative
+             rng.standard_normal((n, mh, mw)).astype(np.float32),                  # noise
+             -_truth_logits(truths, cfg, (ns - cfg.width) // 2)]                   # adversarial
+    d, i = torch.from_numpy(disp).cuda(), torch.from_numpy(img).cuda()
+    rs = _oracle_frames(disp, img, op)
+    fallbacks = 0
+    for z in cases:
+        out = net.detect(d, i, top_k=top_k, logits=torch.from_numpy(z).cuda())
+        torch.cuda.synchronize()
+        got = ld.Detector.lanes(out)
+        for f, r in enumerate(rs):
+            starts, energies, flags, sc, cf = _oracle_learned(r, z[f], cfg, op, top_k)
+            g = got[f]
+            assert list(g["start_u"][:g["n_lanes"]]) == list(starts), (f, top_k)
+            assert list(g["energy"][:g["n_lanes"]]) == list(energies)
+            assert int(g["flags"]) == flags, (f, int(g["flags"]), flags)
+            fallbacks += bool(flags & P.F_FALLBACK)
+            if sc is not None:
+                assert np.array_equal(net.debug(f, ld.NET_STAGE_SCORES), sc)
+                assert np.array_equal(net.debug(f, ld.NET_STAGE_CFLAG), cf)
+    assert fallbacks > 0 or top_k > 4   # the adversarial logits force the fallback at small k
+    net.close()
+    det.close()
+
+
+@pytest.mark.parametrize("name,n", [("small_320x120", 6), ("batch64_1242x375", 8)])
+def test_learned_form_with_every_start_equals_plain(torch_cuda, name, n):
+    """With every coarse start proposed, the learned form evaluates every start: its lanes are the plain
+    method's, whatever the network (here an untrained one) says."""
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS[name]
+    disp, img, _ = _frames(cfg, n, first=41)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    det = ld.Detector(cfg.width, cfg.height, n, p)
+    net = ld.Net(det)
+    net.set_params(torch.from_numpy(init_params(12)).cuda())
+    d, i = torch.from_numpy(disp).cuda(), torch.from_numpy(img).cuda()
+    plain = ld.Detector.lanes(det.detect(d, i))
+    nc = (det.n_starts(cfg.width) + 3) // 4
+    if nc <= ld.NET_TOPK_MAX:
+        learned = ld.Detector.lanes(net.detect(d, i, top_k=nc))
+        assert plain.tobytes() == learned.tobytes()
+    small_k = ld.Detector.lanes(net.detect(d, i, top_k=8))
+    torch.cuda.synchronize()
+    for f in range(n):   # any k: a frame either keeps lanes found among its candidates or falls back
+        ok = small_k[f]["flags"] & ld.F_FALLBACK or small_k[f]["n_lanes"] > 0 or plain[f]["flags"] & ld.F_NO_LANES
+        assert ok
+    net.close()
+    det.close()
