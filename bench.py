@@ -173,6 +173,73 @@ def bilateral_pixels(det, disp, W, H, n):
     return total
 
 
+WEIGHTS = os.path.join(ROOT, "paper_1807_02752_gb300", "proposal_weights.npy")
+
+
+def measure_learned(args, dets, streams, disp, img, n, world):
+    """The learned form (network-ranked starts, exact energies of the top-k) on the same handles, streams,
+    inputs and step count as the plain form; agreement of its lanes with the plain lanes on both input
+    batches.  None when the trained weights are absent."""
+    import torch
+
+    from paper_1807_02752_gb300 import ld, replicas
+
+    if args.no_learned or not os.path.exists(WEIGHTS):
+        return None
+    S, K = len(dets), args.top_k
+    theta = torch.from_numpy(np.load(WEIGHTS).astype(np.float32)).cuda()
+    nets = [ld.Net(d) for d in dets]
+    louts = [[d.alloc_lanes(n), d.alloc_lanes(n)] for d in dets]
+    for k in range(S):
+        with torch.cuda.stream(streams[k]):
+            nets[k].set_params(theta)
+    torch.cuda.synchronize()
+    for s in range(max(args.warmup, 3) * S):
+        k = s % S
+        with torch.cuda.stream(streams[k]):
+            nets[k].detect(disp[s & 1], img[s & 1], K, out=louts[k][s & 1])
+    torch.cuda.synchronize()
+    main = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0.record(main)
+    for st in streams:
+        st.wait_event(ev0)
+    for s in range(args.steps):
+        k = s % S
+        with torch.cuda.stream(streams[k]):
+            nets[k].detect(disp[s & 1], img[s & 1], K, out=louts[k][s & 1])
+    for st in streams:
+        main.wait_stream(st)
+    ev1.record(main)
+    torch.cuda.synchronize()
+    total_ms = replicas.max_over_ranks(ev0.elapsed_time(ev1))
+    # agreement with the plain form on both batches (exact start positions), fallbacks, evaluated starts
+    agree, fallback, evaluated = [], 0, 0
+    ns = dets[0].n_starts(disp[0].shape[2])
+    with torch.cuda.stream(streams[0]):
+        for b in range(2):
+            plain = ld.Detector.lanes(dets[0].detect(disp[b], img[b]))
+            got = ld.Detector.lanes(nets[0].detect(disp[b], img[b], K))
+            for f in range(n):
+                a = set(got[f]["start_u"][:got[f]["n_lanes"]])
+                c = set(plain[f]["start_u"][:plain[f]["n_lanes"]])
+                agree.append(1.0 if not a and not c else 2.0 * len(a & c) / (len(a) + len(c)))
+                fallback += bool(got[f]["flags"] & ld.F_FALLBACK)
+                evaluated += int(np.count_nonzero(nets[0].debug(f, ld.NET_STAGE_CFLAG) & 2))
+    for x in nets:
+        x.close()
+    value = world * n * args.steps / (total_ms * 1e-3)
+    return {"value": round(value, 2), "unit": UNIT, "ms_per_step": round(total_ms / args.steps, 4), "top_k": K,
+            "agreement": round(float(np.mean(agree)), 5),
+            "frames_at_99pct_agreement": round(float(np.mean(np.asarray(agree) >= 0.99)), 5),
+            "fallback_frames": fallback, "frames_compared": len(agree),
+            "evaluated_start_fraction": round(evaluated / (len(agree) * ns), 5),
+            "weights": os.path.relpath(WEIGHTS, ROOT)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -307,6 +374,8 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     e2e_s = replicas.max_over_ranks(e2e_s)
 
+    learned = measure_learned(args, dets, streams, disp, img, n, world)
+
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
     dom = int(np.argmax(per))
@@ -362,6 +431,7 @@ def run_ours(args):
             "e2e": {"value": round(world * n * e2e_steps / e2e_s, 2), "unit": UNIT,
                     "h2d_bytes_per_step": int(n * H * W * 5), "d2h_bytes_per_step": int(n * ld.LANES_DTYPE.itemsize)},
             "gpu_launches": int(ld.load().ld_launches_per_detect() * args.steps),
+            "learned": None if learned is None else dict(learned, vs_plain=round(learned["value"] / value, 4)),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -418,6 +488,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in tile shapes")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal form")
+    ap.add_argument("--top-k", type=int, default=96, help="coarse starts the learned form evaluates per frame")
     ap.add_argument("--streams", type=int, default=4, help="library handles on separate streams, batches rotate over them")
     args = ap.parse_args()
     if args.impl == "reference":

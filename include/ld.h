@@ -294,8 +294,8 @@ void ld_server_destroy(ld_server *s);
  *            16 -> 1 giving a logit z per cell: sigmoid(z) is the chance that a lane crosses the cell, its
  *            rows the per-row lane-position heatmap.  Products in bf16, sums in FP32, activations stored
  *            as bf16; trained with a weighted logistic loss (positive weight 10) and Adam;
- *   ranking  coarse start c covers the starts 4c .. 4c+3; its score sums z along the Eq. 25 track taken
- *            in steps of four rows from u = (4c - S0) + 1.5 on the bottom row;
+ *   ranking  coarse start c covers the starts 4c .. 4c+3; its score sums the heatmap sigmoid(z) along the
+ *            Eq. 25 track taken in steps of four rows from u = (4c - S0) + 1.5 on the bottom row;
  *   search   the top_k coarse starts give candidate starts; each candidate and its neighbours get the
  *            exact energy; lanes are the Alg. 7 minima among the candidates (threshold from the smallest
  *            evaluated energy).  A frame where that finds no lane runs the exhaustive search and is
@@ -314,7 +314,8 @@ typedef struct ld_net ld_net;
 
 enum {
     LD_NET_STAGE_XSUM = 1,     /* int32 [mh][mw]  block sums x of the last learned detection */
-    LD_NET_STAGE_LOGITS = 2,   /* float [mh][mw]  logits z used by the last learned detection */
+    LD_NET_STAGE_HEATMAP = 2,  /* float [mh][mw]  heatmap the last learned detection ranked with; rows
+                                  * i >= v_top / 4 (the network runs on the road rows only) */
     LD_NET_STAGE_SCORES = 3,   /* float [ceil(n_starts / 4)] coarse-start scores */
     LD_NET_STAGE_CFLAG = 4,    /* uint8 [n_starts] bit 0 candidate, bit 1 energy evaluated */
 };
@@ -341,9 +342,9 @@ int ld_net_train_step(ld_net *net, const int32_t *xsum, const uint8_t *labels, i
  * selected lanes on the road rows). */
 int ld_make_training_pairs(ld_net *net, const float *disp, const uint8_t *img, int32_t w, int32_t h_px,
                            int32_t n_frames, int32_t *xsum_out, uint8_t *labels_out, ld_lanes *lanes_out);
-/* The learned form of ld_detect.  logits == NULL runs the network; otherwise logits[n][mh][mw] are used
- * as given.  top_k in [1, LD_NET_TOPK_MAX]. */
-int ld_detect_learned(ld_net *net, const float *logits, const float *disp, const uint8_t *img, int32_t w,
+/* The learned form of ld_detect.  heatmap == NULL runs the network (heatmap sigmoid(z)); otherwise
+ * heatmap[n][mh][mw] is ranked with as given.  top_k in [1, LD_NET_TOPK_MAX]. */
+int ld_detect_learned(ld_net *net, const float *heatmap, const float *disp, const uint8_t *img, int32_t w,
                       int32_t h_px, int32_t n_frames, int32_t top_k, ld_lanes *out_lanes);
 /* Intermediate results of the last learned detection (synchronises the stream), as ld_debug_get. */
 size_t ld_net_debug_size(ld_net *net, int32_t stage);

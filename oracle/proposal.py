@@ -26,11 +26,13 @@ Readings
   on a road row (v_top <= v <= H-1, the column floor(u + 0.5) inside the image), else 0.
 * N5 loss.  Mean over all blocks of pw * y * softplus(-z) + (1 - y) * softplus(z) with pw = 10 (lane
   blocks are about one in a hundred).  Optimiser: Adam (Kingma & Ba, Algorithm 1).
-* N6 ranking.  Coarse start c covers the fine starts 4c..4c+3.  Its score sums z along the Eq. 25 track
-  taken in steps of four rows: u starts at (4c - S0) + 1.5 on row H-1, each step adds z at block
-  (v >> 2, floor(u + 0.5) >> 2) when that column is inside the image, then moves to row v - 4 with
-  u += 4 (V_px(v) - u) / (v - V_py(v)) (the line toward the vanishing point, as in Eq. 25), until v < v_top.
-  Float32, one fixed expression order, no fused multiply-add.
+* N6 ranking.  Coarse start c covers the fine starts 4c..4c+3.  Its score sums the heatmap p =
+  sigmoid(z) along the Eq. 25 track taken in steps of four rows: u starts at (4c - S0) + 1.5 on row H-1,
+  each step adds p at block (v >> 2, floor(u + 0.5) >> 2) when that column is inside the image, then
+  moves to row v - 4 with u += 4 (V_px(v) - u) / (v - V_py(v)) (the line toward the vanishing point, as in
+  Eq. 25), until v < v_top.  Float32, one fixed expression order, no fused multiply-add.  The heatmap, not
+  the logit, is summed: cells off the image add nothing, as they add nothing to an energy, and a sum of
+  logits (negative almost everywhere) would rank tracks that leave the image early above lanes.
 * N7 proposal.  The k best coarse starts (ties: smaller index first) give the candidate fine starts; each
   candidate and its two neighbours get exact Eq. 24 energies.  Local minima are tested only at candidates
   (both neighbours are then exact); the threshold, the ordering and the suppression are those of Alg. 7
@@ -252,11 +254,16 @@ def lane_labels(starts, Vpx, Vpy, v_top: int, H: int, W: int) -> np.ndarray:
     return Y
 
 
-def coarse_scores(z: np.ndarray, Vpx, Vpy, v_top: int, H: int, W: int, S0: int, n_starts: int) -> np.ndarray:
-    """N6: score of every coarse start c in [0, ceil(n_starts / 4))."""
+def heatmap(z: np.ndarray) -> np.ndarray:
+    """N2/N6: the per-cell lane probability sigmoid(z) (float64)."""
+    return sigmoid(np.asarray(z, np.float64))
+
+
+def coarse_scores(hm: np.ndarray, Vpx, Vpy, v_top: int, H: int, W: int, S0: int, n_starts: int) -> np.ndarray:
+    """N6: score of every coarse start c in [0, ceil(n_starts / 4)) from the float32 heatmap hm [h][w]."""
     nc = (n_starts + 3) // 4
     out = np.zeros(nc, np.float32)
-    zz = np.asarray(z, np.float32)
+    zz = np.asarray(hm, np.float32)
     for c in range(nc):
         u = _f(_f(4 * c - S0) + _f(1.5))
         acc = _f(0.0)

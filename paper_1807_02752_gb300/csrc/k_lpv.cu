@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kM1Threads = 512;
 constexpr int kEnThreads = 128;
-constexpr int kEnBatch = 8;    // track rows whose M_1 loads are in flight together
+constexpr int kEnBatchDefault = 8;    // track rows whose M_1 loads are in flight together
 constexpr int kSelThreads = 256;
 
 // k_m1 works on D(u, v) = M_0(u+1, v) - M_0(u-1, v).  An edge pixel at (u_e, v_e) adds g = G_x w_g to the
@@ -184,10 +184,14 @@ __global__ void __launch_bounds__(kM1Threads, 2) k_m1(const KParams kp, const Wo
 
 // MODE 0: every start of every frame; 1: the starts listed per frame (learned proposal); 2: every start of
 // the frames flagged LD_F_FALLBACK (the proposal selected no lane there).
+// A short list (MODE 1) is latency-bound: each start is a serial chain of divisions and gathers, so the
+// list form issues the M_1 loads of 32 rows at a time instead of 8 (fewer dependent round trips).
 template <int MODE>
-__global__ void __launch_bounds__(kEnThreads, 8) k_energy(const KParams kp, const Work w, const int32_t *elist,
-                                                          const int32_t *ecnt, int ecap)
+__global__ void __launch_bounds__(kEnThreads, MODE == 1 ? 2 : 8) k_energy(const KParams kp, const Work w,
+                                                                         const int32_t *elist, const int32_t *ecnt,
+                                                                         int ecap)
 {
+    constexpr int kEnBatch = MODE == 1 ? 32 : kEnBatchDefault;
     extern __shared__ float vrow[];   // [2][H]: V_px, V_py
     const int W = kp.W, H = kp.H;
     const int f = blockIdx.y;

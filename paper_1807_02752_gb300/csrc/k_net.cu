@@ -14,7 +14,7 @@
 //   k_loss      head, weighted logistic loss, dz, dS_4 and the head's gradient partials
 //   k_adam      Adam (Kingma & Ba, Algorithm 1) on the FP32 master weights, then the bf16 operand copies
 //   k_labels    training targets: cells crossed by the Eq. 25 tracks of the selected lanes
-//   k_score     coarse-start scores: z summed along the Eq. 25 track taken in steps of four rows
+//   k_score     coarse-start scores: the heatmap summed along the Eq. 25 track taken in steps of four rows
 //   k_topk      the k best coarse starts of a frame -> candidate and evaluated starts
 //
 // Data layout: cell maps are [n][mh][mw] with mh = ceil(H/4), mw = ceil(W/4); activations are bf16
@@ -56,6 +56,17 @@ __device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// first cell row a layer must produce for frame f, or INT_MAX when the frame needs nothing
+__device__ __forceinline__ int first_needed_row(const FrameState *fs, int f, int depth)
+{
+    if (!fs)
+        return 0;
+    const FrameState &s = fs[f];
+    if (s.flags & (LD_F_NO_ROAD | LD_F_DEGEN_Y | LD_F_DEGEN_X))
+        return 0x7fffffff;
+    return (s.v_top >> 2) - depth;
+}
+
 // network input of one cell: bf16(f32(sum) 2^-22), as a float
 __device__ __forceinline__ float cell_input(int32_t s)
 {
@@ -65,7 +76,8 @@ __device__ __forceinline__ float cell_input(int32_t s)
 // ---------------------------------------------------------------------------------------------------
 // layer 1: one input channel, K = 9, direct FMA per cell
 // ---------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCellThreads) k_conv1(const NetArgs a, const int32_t *xsum, int n)
+__global__ void __launch_bounds__(kCellThreads) k_conv1(const NetArgs a, const int32_t *xsum, int n,
+                                                        const FrameState *fs)
 {
     __shared__ float wsm[16 * 9 + 16];
     for (int i = threadIdx.x; i < 16 * 9; i += kCellThreads)
@@ -80,6 +92,8 @@ __global__ void __launch_bounds__(kCellThreads) k_conv1(const NetArgs a, const i
         const int x = (int)(p % mw);
         const int y = (int)((p / mw) % mh);
         const long long fb = p - (long long)y * mw - x;   // first cell of the frame
+        if (y < first_needed_row(fs, (int)(p / ((long long)mh * mw)), 3))
+            continue;
         float in[9];
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
@@ -118,9 +132,15 @@ struct ConvIO {
     const __nv_bfloat16 *mask;   // [n][mh][mw][COUT] activations whose sign gates the result (kEpiMask)
     const __nv_bfloat16 *wh;     // [16] head weights (kEpiHead)
     const float *bh;             // [1]
-    float *z;                    // [n][mh][mw] logits (kEpiHead)
+    float *z;                    // [n][mh][mw] logits, or the heatmap sigmoid(z) when heat (kEpiHead)
     int n, mh, mw, tiles_r, tiles_c;
+    int heat;
+    // road rows only (learned detection): frame f needs this layer's output rows >= (v_top >> 2) - depth;
+    // tiles entirely above, and frames without a road fit, are skipped (null: every tile)
+    const FrameState *fs;
+    int depth;
 };
+
 
 template <int CIN, int COUT>
 struct ConvSmem {
@@ -160,6 +180,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const ConvIO io)
     for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int f = tile / per_frame, rem = tile % per_frame;
         const int y0 = (rem / io.tiles_c) * kTileR, x0 = (rem % io.tiles_c) * kTileC;
+        if (y0 + kTileR - 1 < first_needed_row(io.fs, f, io.depth))
+            continue;   // uniform over the CTA
         __syncthreads();   // previous tile's reads of sin are done (and the weights are in place)
         constexpr int kChunks = CIN / 8;    // 16-byte chunks per cell
         for (int i = tid; i < kHaloR * kHaloC * kChunks; i += kConvThreads) {
@@ -240,8 +262,10 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const ConvIO io)
                 if (EPI == kEpiHead) {
                     zpart += __shfl_xor_sync(0xffffffffu, zpart, 1);
                     zpart += __shfl_xor_sync(0xffffffffu, zpart, 2);
-                    if (t == 0 && in_map)
-                        io.z[cell] = __fadd_rn(zpart, io.bh[0]);
+                    if (t == 0 && in_map) {
+                        const float zc = __fadd_rn(zpart, io.bh[0]);
+                        io.z[cell] = io.heat ? __frcp_rn(__fadd_rn(1.0f, expf(-zc))) : zc;
+                    }
                 }
             }
         }
@@ -572,7 +596,7 @@ __global__ void k_labels(const KParams kp, const Work w, const ld_lanes *lanes, 
     }
 }
 
-// one thread per (frame, coarse start c): z summed along the track in steps of four rows
+// one thread per (frame, coarse start c): the heatmap summed along the track in steps of four rows
 __global__ void __launch_bounds__(128) k_score(const KParams kp, const Work w, const float *z, float *scores,
                                                int mh, int mw)
 {
@@ -599,40 +623,104 @@ __global__ void __launch_bounds__(128) k_score(const KParams kp, const Work w, c
     scores[(size_t)f * nc + c] = acc;
 }
 
-// one CTA per frame: ranks of the coarse scores (ties to the smaller index), flags of candidate (bit 0)
-// and evaluated (bit 1) starts, and the ascending list of evaluated starts
+// one CTA per frame: the top_k coarse scores (ties to the smaller index), flags of candidate (bit 0) and
+// evaluated (bit 1) starts, and the ascending list of evaluated starts
 constexpr int kTopThreads = 256;
+
+// order-preserving integer key of a float score (-0 taken as +0, so equal scores give equal keys)
+__device__ __forceinline__ uint32_t order_key(float s)
+{
+    const uint32_t u = __float_as_uint(s == 0.0f ? 0.0f : s);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// sum of v over the CTA (every thread gets it); red holds kTopThreads / 32 ints
+__device__ __forceinline__ int cta_sum(int v, int *red)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, d);
+    __syncthreads();   // earlier readers of red are done
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kTopThreads / 32; ++k)
+        s += red[k];
+    return s;
+}
+
+// sum of v over the threads before this one
+__device__ __forceinline__ int cta_exclusive(int v, int *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d)
+            x += y;
+    }
+    __syncthreads();
+    if (lane == 31)
+        red[warp] = x;
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < warp; ++k)
+        before += red[k];
+    return before + x - v;
+}
 
 __global__ void __launch_bounds__(kTopThreads) k_topk(const KParams kp, const Work w, const float *scores, int top_k,
                                                       uint8_t *cflag, int32_t *elist, int32_t *ecnt, int ecap)
 {
     extern __shared__ __align__(16) unsigned char tsm[];
     const int f = blockIdx.x, ns = kp.n_starts, nc = (ns + 3) >> 2;
-    float *sc = reinterpret_cast<float *>(tsm);               // [nc]
-    uint8_t *fl = tsm + sizeof(float) * ((nc + 3) & ~3);       // [ns]
+    uint32_t *key = reinterpret_cast<uint32_t *>(tsm);        // [nc]
+    uint8_t *fl = tsm + sizeof(uint32_t) * ((nc + 3) & ~3);   // [ns]
     __shared__ int wsum[kTopThreads / 32];
+    __shared__ int red[kTopThreads / 32];
     __shared__ int base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool skip = w.fs[f].flags & LD_F_NO_LANES;
     for (int i = tid; i < nc; i += kTopThreads)
-        sc[i] = scores[(size_t)f * nc + i];
+        key[i] = order_key(scores[(size_t)f * nc + i]);
     for (int i = tid; i < ns; i += kTopThreads)
         fl[i] = 0;
     if (tid == 0)
         base = 0;
     __syncthreads();
     if (!skip) {
-        for (int c = tid; c < nc; c += kTopThreads) {
-            const float s = sc[c];
-            int rank = 0;
-            for (int o = 0; o < nc && rank < top_k; ++o) {
-                const float so = sc[o];
-                rank += (so > s) || (so == s && o < c);
-            }
-            if (rank < top_k)
-                for (int r = 0; r < 4; ++r)
-                    if (4 * c + r < ns)
-                        fl[4 * c + r] = 1;
+        // T = the k-th largest key, bit by bit from the top: the largest T with #(key >= T) >= k
+        const int k = top_k < nc ? top_k : nc;
+        const int per = (nc + kTopThreads - 1) / kTopThreads;   // contiguous chunks keep index order
+        const int c0 = tid * per < nc ? tid * per : nc, c1 = c0 + per < nc ? c0 + per : nc;
+        uint32_t T = 0;
+        for (int bit = 31; bit >= 0; --bit) {
+            const uint32_t cand = T | (1u << bit);
+            int cnt = 0;
+            for (int c = c0; c < c1; ++c)
+                cnt += key[c] >= cand;
+            if (cta_sum(cnt, red) >= k)
+                T = cand;
+        }
+        // every key above T is chosen; of the keys equal to T, the first k - #(key > T) in index order
+        int gt = 0, eq = 0;
+        for (int c = c0; c < c1; ++c) {
+            gt += key[c] > T;
+            eq += key[c] == T;
+        }
+        const int need = k - cta_sum(gt, red);
+        int r = cta_exclusive(eq, red);
+        for (int c = c0; c < c1; ++c) {
+            bool sel = key[c] > T;
+            if (key[c] == T)
+                sel = r++ < need;
+            if (sel)
+                for (int q = 0; q < 4; ++q)
+                    if (4 * c + q < ns)
+                        fl[4 * c + q] = 1;
         }
     }
     __syncthreads();
@@ -676,8 +764,8 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const KParams kp, const Wo
 // ---------------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------------
-// Every kernel here stays under the default 48 KB of dynamic shared memory (k_topk: 2.5 bytes per start,
-// at most 30 KB for the widest frame), so no opt-in is needed.
+// Every kernel here stays under the default 48 KB of dynamic shared memory (k_topk: 2 bytes per start,
+// at most 25 KB for the widest frame), so no opt-in is needed.
 
 static int grid_for(int tiles, int per_sm)
 {
@@ -693,11 +781,12 @@ static cudaError_t conv(const ConvIO &io, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, bool keep_a4, cudaStream_t s)
+cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, bool keep_a4, bool heat,
+                        cudaStream_t s, const FrameState *road)
 {
     const long long cells = (long long)n * a.mh * a.mw;
     const int g1 = (int)((cells + kCellThreads - 1) / kCellThreads);
-    k_conv1<<<g1 < 152 * 8 ? g1 : 152 * 8, kCellThreads, 0, s>>>(a, xsum, n);
+    k_conv1<<<g1 < 152 * 8 ? g1 : 152 * 8, kCellThreads, 0, s>>>(a, xsum, n, road);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -707,18 +796,22 @@ cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, 
     io.mw = a.mw;
     io.tiles_r = (a.mh + kTileR - 1) / kTileR;
     io.tiles_c = (a.mw + kTileC - 1) / kTileC;
+    io.fs = road;
     io.in = a.act[0];
     io.wt = a.wf[1];
     io.bias = a.bias[1];
     io.out = a.act[1];
+    io.depth = 2;
     if ((e = conv<16, 32, kEpiRelu>(io, s)) != cudaSuccess)
         return e;
     io.in = a.act[1];
     io.wt = a.wf[2];
     io.bias = a.bias[2];
     io.out = a.act[2];
+    io.depth = 1;
     if ((e = conv<32, 32, kEpiRelu>(io, s)) != cudaSuccess)
         return e;
+    io.depth = 0;
     io.in = a.act[2];
     io.wt = a.wf[3];
     io.bias = a.bias[3];
@@ -726,6 +819,7 @@ cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, 
     io.wh = a.whb;
     io.bh = a.bh;
     io.z = z;
+    io.heat = heat ? 1 : 0;
     return conv<32, 16, kEpiHead>(io, s);
 }
 

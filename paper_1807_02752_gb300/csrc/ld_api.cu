@@ -364,12 +364,16 @@ KParams handle_call(ld_handle *h, int w, int hh, int n)
     h->have_last = true;
     return make_kparams(h, w, hh, n);
 }
-// launches [first, last) of the plain sequence (0 k_vdisp ... 6 k_m1, 7 k_energy, 8 k_select), eager
+KParams handle_kparams(const ld_handle *h, int w, int hh, int n) { return make_kparams(h, w, hh, n); }
+// launches [first, last) of the plain sequence (0 k_vdisp ... 6 k_m1, 7 k_energy, 8 k_select) on stream s
+// (null: the handle's stream)
 int handle_enqueue(ld_handle *h, const KParams &kp, const Work &w, const float *disp, const uint8_t *img,
-                   ld_lanes *out, int first, int last)
+                   ld_lanes *out, int first, int last, cudaStream_t s)
 {
-    return enqueue_range(h, kp, w, disp, img, out, h->stream, false, first, last);
+    return enqueue_range(h, kp, w, disp, img, out, s ? s : h->stream, false, first, last);
 }
+// the workspace seen from frame f0 of a call on frames of kp's size
+Work work_view(const Work &w, const KParams &kp, int f0) { return work_from(w, kp, f0); }
 }  // namespace ld
 
 extern "C" {

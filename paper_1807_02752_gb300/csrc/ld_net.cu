@@ -9,8 +9,24 @@
 
 #include "ld_net.cuh"
 
+namespace {
+constexpr int kLearnedGraphs = 4;
+constexpr int kLearnedSplitMin = 16;   // captured calls of at least this many frames run as two halves
+
+struct LearnedGraph {
+    const void *disp = nullptr, *img = nullptr, *heat = nullptr;
+    void *out = nullptr;
+    int w = 0, h = 0, n = 0, k = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+}  // namespace
+
 struct ld_net {
     ld_handle *h = nullptr;
+    LearnedGraph graphs[kLearnedGraphs];
+    int next_graph = 0;
+    cudaStream_t sub[2] = {};
+    cudaEvent_t fork = nullptr, join[2] = {};
     int training = 0;
     int max_mh = 0, max_mw = 0, max_n = 0, max_ns = 0;
     void *mem = nullptr;
@@ -68,6 +84,52 @@ ld::NetArgs args_for(const ld_net *net, int w, int hh)
     a.mh = (hh + 3) / 4;
     a.mw = (w + 3) / 4;
     return a;
+}
+
+// Frames [f0, f0 + nk) of a learned detection of n frames on stream s: block sums and the plain stages up
+// to M_1, the network on the road rows (or the given heatmap), ranking, energies of the proposed starts,
+// selection among them, and the exhaustive search of the frames where that found no lane.
+int enqueue_learned(ld_net *net, const float *heatmap, const float *disp, const uint8_t *img, int w, int hh, int f0,
+                    int nk, int n, int top_k, ld_lanes *out, cudaStream_t s)
+{
+    ld_handle *h = net->h;
+    const ld::KParams kfull = ld::handle_kparams(h, w, hh, n);
+    const ld::KParams kp = ld::handle_kparams(h, w, hh, nk);
+    ld::Work base = ld::handle_work(h);
+    base.xsum = net->xsum;
+    const ld::Work wk = ld::work_view(base, kfull, f0);
+    ld::NetArgs a = args_for(net, w, hh);
+    const size_t cells = (size_t)a.mh * a.mw, fo = f0;
+    for (int l = 0; l < 3; ++l)
+        a.act[l] += fo * cells * ld::net_ch(l + 1);
+    const int ecap = ld::kEvalPerTop * top_k;
+    const int nc = (kp.n_starts + 3) / 4;
+    float *z = net->z + fo * cells;
+    const size_t px = fo * w * hh;
+    cudaError_t e = cudaMemsetAsync(wk.xsum, 0, sizeof(int32_t) * nk * cells, s);
+    if (e != cudaSuccess)
+        return ncuda(net, e, "block sums");
+    int rc = ld::handle_enqueue(h, kp, wk, disp + px, img + px, out + f0, 0, 7, s);   // k_vdisp .. k_m1
+    if (rc != LD_OK)
+        return nfail(net, rc, ld_last_error(h));
+    if (!heatmap)
+        e = ld::net_forward(a, wk.xsum, nk, z, false, true, s, wk.fs);
+    else
+        e = cudaMemcpyAsync(z, heatmap + fo * cells, sizeof(float) * nk * cells, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess)
+        return ncuda(net, e, "network forward");
+    uint8_t *cflag = net->cflag + fo * kp.n_starts;
+    int32_t *elist = net->elist + fo * ecap, *ecnt = net->ecnt + fo;
+    e = ld::net_propose(kp, wk, z, a.mh, a.mw, top_k, net->scores + fo * nc, cflag, elist, ecnt, ecap, s);
+    if (e == cudaSuccess)
+        e = ld::launch_energy_list(kp, wk, elist, ecnt, ecap, s);
+    if (e == cudaSuccess)
+        e = ld::launch_select_set(kp, wk, cflag, out + f0, s);
+    if (e == cudaSuccess)
+        e = ld::launch_energy_fallback(kp, wk, s);
+    if (e == cudaSuccess)
+        e = ld::launch_select_fallback(kp, wk, out + f0, s);
+    return e == cudaSuccess ? LD_OK : ncuda(net, e, "proposal");
 }
 
 }  // namespace
@@ -164,6 +226,18 @@ int ld_net_create(ld_handle *h, int32_t training, ld_net **out)
         delete net;
         return LD_E_CUDA;
     }
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&net->fork, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&net->sub[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&net->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        ncuda(nullptr, e, "stream and event creation");
+        ld_net_destroy(net);
+        return LD_E_CUDA;
+    }
     *out = net;
     return LD_OK;
 }
@@ -201,7 +275,7 @@ int ld_net_forward(ld_net *net, const int32_t *xsum, int32_t w, int32_t hh, int3
     int rc = check_map(net, w, hh, n);
     if (rc != LD_OK)
         return rc;
-    cudaError_t e = ld::net_forward(args_for(net, w, hh), xsum, n, logits, false, ld::handle_stream(net->h));
+    cudaError_t e = ld::net_forward(args_for(net, w, hh), xsum, n, logits, false, false, ld::handle_stream(net->h));
     return e == cudaSuccess ? LD_OK : ncuda(net, e, "network forward");
 }
 
@@ -217,7 +291,7 @@ int ld_net_grad(ld_net *net, const int32_t *xsum, const uint8_t *labels, int32_t
         return rc;
     const ld::NetArgs a = args_for(net, w, hh);
     cudaStream_t s = ld::handle_stream(net->h);
-    cudaError_t e = ld::net_forward(a, xsum, n, net->z, true, s);
+    cudaError_t e = ld::net_forward(a, xsum, n, net->z, true, false, s);
     if (e == cudaSuccess)
         e = ld::net_backward(a, labels, n, ld::kPosWeight, grad, loss, s);
     return e == cudaSuccess ? LD_OK : ncuda(net, e, "network gradient");
@@ -272,7 +346,7 @@ int ld_make_training_pairs(ld_net *net, const float *disp, const uint8_t *img, i
     return e == cudaSuccess ? LD_OK : ncuda(net, e, "labels");
 }
 
-int ld_detect_learned(ld_net *net, const float *logits, const float *disp, const uint8_t *img, int32_t w, int32_t hh,
+int ld_detect_learned(ld_net *net, const float *heatmap, const float *disp, const uint8_t *img, int32_t w, int32_t hh,
                       int32_t n, int32_t top_k, ld_lanes *out)
 {
     if (!net)
@@ -283,43 +357,64 @@ int ld_detect_learned(ld_net *net, const float *logits, const float *disp, const
     int rc = ld::handle_check(h, disp, img, w, hh, n, out);
     if (rc != LD_OK)
         return nfail(net, rc, ld_last_error(h));
-    const ld::KParams kp = ld::handle_call(h, w, hh, n);
-    ld::Work wk = ld::handle_work(h);
-    wk.xsum = net->xsum;
-    const ld::NetArgs a = args_for(net, w, hh);
-    cudaStream_t s = ld::handle_stream(h);
-    cudaError_t e = cudaMemsetAsync(net->xsum, 0, sizeof(int32_t) * (size_t)n * a.mh * a.mw, s);
-    if (e != cudaSuccess)
-        return ncuda(net, e, "block sums");
-    rc = ld::handle_enqueue(h, kp, wk, disp, img, out, 0, 7);   // k_vdisp .. k_m1
-    if (rc != LD_OK)
-        return nfail(net, rc, ld_last_error(h));
-    const float *z = logits;
-    if (!z) {
-        if ((e = ld::net_forward(a, net->xsum, n, net->z, false, s)) != cudaSuccess)
-            return ncuda(net, e, "network forward");
-        z = net->z;
-    } else if ((e = cudaMemcpyAsync(net->z, logits, sizeof(float) * (size_t)n * a.mh * a.mw, cudaMemcpyDeviceToDevice,
-                                    s)) != cudaSuccess) {
-        return ncuda(net, e, "logits copy");
-    }
-    const int ecap = ld::kEvalPerTop * top_k;
-    e = ld::net_propose(kp, wk, z, a.mh, a.mw, top_k, net->scores, net->cflag, net->elist, net->ecnt, ecap, s);
-    if (e == cudaSuccess)
-        e = ld::launch_energy_list(kp, wk, net->elist, net->ecnt, ecap, s);
-    if (e == cudaSuccess)
-        e = ld::launch_select_set(kp, wk, net->cflag, out, s);
-    if (e == cudaSuccess)
-        e = ld::launch_energy_fallback(kp, wk, s);
-    if (e == cudaSuccess)
-        e = ld::launch_select_fallback(kp, wk, out, s);
-    if (e != cudaSuccess)
-        return ncuda(net, e, "proposal");
+    ld::handle_call(h, w, hh, n);
     net->last_w = w;
     net->last_h = hh;
     net->last_n = n;
     net->have_last = true;
-    return LD_OK;
+    cudaStream_t s = ld::handle_stream(h);
+    for (LearnedGraph &g : net->graphs)
+        if (g.exec && g.disp == disp && g.img == img && g.heat == heatmap && g.out == out && g.w == w && g.h == hh &&
+            g.n == n && g.k == top_k) {
+            cudaError_t e = cudaGraphLaunch(g.exec, s);
+            return e == cudaSuccess ? LD_OK : ncuda(net, e, "graph launch");
+        }
+    cudaStreamCaptureStatus st;
+    cudaError_t e = cudaStreamIsCapturing(s, &st);
+    if (e != cudaSuccess)
+        return ncuda(net, e, "stream query");
+    if (st != cudaStreamCaptureStatusNone || s == nullptr)   // the caller captures, or the legacy stream
+        return enqueue_learned(net, heatmap, disp, img, w, hh, 0, n, n, top_k, out, s);
+    if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return ncuda(net, e, "begin capture");
+    if (n >= kLearnedSplitMin) {
+        // two half-batches on the network's sub-streams, forked from and joined back to the handle's stream
+        rc = (e = cudaEventRecord(net->fork, s)) == cudaSuccess ? LD_OK : ncuda(net, e, "fork");
+        const int n0 = (n + 1) / 2;
+        for (int k = 0; k < 2 && rc == LD_OK; ++k) {
+            if ((e = cudaStreamWaitEvent(net->sub[k], net->fork, 0)) != cudaSuccess) {
+                rc = ncuda(net, e, "fork wait");
+                break;
+            }
+            rc = enqueue_learned(net, heatmap, disp, img, w, hh, k ? n0 : 0, k ? n - n0 : n0, n, top_k, out, net->sub[k]);
+            if (rc == LD_OK && ((e = cudaEventRecord(net->join[k], net->sub[k])) != cudaSuccess ||
+                                (e = cudaStreamWaitEvent(s, net->join[k], 0)) != cudaSuccess))
+                rc = ncuda(net, e, "join");
+        }
+    } else {
+        rc = enqueue_learned(net, heatmap, disp, img, w, hh, 0, n, n, top_k, out, s);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    if (rc != LD_OK) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess)
+        return ncuda(net, e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return ncuda(net, e, "graph instantiate");
+    LearnedGraph &g = net->graphs[net->next_graph];
+    net->next_graph = (net->next_graph + 1) % kLearnedGraphs;
+    if (g.exec)
+        cudaGraphExecDestroy(g.exec);
+    g = LearnedGraph{disp, img, heatmap, out, w, hh, n, top_k, exec};
+    e = cudaGraphLaunch(exec, s);
+    return e == cudaSuccess ? LD_OK : ncuda(net, e, "graph launch");
 }
 
 size_t ld_net_debug_size(ld_net *net, int32_t stage)
@@ -330,7 +425,7 @@ size_t ld_net_debug_size(ld_net *net, int32_t stage)
     const size_t ns = (size_t)ld_n_starts(&ld::handle_params(net->h), net->last_w);
     switch (stage) {
     case LD_NET_STAGE_XSUM: return cells * 4;
-    case LD_NET_STAGE_LOGITS: return cells * 4;
+    case LD_NET_STAGE_HEATMAP: return cells * 4;
     case LD_NET_STAGE_SCORES: return (ns + 3) / 4 * 4;
     case LD_NET_STAGE_CFLAG: return ns;
     default: return 0;
@@ -355,7 +450,7 @@ int ld_net_debug_get(ld_net *net, int32_t frame, int32_t stage, void *host_dst, 
     const void *src = nullptr;
     switch (stage) {
     case LD_NET_STAGE_XSUM: src = net->xsum + f * (want / 4); break;
-    case LD_NET_STAGE_LOGITS: src = net->z + f * (want / 4); break;
+    case LD_NET_STAGE_HEATMAP: src = net->z + f * (want / 4); break;
     case LD_NET_STAGE_SCORES: src = net->scores + f * (want / 4); break;
     default: src = net->cflag + f * want; break;
     }
@@ -370,6 +465,17 @@ void ld_net_destroy(ld_net *net)
     if (!net)
         return;
     cudaStreamSynchronize(ld::handle_stream(net->h));
+    for (LearnedGraph &g : net->graphs)
+        if (g.exec)
+            cudaGraphExecDestroy(g.exec);
+    if (net->fork)
+        cudaEventDestroy(net->fork);
+    for (int k = 0; k < 2; ++k) {
+        if (net->join[k])
+            cudaEventDestroy(net->join[k]);
+        if (net->sub[k])
+            cudaStreamDestroy(net->sub[k]);
+    }
     cudaFree(net->mem);
     delete net;
 }

@@ -34,7 +34,10 @@ struct NetArgs {
     float *part_head;               // loss partials [608][18]
 };
 
-cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, bool keep_a4, cudaStream_t s);
+// logits (heat = false) or the heatmap sigmoid(z) of every cell; with road (the frames' fit states) only
+// the cells on and just above each frame's road rows (v >= v_top), and nothing for frames without a road
+cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, bool keep_a4, bool heat,
+                        cudaStream_t s, const FrameState *road = nullptr);
 cudaError_t net_backward(const NetArgs &a, const uint8_t *labels, int n, float pw, float *grad, float *loss,
                          cudaStream_t s);
 cudaError_t net_pack(const NetArgs &a, cudaStream_t s);
@@ -54,7 +57,9 @@ const ld_params &handle_params(const ld_handle *h);
 cudaStream_t handle_stream(const ld_handle *h);
 Work handle_work(const ld_handle *h);
 KParams handle_call(ld_handle *h, int w, int hh, int n);
+KParams handle_kparams(const ld_handle *h, int w, int hh, int n);
 int handle_enqueue(ld_handle *h, const KParams &kp, const Work &w, const float *disp, const uint8_t *img,
-                   ld_lanes *out, int first, int last);
+                   ld_lanes *out, int first, int last, cudaStream_t s = nullptr);
+Work work_view(const Work &w, const KParams &kp, int f0);
 
 }  // namespace ld

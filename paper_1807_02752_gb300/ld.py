@@ -18,7 +18,7 @@ LD_STATIC_SCRATCH_BYTES = 8 << 20
 OK, E_ARG, E_CUDA, E_NOMEM, E_STATE = 0, -1, -2, -3, -4
 F_NO_ROAD, F_CAP_Y, F_DEGEN_Y, F_CAP_X, F_DEGEN_X, F_NO_LANES, F_FALLBACK = 1, 2, 4, 8, 16, 32, 64
 NET_PARAMS, NET_TOPK_MAX = 18689, 256
-NET_STAGE_XSUM, NET_STAGE_LOGITS, NET_STAGE_SCORES, NET_STAGE_CFLAG = 1, 2, 3, 4
+NET_STAGE_XSUM, NET_STAGE_HEATMAP, NET_STAGE_SCORES, NET_STAGE_CFLAG = 1, 2, 3, 4
 STAGE_VDISP, STAGE_PATH_Y, STAGE_INL_Y, STAGE_ROWS, STAGE_EDGES, STAGE_PATH_X, STAGE_INL_X, STAGE_M1, STAGE_HE = range(1, 10)
 
 
@@ -458,12 +458,12 @@ class Net:
                                                   lb.data_ptr(), ln.data_ptr()))
         return xs, lb, ln
 
-    def detect(self, disp, img, top_k: int = 32, logits=None, out=None):
-        """Learned form of Detector.detect (device tensors); logits [n][mh][mw] replace the network's."""
+    def detect(self, disp, img, top_k: int = 32, heatmap=None, out=None):
+        """Learned form of Detector.detect (device tensors); heatmap [n][mh][mw] replaces the network's."""
         n, H, W = disp.shape
         out = self.det.alloc_lanes(n) if out is None else out
-        self._check(self.L.ld_detect_learned(self.h, None if logits is None else logits.data_ptr(), disp.data_ptr(),
-                                             img.data_ptr(), W, H, n, top_k, out.data_ptr()))
+        self._check(self.L.ld_detect_learned(self.h, None if heatmap is None else heatmap.data_ptr(),
+                                             disp.data_ptr(), img.data_ptr(), W, H, n, top_k, out.data_ptr()))
         return out
 
     def debug(self, frame: int, stage: int):
@@ -472,7 +472,7 @@ class Net:
         self._check(self.L.ld_net_debug_get(self.h, frame, stage, buf.ctypes.data, size))
         if stage in (NET_STAGE_XSUM,):
             return buf.view(np.int32)
-        if stage in (NET_STAGE_LOGITS, NET_STAGE_SCORES):
+        if stage in (NET_STAGE_HEATMAP, NET_STAGE_SCORES):
             return buf.view(np.float32)
         return buf
 

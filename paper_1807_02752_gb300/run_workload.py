@@ -2,12 +2,16 @@
 that a profiler attached to the process sees every kernel of every call as a separate launch.
 
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4
+    python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4 learned 64
 
 Each call launches the nine kernels of the path once, in order, on the handle's stream, and times each
-with CUDA events; the per-kernel times of the last call are printed.
+with CUDA events; the per-kernel times of the last call are printed.  With `learned [top_k]` each call is
+the learned form instead (the network with the package's trained weights ranks the starts; exact
+energies for the top_k coarse starts), timed as a whole.
 """
 from __future__ import annotations
 
+import os
 import sys
 
 
@@ -20,6 +24,8 @@ def main(argv=None):
     argv = sys.argv[1:] if argv is None else argv
     name = argv[0] if argv else "batch64_1242x375"
     calls = int(argv[1]) if len(argv) > 1 else 4
+    learned = len(argv) > 2 and argv[2] == "learned"
+    top_k = int(argv[3]) if len(argv) > 3 else 64
     if name not in scenes.WORKLOADS:
         raise SystemExit(f"unknown workload {name!r}; known: {', '.join(scenes.WORKLOADS)}")
     cfg, n = scenes.WORKLOADS[name]
@@ -29,11 +35,26 @@ def main(argv=None):
     d = torch.from_numpy(disp).cuda()
     i = torch.from_numpy(img).cuda()
     out = det.alloc_lanes(n)
-    ms = None
-    for _ in range(calls):
-        ms = det.detect_timed(d, i, out)
-    torch.cuda.synchronize()
-    print(name, n, "frames:", {k: round(float(x), 4) for k, x in zip(ld.launch_names(), np.asarray(ms))})
+    if learned:
+        net = ld.Net(det)
+        w = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "proposal_weights.npy"))
+        net.set_params(torch.from_numpy(w.astype(np.float32)).cuda())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(calls):
+            e0.record()
+            net.detect(d, i, top_k, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        print(name, n, "frames, learned form, top_k", top_k, "ms per call:", [round(x, 4) for x in ms])
+        net.close()
+    else:
+        ms = None
+        for _ in range(calls):
+            ms = det.detect_timed(d, i, out)
+        torch.cuda.synchronize()
+        print(name, n, "frames:", {k: round(float(x), 4) for k, x in zip(ld.launch_names(), np.asarray(ms))})
     det.close()
 
 

@@ -1,7 +1,7 @@
 """GPU parity of the learned lane-position proposal (ld_net_*, ld_detect_learned) against oracle/proposal.py.
 
 Exact: the block sums of |G_x w_g|, the training labels, the coarse-start scores (one float32 expression
-order on both sides), the candidate and evaluated sets, and the lanes chosen from given logits.
+order on both sides), the candidate and evaluated sets, and the lanes chosen from a given heatmap.
 Tolerances (network arithmetic): the kernels sum bf16 products in float32 in another order than the
 oracle's float64 sums.  The two sums of a 288-term dot product differ by about 2e-5 relative, against a
 bf16 spacing of 2^-8, so about one stored activation in a hundred rounds to the neighbouring bf16 value
@@ -155,12 +155,12 @@ def test_adam_matches_oracle(torch_cuda):
     det.close()
 
 
-def _truth_logits(truths, cfg, S0):
-    """Seeded input logits that favour the generator's planted lanes: +3 on cells crossed by the planted
-    markings' tracks toward the planted vanishing points, -3 elsewhere."""
+def _truth_heatmap(truths, cfg):
+    """Input heatmaps that favour the generator's planted lanes: 1 on cells crossed by the planted
+    markings' tracks toward the planted vanishing points, 0 elsewhere."""
     H, W = cfg.height, cfg.width
     mh, mw = P.map_shape(H, W)
-    out = np.full((len(truths), mh, mw), -3.0, np.float32)
+    out = np.zeros((len(truths), mh, mw), np.float32)
     for f, t in enumerate(truths):
         for s in t.lane_starts:
             u = float(s)
@@ -169,7 +169,7 @@ def _truth_logits(truths, cfg, S0):
                     break
                 c = int(np.floor(u + 0.5))
                 if 0 <= c < W:
-                    out[f, v >> 2, c >> 2] = 3.0
+                    out[f, v >> 2, c >> 2] = 1.0
                 u = u + (t.vpx[v] - u) / (v - t.vpy[v])
     return out
 
@@ -194,7 +194,7 @@ def _oracle_learned(r, z, cfg, op, top_k):
 
 @pytest.mark.parametrize("name,n,top_k", [("small_320x120", 6, 4), ("small_320x120", 6, 32),
                                           ("single_1242x375", 2, 32), ("single_1242x375", 2, 3)])
-def test_proposal_from_given_logits_matches_oracle(torch_cuda, name, n, top_k):
+def test_proposal_from_given_heatmap_matches_oracle(torch_cuda, name, n, top_k):
     torch = torch_cuda
     cfg, _ = scenes.WORKLOADS[name]
     disp, img, truths = _frames(cfg, n, first=31)
@@ -202,17 +202,17 @@ def test_proposal_from_given_logits_matches_oracle(torch_cuda, name, n, top_k):
     op = oracle.default_params(n_disp=cfg.n_disp)
     det = ld.Detector(cfg.width, cfg.height, n, p)
     net = ld.Net(det)
-    ns = det.n_starts(cfg.width)
     rng = np.random.default_rng(9)
     mh, mw = P.map_shape(cfg.height, cfg.width)
-    cases = [_truth_logits(truths, cfg, (ns - cfg.width) // 2),                   # informative
-             rng.standard_normal((n, mh, mw)).astype(np.float32),                  # noise
-             -_truth_logits(truths, cfg, (ns - cfg.width) // 2)]                   # adversarial
+    truth = _truth_heatmap(truths, cfg)
+    cases = [truth,                                                   # informative
+             rng.random((n, mh, mw)).astype(np.float32),              # noise
+             1.0 - truth]                                             # adversarial
     d, i = torch.from_numpy(disp).cuda(), torch.from_numpy(img).cuda()
     rs = _oracle_frames(disp, img, op)
     fallbacks = 0
     for z in cases:
-        out = net.detect(d, i, top_k=top_k, logits=torch.from_numpy(z).cuda())
+        out = net.detect(d, i, top_k=top_k, heatmap=torch.from_numpy(z).cuda())
         torch.cuda.synchronize()
         got = ld.Detector.lanes(out)
         for f, r in enumerate(rs):
@@ -249,8 +249,46 @@ def test_learned_form_with_every_start_equals_plain(torch_cuda, name, n):
         assert plain.tobytes() == learned.tobytes()
     small_k = ld.Detector.lanes(net.detect(d, i, top_k=8))
     torch.cuda.synchronize()
+    # the heatmap the learned detection ranked with is sigmoid of the network's logits on the road rows
+    # (cells v >= v_top; the rest of the map is not computed)
+    xs = torch.from_numpy(np.stack([net.debug(f, ld.NET_STAGE_XSUM) for f in range(n)])).cuda()
+    mh, mw = P.map_shape(cfg.height, cfg.width)
+    z = net.forward(xs.reshape(n, mh, mw), cfg.width, cfg.height).cpu().numpy().reshape(n, mh, mw)
+    for f in range(n):
+        if plain[f]["flags"] & (ld.F_NO_ROAD | ld.F_DEGEN_Y | ld.F_DEGEN_X):
+            continue
+        r0 = int(plain[f]["v_top"]) >> 2
+        hm = net.debug(f, ld.NET_STAGE_HEATMAP).reshape(mh, mw)
+        assert np.allclose(hm[r0:], P.heatmap(z[f, r0:]), rtol=1e-6, atol=1e-7)
     for f in range(n):   # any k: a frame either keeps lanes found among its candidates or falls back
         ok = small_k[f]["flags"] & ld.F_FALLBACK or small_k[f]["n_lanes"] > 0 or plain[f]["flags"] & ld.F_NO_LANES
         assert ok
     net.close()
     det.close()
+
+
+def test_captured_split_learned_form_equals_eager(torch_cuda):
+    """On a stream of its own a learned detection of 16+ frames is captured as two concurrent half-batches;
+    its results are the eager call's, byte for byte (trained weights of the package)."""
+    import os
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS["batch64_1242x375"]
+    n = 20
+    disp, img, _ = _frames(cfg, n, first=51)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    theta = np.load(os.path.join(os.path.dirname(ld.__file__), "proposal_weights.npy")).astype(np.float32)
+    d, i = torch.from_numpy(disp).cuda(), torch.from_numpy(img).cuda()
+    results = []
+    for stream in (None, torch.cuda.Stream()):
+        det = ld.Detector(cfg.width, cfg.height, n, p, stream=stream)
+        net = ld.Net(det)
+        with torch.cuda.stream(stream or torch.cuda.current_stream()):
+            net.set_params(torch.from_numpy(theta).cuda())
+            out = det.alloc_lanes(n)
+            for _ in range(3):          # capture, then two replays
+                net.detect(d, i, top_k=32, out=out)
+        torch.cuda.synchronize()
+        results.append(ld.Detector.lanes(out).tobytes())
+        net.close()
+        det.close()
+    assert results[0] == results[1]
