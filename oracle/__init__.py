@@ -42,7 +42,8 @@ class Params(C.Structure):
         ("tr_x", C.c_float), ("sigma_g", C.c_double), ("box_nu", C.c_int32), ("box_vs", C.c_int32),
         ("lambda_g", C.c_int32), ("xi_num", C.c_int32), ("xi_den", C.c_int32), ("thr_num", C.c_int32),
         ("thr_den", C.c_int32), ("near_px", C.c_int32), ("max_lanes", C.c_int32), ("ransac_hyps", C.c_int32),
-        ("ransac_rounds", C.c_int32), ("seed", C.c_uint64),
+        ("ransac_rounds", C.c_int32), ("seed", C.c_uint64), ("wg_gaussian", C.c_int32), ("pad0", C.c_int32),
+        ("thr_abs", C.c_int64),
     ]
 
     def as_dict(self):
@@ -87,6 +88,7 @@ def lib():
         L.or_ransac.argtypes = [p, p, i32, i32, C.c_float, i32, C.POINTER(Params), i32, i32, p, p, p]
         L.or_ransac.restype = i32
         L.or_bilateral.argtypes = [p, i32, i32, C.POINTER(Params), p]
+        L.or_median.argtypes = [p, i32, i32, i32, p]
         L.or_sobel.argtypes = [p, i32, i32, p, p]
         L.or_band.argtypes = [p, i32, i32, i32, i32, i32, p]
         L.or_dp_vpx.argtypes = [p, i32, i32, i32, i32, i32, p]
@@ -200,6 +202,14 @@ def bilateral(img: np.ndarray, p: Params | None = None) -> np.ndarray:
     H, W = im.shape
     out = np.zeros_like(im)
     lib().or_bilateral(_ptr(im), W, H, C.byref(p), _ptr(out))
+    return out
+
+
+def median(img: np.ndarray, rho: int = 5) -> np.ndarray:
+    im = np.ascontiguousarray(img, np.uint8)
+    H, W = im.shape
+    out = np.zeros_like(im)
+    lib().or_median(_ptr(im), W, H, rho, _ptr(out))
     return out
 
 

@@ -52,6 +52,9 @@ void or_default_params(or_params *p)
     p->ransac_hyps = 64;
     p->ransac_rounds = 64;
     p->seed = 0x1807027520ull;
+    p->wg_gaussian = 0;
+    p->pad0 = 0;
+    p->thr_abs = 0;
 }
 
 /* Sec. 2.4 and Alg. 7: the histogram H spans starts u in [-xi W, (1 + xi) W) (xi = 0.5). */
@@ -89,7 +92,9 @@ void or_tables(const or_params *p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_q)
     if (wg_q) {
         for (int32_t i = 0; i <= 16384; i++) {
             double dtheta = asin((double)i / 32768.0);
-            double w = exp(-(dtheta / (p->sigma_g * p->sigma_g)) * (36.0 / M_PI));
+            double pp = dtheta * (36.0 / M_PI);   /* p = dtheta / theta_s, theta_s = pi / 36 */
+            double w = p->wg_gaussian ? exp(-(pp * pp) / (p->sigma_g * p->sigma_g))
+                                      : exp(-pp / (p->sigma_g * p->sigma_g));
             wg_q[i] = (int32_t)floor(w * 4096.0 + 0.5);
         }
     }
@@ -408,6 +413,28 @@ int32_t or_ransac(const int32_t *x, const int32_t *y, int32_t n, int32_t m, floa
 }
 
 /* ------------------------------------------------------------------------------------------------ */
+/* Median filter (the pre-filter the paper compares the bilateral with, Sec. 2.3.1): the lower median  */
+/* of the window's taps inside the image, i.e. the ((n + 1) / 2)-th smallest of the n taps (n odd for  */
+/* every interior pixel, so the middle value there), found by sorting the taps.                     */
+/* ------------------------------------------------------------------------------------------------ */
+static int cmp_u8(const void *a, const void *b) { return (int)*(const uint8_t *)a - (int)*(const uint8_t *)b; }
+
+void or_median(const uint8_t *img, int32_t W, int32_t H, int32_t rho, uint8_t *out)
+{
+    uint8_t win[(2 * 16 + 1) * (2 * 16 + 1)];
+    for (int32_t v = 0; v < H; v++)
+        for (int32_t u = 0; u < W; u++) {
+            int32_t n = 0;
+            for (int32_t y = v - rho; y <= v + rho; y++)
+                for (int32_t x = u - rho; x <= u + rho; x++)
+                    if (y >= 0 && y < H && x >= 0 && x < W)
+                        win[n++] = img[(size_t)y * W + x];
+            qsort(win, (size_t)n, 1, cmp_u8);
+            out[(size_t)v * W + u] = win[(n + 1) / 2 - 1];
+        }
+}
+
+/* ------------------------------------------------------------------------------------------------ */
 /* Eq. 15-16: bilateral filter over a (2 rho + 1)^2 window, clipped at the image border.            */
 /* Weights per tap: w = (ws_q * wr_q[|I(i,j) - I(u,v)|] + 2^14) >> 15 (Q15).  The output is the      */
 /* weighted mean rounded half up: (2 sum(w I) + sum(w)) / (2 sum(w)), an exact integer expression.   */
@@ -613,7 +640,7 @@ void or_select(const int64_t *he, int32_t n_starts, int32_t S0, const or_params 
         out->flags |= OR_F_NO_LANES;
         return;
     }
-    int64_t t = -(((-mn) * p->thr_num) / p->thr_den);
+    int64_t t = p->thr_abs != 0 ? p->thr_abs : -(((-mn) * p->thr_num) / p->thr_den);
     int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * n_starts);
     int32_t nc = 0;
     for (int32_t i = 1; i < n_starts - 1; i++)
@@ -753,7 +780,9 @@ int32_t or_detect(const float *disp, const uint8_t *img, int32_t W, int32_t H, c
     /* ---- Sec. 2.3.1: road mask, bilateral filter, Sobel edges, sparse V_px votes ---- */
     {
         uint8_t *Ibf = (uint8_t *)malloc(WH);
-        if (p->bilateral)
+        if (p->bilateral == 2)
+            or_median(img, W, H, p->bf_rho, Ibf);
+        else if (p->bilateral)
             or_bilateral(img, W, H, p, Ibf);
         else
             memcpy(Ibf, img, WH);

@@ -32,7 +32,8 @@ typedef struct or_params {
     float tr_y;              /* Sec. 2.2: squared-residual tolerance of the road fit (4) */
     int32_t eps_num, eps_den;/* inlier-fraction stop test eps = eps_num/eps_den (0.99) */
     float varpi;             /* Sec. 2.3.1: on-road tolerance (3) */
-    int32_t bilateral;       /* 1: bilateral pre-filter (Eq. 15-16); 0: Sobel on the raw image */
+    int32_t bilateral;       /* 1: bilateral pre-filter (Eq. 15-16); 2: median filter over the same window
+                                (the filter of the authors' previous system, Sec. 2.3.1); 0: none */
     int32_t bf_rho;          /* window half-size (5 -> 11x11) */
     double sigma_s, sigma_r; /* Eq. 16 (300, 0.3; intensities scaled to [0,1]) */
     int32_t edge_thresh;     /* Sobel magnitude threshold (100) */
@@ -51,6 +52,10 @@ typedef struct or_params {
     int32_t ransac_hyps;     /* hypotheses drawn per RANSAC round (64) */
     int32_t ransac_rounds;   /* round cap (64) */
     uint64_t seed;           /* Philox key */
+    int32_t wg_gaussian;     /* 0: Eq. 23 as printed, exp(-p / sigma_g^2); 1: the Gaussian the text names,
+                                exp(-p^2 / sigma_g^2); p = dtheta / (pi / 36) */
+    int32_t pad0;
+    int64_t thr_abs;         /* 0: t = ceil(thr * min H); < 0: the absolute threshold t = thr_abs */
 } or_params;
 
 typedef struct or_lanes {
@@ -102,6 +107,7 @@ int32_t or_ransac(const int32_t *x, const int32_t *y, int32_t n, int32_t m, floa
                   const or_params *p, int32_t centre, int32_t e, uint8_t *member, double *coef,
                   int32_t *rounds);
 void or_bilateral(const uint8_t *img, int32_t W, int32_t H, const or_params *p, uint8_t *out);
+void or_median(const uint8_t *img, int32_t W, int32_t H, int32_t rho, uint8_t *out);
 void or_sobel(const uint8_t *I, int32_t W, int32_t H, int16_t *gx, int16_t *gy);
 void or_band(const int32_t *votes, int32_t W, int32_t H, int32_t v_top, int32_t chi, int32_t rho,
              int32_t *m_x);

@@ -299,8 +299,9 @@ def candidate_sets(top: np.ndarray, n_starts: int):
 
 
 def select_on_set(he: np.ndarray, cand: np.ndarray, ev: np.ndarray, S0: int, thr_num: int, thr_den: int,
-                  near_px: int, max_lanes: int):
-    """N7: Alg. 7 selection restricted to the evaluated starts.  Returns (start positions, energies)."""
+                  near_px: int, max_lanes: int, thr_abs: int = 0):
+    """N7: Alg. 7 selection restricted to the evaluated starts (thr_abs < 0: absolute threshold).
+    Returns (start positions, energies)."""
     ns = len(he)
     idx = np.nonzero(ev)[0]
     if ns < 3 or len(idx) == 0:
@@ -308,7 +309,7 @@ def select_on_set(he: np.ndarray, cand: np.ndarray, ev: np.ndarray, S0: int, thr
     mn = int(min(int(he[i]) for i in idx))
     if mn >= 0:
         return [], []
-    t = -(((-mn) * thr_num) // thr_den)
+    t = thr_abs if thr_abs != 0 else -(((-mn) * thr_num) // thr_den)
     minima = [i for i in range(1, ns - 1)
               if cand[i] and he[i] < he[i - 1] and he[i] < he[i + 1] and he[i] < t]
     minima.sort(key=lambda i: (int(he[i]), i))
