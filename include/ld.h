@@ -60,7 +60,9 @@ typedef struct ld_params {
     float tr_y;               /* Sec. 2.2 squared-residual tolerance (4) */
     int32_t eps_num, eps_den; /* Alg. 4 / Alg. 6 stop fraction eps = 99/100 */
     float varpi;              /* Sec. 2.3.1 on-road tolerance |l - f(v)| <= varpi (3) */
-    int32_t bilateral;        /* 1: Eq. 15-16 pre-filter before Sobel; 0: Sobel on the raw image */
+    int32_t bilateral;        /* 1: Eq. 15-16 pre-filter before Sobel; 2: median filter over the same
+                                 window (the pre-filter of the authors' previous system, Sec. 2.3.1: lower
+                                 median of the in-image taps); 0: Sobel on the raw image */
     int32_t bf_rho;           /* bilateral window half-size rho, 1..5 (5 -> 11x11) */
     double sigma_s, sigma_r;  /* Eq. 16 (300, 0.3 with intensities scaled to [0,1]) */
     int32_t edge_thresh;      /* Sobel magnitude threshold (100) */
@@ -79,6 +81,10 @@ typedef struct ld_params {
     int32_t ransac_hyps;      /* hypotheses per RANSAC round (64, at most 256) */
     int32_t ransac_rounds;    /* RANSAC round cap (64) */
     uint64_t seed;            /* Philox4x32-10 key of the RANSAC draws */
+    int32_t wg_gaussian;      /* 0: Eq. 23 as printed, w_g = exp(-p / sigma_g^2); 1: the Gaussian the
+                                 Sec. 2.4 text names, exp(-p^2 / sigma_g^2); p = dtheta / (pi / 36) */
+    int32_t pad0;             /* 0 */
+    int64_t thr_abs;          /* 0: relative lane threshold (thr_num / thr_den); < 0: absolute, H < thr_abs */
 } ld_params;
 
 /* Result of one frame (caller-allocated; device memory for ld_detect, host memory for ld_detect_host). */

@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const 
         if (ns < 3 || mn >= 0) {
             flags |= LD_F_NO_LANES;
         } else {
-            const long long t = -(((-mn) * (long long)kp.thr_num) / (long long)kp.thr_den);
+            const long long t = kp.thr_abs != 0 ? kp.thr_abs : -(((-mn) * (long long)kp.thr_num) / (long long)kp.thr_den);
             int *pos = cand;
             for (int i = 1 + tid; i < ns - 1; i += kSelThreads) {
                 if (cf && !(cf[i] & 1))

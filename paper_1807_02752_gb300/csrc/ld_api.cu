@@ -90,8 +90,9 @@ void build_tables(const ld_params &p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_
         }
     if (wg_q)
         for (int i = 0; i < ld::kWgEntries; ++i) {
-            const double dth = std::asin((double)i / 32768.0);
-            wg_q[i] = (int32_t)std::floor(std::exp(-(dth / (p.sigma_g * p.sigma_g)) * (36.0 / M_PI)) * 4096.0 + 0.5);
+            const double pp = std::asin((double)i / 32768.0) * (36.0 / M_PI);   // p = dtheta / (pi / 36)
+            const double e = p.wg_gaussian ? pp * pp : pp;
+            wg_q[i] = (int32_t)std::floor(std::exp(-e / (p.sigma_g * p.sigma_g)) * 4096.0 + 0.5);
         }
 }
 
@@ -135,6 +136,10 @@ const char *check_params(const ld_params *p)
         return "near_px must be >= 0 and max_lanes in [1, 8]";
     if (p->ransac_hyps < 1 || p->ransac_hyps > ld::kMaxHyps || p->ransac_rounds < 1 || p->ransac_rounds > 1 << 20)
         return "ransac_hyps must be in [1, 256] and ransac_rounds >= 1";
+    if (p->bilateral < 0 || p->bilateral > 2)
+        return "bilateral must be 0 (none), 1 (bilateral) or 2 (median)";
+    if (p->wg_gaussian < 0 || p->wg_gaussian > 1 || p->thr_abs > 0)
+        return "wg_gaussian must be 0 or 1 and thr_abs <= 0";
     return nullptr;
 }
 
@@ -169,6 +174,7 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
     k.thr_den = p.thr_den;
     k.near_px = p.near_px;
     k.max_lanes = p.max_lanes;
+    k.thr_abs = p.thr_abs;
     k.hyps = p.ransac_hyps;
     k.rounds = p.ransac_rounds;
     k.key0 = (uint32_t)p.seed;
@@ -224,7 +230,17 @@ int enqueue_range(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const 
         case 0: e = ld::launch_vdisp(kp, w, disp, s); break;
         case 1: e = ld::launch_road(kp, w, s); break;
         case 2: e = ld::launch_fit_y(kp, w, s); break;
-        case 3: e = ld::launch_grad(kp, w, disp, img, s); break;
+        case 3:
+            if (kp.bilateral == 2) {   // median pre-filter into the workspace, then Sobel on its output
+                ld::KParams kg = kp;
+                kg.bilateral = 0;
+                e = ld::launch_median(kp, w, img, s);
+                if (e == cudaSuccess)
+                    e = ld::launch_grad(kg, w, disp, w.med, s);
+            } else {
+                e = ld::launch_grad(kp, w, disp, img, s);
+            }
+            break;
         case 4: e = ld::launch_vpx(kp, w, s); break;
         case 5: e = ld::launch_fit_x(kp, w, s); break;
         case 6: e = ld::launch_m1(kp, w, s); break;
@@ -272,6 +288,8 @@ ld::Work work_from(const ld::Work &w, const ld::KParams &kp, int f0)
     v.npts += f * 2;
     v.gbt += f * (size_t)w.max_h * ld::vpx_row_bytes(w.max_w);
     v.M1 += f * H * W;
+    if (v.med)
+        v.med += f * H * W;
     if (v.xsum)
         v.xsum += f * (size_t)((H + 3) / 4) * ((W + 3) / 4);
     v.HE += f * (size_t)kp.n_starts;
@@ -489,6 +507,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     const size_t o_pts = take(n * 2 * 3 * pmax * 2), o_np = take(n * 2 * 4);
     const size_t o_tab = take(sizeof(int32_t) * (ld::kWrEntries + ld::kWgEntries));
     const size_t o_d = take(n * H * W * 4), o_i = take(n * H * W), o_l = take(n * sizeof(ld_lanes));
+    const size_t o_med = take(p->bilateral == 2 ? n * H * W : 0);
     e = cudaMalloc(&h->ws, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -510,6 +529,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     w.inl_x = (uint8_t *)(b + o_ix);
     w.gbt = (uint8_t *)(b + o_bt);
     w.M1 = (int32_t *)(b + o_m1);
+    w.med = p->bilateral == 2 ? (uint8_t *)(b + o_med) : nullptr;
     w.HE = (int64_t *)(b + o_he);
     w.pts = (int16_t *)(b + o_pts);
     w.npts = (int32_t *)(b + o_np);

@@ -32,6 +32,7 @@ struct KParams {
     int32_t box_nu, box_vs, lambda_g;
     int32_t S0, n_starts;
     int32_t thr_num, thr_den, near_px, max_lanes;
+    long long thr_abs;                 // 0: relative threshold; < 0: lanes need H < thr_abs
     int32_t hyps, rounds;
     uint32_t key0, key1;
     int32_t centre, e;                 // polynomial basis tau = (v - centre) / 2^e
@@ -71,6 +72,7 @@ struct Work {
     uint8_t *gbt;        // [n][max_h][vpx_row_bytes(max_w)] V_px backtrack rows below the shared-memory block
     int32_t *M1;         // [n][H][W]
     int32_t *xsum;       // [n][ceil(H/4)][ceil(W/4)] block sums of |G_x w_g| for the learned proposal, or null
+    uint8_t *med;        // [n][H][W] median-filtered image (bilateral = 2), or null
     int64_t *HE;         // [n][n_starts]
     const int32_t *wr;   // [kWrEntries] Q15
     const int32_t *wg;   // [kWgEntries] Q12
@@ -142,6 +144,7 @@ cudaError_t launch_road(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_fit_y(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_fit_x(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_grad(const KParams &kp, const Work &w, const float *disp, const uint8_t *img, cudaStream_t s);
+cudaError_t launch_median(const KParams &kp, const Work &w, const uint8_t *img, cudaStream_t s);
 cudaError_t launch_vpx(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_energy(const KParams &kp, const Work &w, cudaStream_t s);

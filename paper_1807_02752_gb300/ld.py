@@ -33,7 +33,8 @@ class Params(C.Structure):
         ("tr_x", C.c_float), ("sigma_g", C.c_double), ("box_nu", C.c_int32), ("box_vs", C.c_int32),
         ("lambda_g", C.c_int32), ("xi_num", C.c_int32), ("xi_den", C.c_int32), ("thr_num", C.c_int32),
         ("thr_den", C.c_int32), ("near_px", C.c_int32), ("max_lanes", C.c_int32), ("ransac_hyps", C.c_int32),
-        ("ransac_rounds", C.c_int32), ("seed", C.c_uint64),
+        ("ransac_rounds", C.c_int32), ("seed", C.c_uint64), ("wg_gaussian", C.c_int32), ("pad0", C.c_int32),
+        ("thr_abs", C.c_int64),
     ]
 
     def as_dict(self):

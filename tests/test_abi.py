@@ -35,7 +35,8 @@ def test_defaults_match_oracle(ldmod, oracle_mod):
 
 
 def test_tables_match_oracle(ldmod, oracle_mod):
-    for kw in ({}, {"sigma_r": 0.2, "sigma_s": 5.0, "bf_rho": 3}, {"sigma_g": 2.0}):
+    for kw in ({}, {"sigma_r": 0.2, "sigma_s": 5.0, "bf_rho": 3}, {"sigma_g": 2.0}, {"wg_gaussian": 1},
+               {"wg_gaussian": 1, "sigma_g": 2.0}):
         ws, wr, wg = ldmod.tables(ldmod.default_params(**kw))
         ows, owr, owg = oracle_mod.tables(oracle_mod.default_params(**kw))
         assert (ws == ows).all() and (wr == owr).all() and (wg == owg).all()
@@ -51,7 +52,8 @@ def test_n_starts(ldmod, oracle_mod):
 def test_invalid_params_rejected_without_device(ldmod):
     L = ldmod.load()
     h = ctypes.c_void_p()
-    for kw in ({"bf_rho": 6}, {"tau_x": 8}, {"n_disp": 300}, {"ransac_hyps": 0}, {"max_lanes": 9}):
+    for kw in ({"bf_rho": 6}, {"tau_x": 8}, {"n_disp": 300}, {"ransac_hyps": 0}, {"max_lanes": 9}, {"bilateral": 3},
+               {"wg_gaussian": 2}, {"thr_abs": 5}):
         p = ldmod.default_params(**kw)
         assert L.ld_create(ctypes.byref(p), 1242, 375, 4, None, ctypes.byref(h)) == ldmod.E_ARG
         assert h.value is None

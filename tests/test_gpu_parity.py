@@ -109,11 +109,24 @@ def test_param_variants(torch_cuda):
     for kw in ({"bilateral": 0}, {"bf_rho": 3, "sigma_r": 0.2}, {"ransac_hyps": 1}, {"ransac_hyps": 256, "seed": 7},
                {"chi": 5, "tau_x": 7, "lambda_x": 3}, {"thr_den": 4, "near_px": 5, "max_lanes": 2},
                {"ransac_rounds": 1}, {"box_nu": 0, "box_vs": 0}, {"box_nu": 3, "box_vs": 8},
-               {"box_nu": 8, "box_vs": 1}):
+               {"box_nu": 8, "box_vs": 1}, {"bilateral": 2}, {"bilateral": 2, "bf_rho": 2}, {"wg_gaussian": 1},
+               {"thr_abs": -(1 << 22)}, {"thr_abs": -(1 << 22), "wg_gaussian": 1, "bilateral": 2}):
         p = ld.default_params(n_disp=cfg.n_disp, **kw)
         det = ld.Detector(cfg.width, cfg.height, 3, p)
         res = _run(torch_cuda, det, disp, img)
         for f in range(3):
+            compare_frame(det, res[f], f, disp[f], img[f], p)
+
+
+def test_paper_literal_variants_full_size(torch_cuda):
+    """The median pre-filter (ragged 8 x 32 tiles at 1242x375) and the Gaussian w_g at the full size."""
+    cfg = scenes.SINGLE_1242x375
+    disp, img, _ = scenes.make_batch(cfg, 2, first_frame=61)
+    for kw in ({"bilateral": 2}, {"wg_gaussian": 1}):
+        p = ld.default_params(n_disp=cfg.n_disp, **kw)
+        det = ld.Detector(cfg.width, cfg.height, 2, p)
+        res = _run(torch_cuda, det, disp, img)
+        for f in range(2):
             compare_frame(det, res[f], f, disp[f], img[f], p)
 
 
