@@ -89,6 +89,13 @@ def lib():
         L.or_ransac.restype = i32
         L.or_bilateral.argtypes = [p, i32, i32, C.POINTER(Params), p]
         L.or_median.argtypes = [p, i32, i32, i32, p]
+        L.or_integral.argtypes = [p, i32, i32, i32, p]
+        L.or_block_stats.argtypes = [p, i32, i32, i32, p, p]
+        L.or_ncc_cmp.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64]
+        L.or_ncc_cmp.restype = i32
+        L.or_srp.argtypes = [p, p, i32, i32, i32, i32, i32, i32, p]
+        L.or_lrc.argtypes = [p, p, i32, i32, i32, p]
+        L.or_stereo.argtypes = [p, p, i32, i32, i32, i32, i32, i32, p, p, p]
         L.or_sobel.argtypes = [p, i32, i32, p, p]
         L.or_band.argtypes = [p, i32, i32, i32, i32, i32, p]
         L.or_dp_vpx.argtypes = [p, i32, i32, i32, i32, i32, p]
@@ -211,6 +218,52 @@ def median(img: np.ndarray, rho: int = 5) -> np.ndarray:
     out = np.zeros_like(im)
     lib().or_median(_ptr(im), W, H, rho, _ptr(out))
     return out
+
+
+def integral(img: np.ndarray, square: bool = False) -> np.ndarray:
+    im = np.ascontiguousarray(img, np.uint8)
+    H, W = im.shape
+    out = np.zeros((H + 1, W + 1), np.int64)
+    lib().or_integral(_ptr(im), W, H, 1 if square else 0, _ptr(out))
+    return out
+
+
+def block_stats(img: np.ndarray, rho: int = 3):
+    im = np.ascontiguousarray(img, np.uint8)
+    H, W = im.shape
+    s = np.zeros((H, W), np.int32)
+    D = np.zeros((H, W), np.int64)
+    lib().or_block_stats(_ptr(im), W, H, rho, _ptr(s), _ptr(D))
+    return s, D
+
+
+def ncc_cmp(N1: int, D1: int, N2: int, D2: int) -> int:
+    return int(lib().or_ncc_cmp(N1, D1, N2, D2))
+
+
+def srp(a: np.ndarray, b: np.ndarray, rho: int = 3, dmax: int = 127, tau: int = 1, direction: int = 0):
+    aa, bb = np.ascontiguousarray(a, np.uint8), np.ascontiguousarray(b, np.uint8)
+    H, W = aa.shape
+    out = np.zeros((H, W), np.int16)
+    lib().or_srp(_ptr(aa), _ptr(bb), W, H, rho, dmax, tau, direction, _ptr(out))
+    return out
+
+
+def lrc(lf: np.ndarray, rt: np.ndarray, tr: int = 3):
+    a, b = np.ascontiguousarray(lf, np.int16), np.ascontiguousarray(rt, np.int16)
+    H, W = a.shape
+    out = np.zeros((H, W), np.int16)
+    lib().or_lrc(_ptr(a), _ptr(b), W, H, tr, _ptr(out))
+    return out
+
+
+def stereo(left: np.ndarray, right: np.ndarray, rho: int = 3, dmax: int = 127, tau: int = 1, tr: int = 3):
+    """(left map, right map, checked disparity) of a rectified pair, int16 [H][W]."""
+    L_, R_ = np.ascontiguousarray(left, np.uint8), np.ascontiguousarray(right, np.uint8)
+    H, W = L_.shape
+    lf, rt, d = (np.zeros((H, W), np.int16) for _ in range(3))
+    lib().or_stereo(_ptr(L_), _ptr(R_), W, H, rho, dmax, tau, tr, _ptr(lf), _ptr(rt), _ptr(d))
+    return lf, rt, d
 
 
 def sobel(I: np.ndarray):

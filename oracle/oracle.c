@@ -934,3 +934,165 @@ done_early:
     free(Vpx);
     return 0;
 }
+
+/* ================================================================================================ */
+/* Sec. 2.1 stereo matching: block statistics through integral images (Alg. 1, Eq. 4-5), the NCC cost */
+/* (Eq. 1-8), search range propagation (Eq. 9, Alg. 2) and the left-right consistency check (Alg. 3). */
+/*                                                                                                  */
+/* Readings.  Blocks are (2 rho + 1)^2 and must lie inside both images: rows rho .. H-1-rho, columns  */
+/* rho .. W-1-rho, and a candidate d only while the other image's block stays inside; pixels with no */
+/* candidate get 0.  With s the block sum, Q the sum of squares, P the sum of products and n the     */
+/* block size, Eq. 8 is c = (n P - s_l s_r) / sqrt(D_l D_r), D = n Q - s^2 (multiply Eq. 8's numerator */
+/* and denominator by n); c = 0 where D_l D_r = 0 (then the numerator is 0 as well).  The best d has  */
+/* the largest c, compared exactly in integers (below), ties to the smaller d.  Rows are estimated   */
+/* from H-1-rho up to rho; the first over the full range [0, d_max], each later pixel over the union  */
+/* of [l - tau, l + tau] for the three estimates below it that exist.  The right map matches the     */
+/* right image's block at (u, v) with the left image's at (u + d, v).  LRC keeps l_lf(u, v) when      */
+/* |l_lf(u, v) - l_rt(u - l_lf(u, v), v)| <= tr, else 0.                                             */
+/* ================================================================================================ */
+
+/* Alg. 1: In(u, v) = sum of I over [0, u] x [0, v], by the serial recurrence; stored with a zero     */
+/* first row and column so that In(-1, .) = In(., -1) = 0: entry (v + 1) * (W + 1) + (u + 1).          */
+void or_integral(const uint8_t *img, int32_t W, int32_t H, int32_t square, int64_t *In)
+{
+    const int32_t Wp = W + 1;
+    for (int32_t u = 0; u <= W; u++)
+        In[u] = 0;
+    for (int32_t v = 0; v < H; v++) {
+        In[(size_t)(v + 1) * Wp] = 0;
+        for (int32_t u = 0; u < W; u++) {
+            int64_t x = img[(size_t)v * W + u];
+            if (square)
+                x *= x;
+            In[(size_t)(v + 1) * Wp + u + 1] = x + In[(size_t)(v + 1) * Wp + u] + In[(size_t)v * Wp + u + 1] -
+                                               In[(size_t)v * Wp + u];
+        }
+    }
+}
+
+/* Eq. 5: block sums from four references of the integral images; s and D = n Q - s^2 at every pixel */
+/* whose block lies inside the image (0 elsewhere).                                                 */
+void or_block_stats(const uint8_t *img, int32_t W, int32_t H, int32_t rho, int32_t *s, int64_t *D)
+{
+    const int32_t Wp = W + 1;
+    const int64_t n = (int64_t)(2 * rho + 1) * (2 * rho + 1);
+    int64_t *In = (int64_t *)malloc(sizeof(int64_t) * (size_t)(W + 1) * (H + 1));
+    int64_t *In2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(W + 1) * (H + 1));
+    or_integral(img, W, H, 0, In);
+    or_integral(img, W, H, 1, In2);
+    for (int32_t v = 0; v < H; v++)
+        for (int32_t u = 0; u < W; u++) {
+            size_t o = (size_t)v * W + u;
+            if (v < rho || v > H - 1 - rho || u < rho || u > W - 1 - rho) {
+                s[o] = 0;
+                D[o] = 0;
+                continue;
+            }
+            /* r1 = In(u + rho, v + rho), r2 = In(u - rho - 1, v - rho - 1), r3 = In(u - rho - 1, v + rho),
+               r4 = In(u + rho, v - rho - 1); s = r1 + r2 - r3 - r4 (padded indices are +1) */
+            size_t a = (size_t)(v + rho + 1) * Wp + (u + rho + 1), b = (size_t)(v - rho) * Wp + (u - rho);
+            size_t c = (size_t)(v + rho + 1) * Wp + (u - rho), d = (size_t)(v - rho) * Wp + (u + rho + 1);
+            int64_t s1 = In[a] + In[b] - In[c] - In[d];
+            int64_t q1 = In2[a] + In2[b] - In2[c] - In2[d];
+            s[o] = (int32_t)s1;
+            D[o] = n * q1 - s1 * s1;
+        }
+    free(In);
+    free(In2);
+}
+
+/* Sign of c1 - c2 for c = N / sqrt(D_a D_b) with a common D_a > 0: c1 > c2 compared as                */
+/* N1 |N1| D2 > N2 |N2| D1 in 128-bit integers (the square root never taken); D = 0 means c = 0.     */
+int32_t or_ncc_cmp(int64_t N1, int64_t D1, int64_t N2, int64_t D2)
+{
+    if (D1 == 0)
+        N1 = 0;
+    if (D2 == 0)
+        N2 = 0;
+    __int128 l = (__int128)N1 * (N1 < 0 ? -N1 : N1) * (D2 == 0 ? 1 : D2);
+    __int128 r = (__int128)N2 * (N2 < 0 ? -N2 : N2) * (D1 == 0 ? 1 : D1);
+    if (N1 == 0 && N2 == 0)
+        return 0;
+    if (N1 == 0)
+        return N2 > 0 ? -1 : 1;
+    if (N2 == 0)
+        return N1 > 0 ? 1 : -1;
+    return l > r ? 1 : (l < r ? -1 : 0);
+}
+
+/* Eq. 9, Alg. 2: one disparity map by search range propagation.  dir 0: the left map (blocks of a   */
+/* at u against b at u - d); dir 1: the right map (a at u against b at u + d).                        */
+void or_srp(const uint8_t *a, const uint8_t *b, int32_t W, int32_t H, int32_t rho, int32_t dmax, int32_t tau,
+            int32_t dir, int16_t *out)
+{
+    const int64_t n = (int64_t)(2 * rho + 1) * (2 * rho + 1);
+    int32_t *sa = (int32_t *)malloc(sizeof(int32_t) * (size_t)W * H), *sb = (int32_t *)malloc(sizeof(int32_t) * (size_t)W * H);
+    int64_t *Da = (int64_t *)malloc(sizeof(int64_t) * (size_t)W * H), *Db = (int64_t *)malloc(sizeof(int64_t) * (size_t)W * H);
+    or_block_stats(a, W, H, rho, sa, Da);
+    or_block_stats(b, W, H, rho, sb, Db);
+    memset(out, 0, sizeof(int16_t) * (size_t)W * H);
+    for (int32_t v = H - 1 - rho; v >= rho; v--) {
+        for (int32_t u = rho; u <= W - 1 - rho; u++) {
+            /* candidate disparities: d in [0, dmax] with the other block inside */
+            int32_t dhi = dir == 0 ? u - rho : W - 1 - rho - u;
+            if (dhi > dmax)
+                dhi = dmax;
+            int32_t best = -1;
+            int64_t bN = 0, bD = 0;
+            for (int32_t d = 0; d <= dhi; d++) {
+                if (v < H - 1 - rho) {
+                    int32_t in = 0;
+                    for (int32_t k = u - 1; k <= u + 1; k++) {
+                        if (k < rho || k > W - 1 - rho)
+                            continue;
+                        int32_t l = out[(size_t)(v + 1) * W + k];
+                        if (d >= l - tau && d <= l + tau)
+                            in = 1;
+                    }
+                    if (!in)
+                        continue;
+                }
+                int32_t ub = dir == 0 ? u - d : u + d;
+                int64_t P = 0;
+                for (int32_t y = v - rho; y <= v + rho; y++)
+                    for (int32_t x = -rho; x <= rho; x++)
+                        P += (int64_t)a[(size_t)y * W + u + x] * b[(size_t)y * W + ub + x];
+                size_t oa = (size_t)v * W + u, ob = (size_t)v * W + ub;
+                int64_t N = n * P - (int64_t)sa[oa] * sb[ob];
+                if (Da[oa] == 0)
+                    N = 0;
+                if (best < 0 || or_ncc_cmp(N, Db[ob], bN, bD) > 0) {
+                    best = d;
+                    bN = N;
+                    bD = Db[ob];
+                }
+            }
+            out[(size_t)v * W + u] = (int16_t)(best < 0 ? 0 : best);
+        }
+    }
+    free(sa);
+    free(sb);
+    free(Da);
+    free(Db);
+}
+
+/* Alg. 3: left-right consistency. */
+void or_lrc(const int16_t *lf, const int16_t *rt, int32_t W, int32_t H, int32_t tr, int16_t *out)
+{
+    for (int32_t v = 0; v < H; v++)
+        for (int32_t u = 0; u < W; u++) {
+            int32_t l = lf[(size_t)v * W + u];
+            int32_t x = u - l;
+            int32_t ok = x >= 0 && abs(l - rt[(size_t)v * W + x]) <= tr;
+            out[(size_t)v * W + u] = (int16_t)(ok ? l : 0);
+        }
+}
+
+/* The disparity map of a rectified pair: both SRP maps, then LRC. */
+void or_stereo(const uint8_t *left, const uint8_t *right, int32_t W, int32_t H, int32_t rho, int32_t dmax,
+               int32_t tau, int32_t tr, int16_t *lf, int16_t *rt, int16_t *disp)
+{
+    or_srp(left, right, W, H, rho, dmax, tau, 0, lf);
+    or_srp(right, left, W, H, rho, dmax, tau, 1, rt);
+    or_lrc(lf, rt, W, H, tr, disp);
+}

@@ -118,6 +118,17 @@ void or_energy(const int32_t *m1, int32_t W, int32_t H, int32_t v_top, const flo
                int32_t S0, int32_t n_starts, int32_t lambda_g, int64_t *he);
 void or_select(const int64_t *he, int32_t n_starts, int32_t S0, const or_params *p, or_lanes *out);
 
+/* Sec. 2.1 stereo matching (the disparity the path takes as input).  Integral images are (W+1) x (H+1)
+   with a zero first row and column; block statistics s (sum) and D = n Q - s^2 per pixel; maps int16. */
+void or_integral(const uint8_t *img, int32_t W, int32_t H, int32_t square, int64_t *In);
+void or_block_stats(const uint8_t *img, int32_t W, int32_t H, int32_t rho, int32_t *s, int64_t *D);
+int32_t or_ncc_cmp(int64_t N1, int64_t D1, int64_t N2, int64_t D2);
+void or_srp(const uint8_t *a, const uint8_t *b, int32_t W, int32_t H, int32_t rho, int32_t dmax, int32_t tau,
+            int32_t dir, int16_t *out);
+void or_lrc(const int16_t *lf, const int16_t *rt, int32_t W, int32_t H, int32_t tr, int16_t *out);
+void or_stereo(const uint8_t *left, const uint8_t *right, int32_t W, int32_t H, int32_t rho, int32_t dmax,
+               int32_t tau, int32_t tr, int16_t *lf, int16_t *rt, int16_t *disp);
+
 /* The whole path on one frame.  Returns 0, or -1 on bad arguments / allocation failure. */
 int32_t or_detect(const float *disp, const uint8_t *img, int32_t W, int32_t H, const or_params *p,
                   or_lanes *out, or_dumps *dumps);

@@ -132,8 +132,9 @@ def _lanes(cfg: SceneConfig, r: np.random.Generator, f: np.ndarray, fp: np.ndarr
     raise RuntimeError("lane sampling failed")
 
 
-def make_frame(cfg: SceneConfig, frame: int, seed: int = BASE_SEED):
-    """Render one frame.  Returns (disparity f32 [H,W], image u8 [H,W], Truth)."""
+def make_frame(cfg: SceneConfig, frame: int, seed: int = BASE_SEED, with_clean: bool = False):
+    """Render one frame.  Returns (disparity f32 [H,W], image u8 [H,W], Truth), and with with_clean also the
+    disparity before the outlier and invalid pixels (the scene's own disparity)."""
     W, H, D = cfg.width, cfg.height, cfg.n_disp
     vmax = H - 1
     r_geo = _rng(seed, frame, 1)
@@ -225,6 +226,7 @@ def make_frame(cfg: SceneConfig, frame: int, seed: int = BASE_SEED):
         img[v0:vb + 1, u0:u0 + wid] = r_pix.uniform(30, 220, size=(vb + 1 - v0, wid))
         occl[v0:vb + 1, u0:u0 + wid] = True
 
+    clean = disp.copy() if with_clean else None
     # ---- outliers and invalid pixels -------------------------------------------------------------
     if cfg.outlier_frac > 0:
         m = r_pix.random((H, W)) < cfg.outlier_frac
@@ -240,7 +242,43 @@ def make_frame(cfg: SceneConfig, frame: int, seed: int = BASE_SEED):
     vis_rows = np.array([(m & ~occl).any(axis=1).sum() for m in lane_rows_vis])
     truth = Truth(beta=beta, v_horizon=vh, vpy=vpy, vpx=vpx, lane_starts=starts, lane_widths=widths,
                   lane_visible_rows=vis_rows, alpha=alpha)
+    if with_clean:
+        return disp, img, truth, clean
     return disp, img, truth
+
+
+def make_stereo_frame(cfg: SceneConfig, frame: int, seed: int = BASE_SEED):
+    """A rectified stereo pair of one frame: (left u8 [H,W], right u8 [H,W], clean disparity f32 [H,W], Truth).
+
+    The left image is make_frame's image.  The right image sees the scene shifted by its disparity: the left
+    pixel (u, v) lands on column round(u - d(u, v)), the nearest surface (largest d) winning where several
+    land; columns nothing lands on (occlusions) take the nearest landed value to their right (the farther
+    surface); then independent Gaussian noise of sigma 2 and rounding."""
+    _, left, truth, clean = make_frame(cfg, frame, seed, with_clean=True)
+    H, W = left.shape
+    r = _rng(seed, frame, 3)
+    right = np.zeros((H, W), dtype=np.float64)
+    cols = np.arange(W)
+    for v in range(H):
+        order = np.argsort(clean[v], kind="stable")            # far first: the nearest surface lands last
+        x = np.rint(cols[order] - clean[v][order].astype(np.float64)).astype(np.int64)
+        ok = (x >= 0) & (x < W)
+        row = np.full(W, -1.0)
+        row[x[ok]] = left[v][order[ok]]
+        filled = row >= 0
+        if not filled.any():
+            row[:] = left[v]
+        else:
+            # nearest landed value to the right (then to the left at the right edge)
+            idx = np.where(filled, cols, W)
+            nxt = np.minimum.accumulate(idx[::-1])[::-1]
+            prv = np.maximum.accumulate(np.where(filled, cols, -1))
+            take = np.where(nxt < W, nxt, prv)
+            row = row[take]
+        right[v] = row
+    right += r.normal(0.0, 2.0, size=(H, W))
+    right = np.clip(np.rint(right), 0, 255).astype(np.uint8)
+    return left, right, clean, truth
 
 
 def make_batch(cfg: SceneConfig, n_frames: int, seed: int = BASE_SEED, first_frame: int = 0):
