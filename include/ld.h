@@ -358,6 +358,50 @@ int ld_net_debug_get(ld_net *net, int32_t frame, int32_t stage, void *host_dst, 
 const char *ld_net_last_error(const ld_net *net);
 void ld_net_destroy(ld_net *net);
 
+/*
+ * Stereo matching (Sec. 2.1): the disparity map of a rectified grey pair, the input the lane path takes.
+ * For each pixel the NCC of its (2 rho + 1)^2 block with the other image's blocks on the same row
+ * (Eq. 1-8, from block sums and sums of squares, the quantities the paper gets from integral images,
+ * Alg. 1 and Eq. 5), searched by search range propagation (Eq. 9, Alg. 2): rows from the bottom up, the
+ * first over [0, d_max], every later pixel over [l - tau, l + tau] around the three estimates below it.
+ * Both the left map (left block at u against right at u - d) and the right map (right at u against left
+ * at u + d) are estimated, then the left-right consistency check (Alg. 3) keeps l_lf(u, v) where
+ * |l_lf(u, v) - l_rt(u - l_lf(u, v), v)| <= tr_lrc and writes 0 elsewhere.
+ *
+ * Readings: blocks lie inside both images (border pixels and candidates whose other block would leave
+ * the image are skipped; a pixel without a candidate gets 0); the best candidate has the largest NCC,
+ * compared exactly in integers (ties to the smaller disparity); a block of constant intensity has NCC 0.
+ * A stereo object belongs to a handle (its stream, largest frame and batch) and owns its two int16 maps
+ * and a float disparity buffer.  Images are DEVICE uint8 [n][h][w]; outputs DEVICE float [n][h][w] with
+ * integer values (0 = no disparity).  Errors: LD_E_ARG, LD_E_NOMEM, LD_E_STATE, LD_E_CUDA.
+ */
+typedef struct ld_stereo ld_stereo;
+typedef struct ld_stereo_params {
+    int32_t rho;     /* block half-size, 1..3 (3: 7 x 7 blocks, the paper's setting) */
+    int32_t tau;     /* search range bound of Eq. 9 (1) */
+    int32_t d_max;   /* largest disparity searched; -1: n_disp - 1 of the handle */
+    int32_t tr_lrc;  /* LRC threshold of Alg. 3 (3) */
+} ld_stereo_params;
+
+void ld_stereo_params_default(ld_stereo_params *sp);
+int ld_stereo_create(ld_handle *h, const ld_stereo_params *sp, ld_stereo **out);
+/* Disparity of n frames into disp_out (enqueued on the handle's stream). */
+int ld_stereo_run(ld_stereo *st, const uint8_t *left, const uint8_t *right, int32_t w, int32_t h_px, int32_t n_frames,
+                  float *disp_out);
+/* ld_stereo_run with CUDA events: ms_out[0] = both search-range-propagation maps, ms_out[1] = the check
+ * (waits for the stream). */
+int ld_stereo_run_timed(ld_stereo *st, const uint8_t *left, const uint8_t *right, int32_t w, int32_t h_px,
+                        int32_t n_frames, float *disp_out, float *ms_out);
+/* The whole path from stereo pairs: the disparity into the object's buffer, then ld_detect on it with the
+ * left image. */
+int ld_detect_stereo(ld_stereo *st, const uint8_t *left, const uint8_t *right, int32_t w, int32_t h_px,
+                     int32_t n_frames, ld_lanes *out_lanes);
+/* Host copies of frame `frame` of the last call: left map, right map (int16 [h][w]) and the checked
+ * disparity (float [h][w], the object's buffer: valid after ld_detect_stereo); any pointer may be NULL. */
+int ld_stereo_maps(ld_stereo *st, int32_t frame, int16_t *lf_host, int16_t *rt_host, float *disp_host);
+const char *ld_stereo_last_error(const ld_stereo *st);
+void ld_stereo_destroy(ld_stereo *st);
+
 /* Message of the last error on h (or of the last failed ld_create when h is NULL). */
 const char *ld_last_error(const ld_handle *h);
 

@@ -52,6 +52,12 @@ MAX_SIZE_CLASSES = 8
 E_BUSY = -5
 
 
+class StereoParams(C.Structure):
+    """ld_stereo_params."""
+
+    _fields_ = [("rho", C.c_int32), ("tau", C.c_int32), ("d_max", C.c_int32), ("tr_lrc", C.c_int32)]
+
+
 class ServerConfig(C.Structure):
     _fields_ = [("n_sizes", C.c_int32), ("sizes", (C.c_int32 * 2) * MAX_SIZE_CLASSES), ("slots_per_size", C.c_int32),
                 ("max_batch", C.c_int32), ("max_wait_us", C.c_int32), ("n_streams", C.c_int32)]
@@ -142,6 +148,19 @@ def load():
     L.ld_net_last_error.restype = C.c_char_p
     L.ld_net_destroy.argtypes = [p]
     L.ld_net_destroy.restype = None
+    L.ld_stereo_params_default.argtypes = [C.POINTER(StereoParams)]
+    L.ld_stereo_params_default.restype = None
+    L.ld_stereo_create.argtypes = [p, C.POINTER(StereoParams), C.POINTER(p)]
+    L.ld_stereo_run.argtypes = [p, p, p, i32, i32, i32, p]
+    L.ld_stereo_run_timed.argtypes = [p, p, p, i32, i32, i32, p, p]
+    L.ld_detect_stereo.argtypes = [p, p, p, i32, i32, i32, p]
+    L.ld_stereo_maps.argtypes = [p, i32, p, p, p]
+    L.ld_stereo_last_error.argtypes = [p]
+    L.ld_stereo_last_error.restype = C.c_char_p
+    L.ld_stereo_destroy.argtypes = [p]
+    L.ld_stereo_destroy.restype = None
+    for name in ("ld_stereo_create", "ld_stereo_run", "ld_stereo_run_timed", "ld_detect_stereo", "ld_stereo_maps"):
+        getattr(L, name).restype = C.c_int
     for name in ("ld_net_create", "ld_net_set_params", "ld_net_get_params", "ld_net_forward", "ld_net_grad",
                  "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs", "ld_detect_learned",
                  "ld_net_debug_get"):
@@ -156,7 +175,9 @@ EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_de
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
             "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
-            "ld_detect_learned", "ld_net_debug_size", "ld_net_debug_get", "ld_net_last_error", "ld_net_destroy"]
+            "ld_detect_learned", "ld_net_debug_size", "ld_net_debug_get", "ld_net_last_error", "ld_net_destroy",
+            "ld_stereo_params_default", "ld_stereo_create", "ld_stereo_run", "ld_stereo_run_timed", "ld_detect_stereo",
+            "ld_stereo_maps", "ld_stereo_last_error", "ld_stereo_destroy"]
 
 
 def launch_names():
@@ -480,6 +501,71 @@ class Net:
     def close(self):
         if getattr(self, "h", None):
             self.L.ld_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stereo_params(**kw) -> StereoParams:
+    sp = StereoParams()
+    load().ld_stereo_params_default(C.byref(sp))
+    for k, v in kw.items():
+        setattr(sp, k, v)
+    return sp
+
+
+class Stereo:
+    """Stereo matching of a Detector's frames (ld_stereo_*): device uint8 pairs in, device float disparity out."""
+
+    def __init__(self, det: "Detector", sp: StereoParams | None = None):
+        self.L = load()
+        self.det = det
+        self.sp = sp if sp is not None else stereo_params()
+        h = C.c_void_p()
+        rc = self.L.ld_stereo_create(det.h, C.byref(self.sp), C.byref(h))
+        if rc != OK:
+            raise LDError(rc, self.L.ld_stereo_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LDError(rc, self.L.ld_stereo_last_error(self.h).decode())
+
+    def run(self, left, right, out=None):
+        import torch
+
+        n, H, W = left.shape
+        out = torch.empty((n, H, W), dtype=torch.float32, device="cuda") if out is None else out
+        self._check(self.L.ld_stereo_run(self.h, left.data_ptr(), right.data_ptr(), W, H, n, out.data_ptr()))
+        return out
+
+    def run_timed(self, left, right, out):
+        n, H, W = left.shape
+        ms = np.zeros(2, np.float32)
+        self._check(self.L.ld_stereo_run_timed(self.h, left.data_ptr(), right.data_ptr(), W, H, n, out.data_ptr(),
+                                               ms.ctypes.data))
+        return ms
+
+    def detect(self, left, right, out=None):
+        n, H, W = left.shape
+        out = self.det.alloc_lanes(n) if out is None else out
+        self._check(self.L.ld_detect_stereo(self.h, left.data_ptr(), right.data_ptr(), W, H, n, out.data_ptr()))
+        return out
+
+    def maps(self, frame: int, W: int, H: int):
+        lf = np.zeros((H, W), np.int16)
+        rt = np.zeros((H, W), np.int16)
+        d = np.zeros((H, W), np.float32)
+        self._check(self.L.ld_stereo_maps(self.h, frame, lf.ctypes.data, rt.ctypes.data, d.ctypes.data))
+        return lf, rt, d
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.ld_stereo_destroy(self.h)
             self.h = None
 
     def __del__(self):
