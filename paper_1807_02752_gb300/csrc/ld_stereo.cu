@@ -5,12 +5,15 @@
 //
 //   k_srp   one CTA per (frame, map): rows from H-1-rho up to rho, in order, since a row's search range
 //           comes from the row below.  A ring of the 2 rho + 1 image rows of both images sits in shared
-//           memory; when the window moves up one row the new top row replaces the old bottom row and
-//           per-column sums of I and I^2 are updated by their difference, so the block statistics of
-//           every pixel of the row are two 7-wide sums of column sums (exact integers, the quantities the
-//           paper gets from integral images, Eq. 5).  A pixel keeps its own block in registers and takes
-//           the candidate with the largest NCC, compared exactly: c = N / sqrt(D_a D_b) with
-//           N = n P - s_a s_b and D = n Q - s^2, so c1 > c2 <=> N1 |N1| D2 > N2 |N2| D1 in 128-bit integers.
+//           memory, stored by column (a column's rows in 8 bytes); when the window moves up one row the new
+//           top row (loaded a row ahead) replaces the old bottom row and per-column sums of I and I^2 are
+//           updated by their difference, so the block statistics of every pixel of the row are two 7-wide
+//           sums of column sums (exact integers, the quantities the paper gets from integral images, Eq. 5).
+//           A thread takes a pixel, keeps its block's columns in registers and forms each candidate's
+//           block product P from 7 column dot products (two dp4a each, in four independent chains).  The best candidate has the
+//           largest NCC, compared exactly: c = N / sqrt(D_a D_b) with N = n P - s_a s_b and
+//           D = n Q - s^2, so c1 > c2 <=> N1 |N1| D2 > N2 |N2| D1 (a float filter decides clear cases,
+//           128-bit integers the rest).
 //   k_lrc   l(u, v) = l_lf(u, v) when |l_lf(u, v) - l_rt(u - l_lf(u, v), v)| <= tr, else 0; float output.
 //
 // Readings: blocks lie inside both images (other pixels and candidates are skipped; a pixel without a
@@ -30,10 +33,13 @@ constexpr int kSrpThreads = 512;
 struct SrpArgs {
     const uint8_t *left, *right;     // [n][H][W]
     int16_t *lf, *rt;                // [n][H][W]
-    int W, H, dmax, tau, Wp;         // Wp: ring row stride (W rounded up to 16)
+    int W, H, dmax, tau;
 };
 
-// c1 > c2 for c = N / sqrt(D) (a common positive factor dropped); D = 0 means c = 0
+// c1 > c2 for c = N / sqrt(D) (a common positive factor dropped); D = 0 means c = 0.  Decided exactly:
+// c1 > c2 <=> N1 |N1| D2 > N2 |N2| D1.  Each side in float carries four roundings (the two conversions and
+// two products; relative error about 2^-22), so a float gap above 2^-20 (|L| + |R|) has the sign of the
+// exact one; closer pairs compare in 128-bit integers.
 __device__ __forceinline__ bool ncc_better(long long N1, int D1, long long N2, int D2)
 {
     if (D1 == 0)
@@ -42,9 +48,28 @@ __device__ __forceinline__ bool ncc_better(long long N1, int D1, long long N2, i
         N2 = 0;
     if (N1 == 0 || N2 == 0)
         return N2 == 0 ? N1 > 0 : N2 < 0 && N1 == 0;
+    const float f1 = (float)N1, f2 = (float)N2;
+    const float L = __fmul_rn(__fmul_rn(f1, fabsf(f1)), (float)D2);
+    const float R = __fmul_rn(__fmul_rn(f2, fabsf(f2)), (float)D1);
+    const float gap = __fsub_rn(L, R);
+    if (fabsf(gap) > 9.5367431640625e-07f * (fabsf(L) + fabsf(R)))
+        return gap > 0.0f;
     const __int128 l = (__int128)N1 * (N1 < 0 ? -N1 : N1) * D2;
     const __int128 r = (__int128)N2 * (N2 < 0 ? -N2 : N2) * D1;
     return l > r;
+}
+
+constexpr int kMaxColsPerThread = 8;  // columns per thread in the row loads (the launch guarantees W <= 8 x threads)
+
+// threads of a k_srp CTA: the pixels with a block spread evenly (every thread the same number of them),
+// at most kSrpThreads, and enough threads that each loads at most kMaxColsPerThread columns of a row
+inline int srp_threads(int W, int rho)
+{
+    const int valid = W - 2 * rho, per = (valid + kSrpThreads - 1) / kSrpThreads;
+    int t = (valid + per - 1) / per;
+    t = t > (W + kMaxColsPerThread - 1) / kMaxColsPerThread ? t : (W + kMaxColsPerThread - 1) / kMaxColsPerThread;
+    t = t < 32 ? 32 : t;
+    return t < kSrpThreads ? t : kSrpThreads;
 }
 
 template <int RHO>
@@ -52,64 +77,91 @@ __global__ void __launch_bounds__(kSrpThreads, 1) k_srp(const SrpArgs a)
 {
     constexpr int K = 2 * RHO + 1, NB = K * K;
     extern __shared__ __align__(16) unsigned char sm[];
-    const int W = a.W, H = a.H, Wp = a.Wp, f = blockIdx.x, dir = blockIdx.y;
+    const int W = a.W, H = a.H, f = blockIdx.x, dir = blockIdx.y;
     const size_t fo = (size_t)f * H * W;
     const uint8_t *A = (dir == 0 ? a.left : a.right) + fo;   // the image whose map this is
     const uint8_t *B = (dir == 0 ? a.right : a.left) + fo;
     int16_t *out = (dir == 0 ? a.lf : a.rt) + fo;
-    uint8_t *ra = sm;                                          // [K][Wp] rows of A, row y in slot y % K
-    uint8_t *rb = ra + K * Wp;                                 // [K][Wp] rows of B
-    int *cs = reinterpret_cast<int *>(rb + K * Wp);            // [4][W]: column sums of A, A^2, B, B^2
-    int *rs = cs + 4 * W;                                      // [4][W]: block s_A, D_A, s_B, D_B of the row
-    int16_t *lv = reinterpret_cast<int16_t *>(rs + 4 * W);     // [2][W]: estimates of the row below / this row
-    const int tid = threadIdx.x;
+    // ring of the K block rows, stored by column: byte r of column c is ring slot r (row y with y % K == r),
+    // byte 7 stays 0, so the dot product of two columns is two dp4a
+    uint2 *ca = reinterpret_cast<uint2 *>(sm);                 // [W]
+    uint2 *cb = ca + W;                                        // [W]
+    int *cs = reinterpret_cast<int *>(cb + W);                 // [4][W]: column sums of A, A^2, B, B^2
+    int2 *ra2 = reinterpret_cast<int2 *>(cs + 4 * W);           // [W]: block (s_A, D_A) of the row
+    int2 *rb2 = ra2 + W;                                       // [W]: block (s_B, D_B)
+    int16_t *lv = reinterpret_cast<int16_t *>(rb2 + W);        // [2][W]: estimates of the row below / this row
+    uint8_t *ca8 = reinterpret_cast<uint8_t *>(ca), *cb8 = reinterpret_cast<uint8_t *>(cb);
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const int vb = H - 1 - RHO;
-    // rows without a block are 0
-    for (int i = tid; i < RHO * W; i += kSrpThreads) {
+    for (int i = tid; i < RHO * W; i += nthr) {
         out[i] = 0;
         out[(size_t)(H - RHO) * W + i] = 0;
     }
-    if (vb < RHO)
-        return;
+    // initial window: rows vb - RHO .. vb + RHO
+    for (int u = tid; u < W; u += nthr) {
+        int s0 = 0, q0 = 0, s1 = 0, q1 = 0;
+        uint8_t xa[8], xb[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+            xa[r] = xb[r] = 0;
+        for (int y = vb - RHO; y <= vb + RHO; ++y) {
+            const int x = A[(size_t)y * W + u], z = B[(size_t)y * W + u];
+            xa[y % K] = (uint8_t)x;
+            xb[y % K] = (uint8_t)z;
+            s0 += x;
+            q0 += x * x;
+            s1 += z;
+            q1 += z * z;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            ca8[u * 8 + r] = xa[r];
+            cb8[u * 8 + r] = xb[r];
+        }
+        cs[u] = s0;
+        cs[W + u] = q0;
+        cs[2 * W + u] = s1;
+        cs[3 * W + u] = q1;
+    }
+    // the row entering next (vb - RHO - 1), loaded a row ahead
+    int na[kMaxColsPerThread], nb[kMaxColsPerThread];
+#pragma unroll
+    for (int k = 0; k < kMaxColsPerThread; ++k) {
+        const int u = tid + k * nthr, y = vb - RHO - 1;
+        na[k] = (u < W && y >= 0) ? A[(size_t)y * W + u] : 0;
+        nb[k] = (u < W && y >= 0) ? B[(size_t)y * W + u] : 0;
+    }
     int cur = 0;
     for (int v = vb; v >= RHO; --v) {
-        if (v == vb) {
-            for (int i = tid; i < K * W; i += kSrpThreads) {
-                const int r = i / W, u = i % W, y = v - RHO + r;
-                ra[(y % K) * Wp + u] = A[(size_t)y * W + u];
-                rb[(y % K) * Wp + u] = B[(size_t)y * W + u];
-            }
-            __syncthreads();
-            for (int u = tid; u < W; u += kSrpThreads) {
-                int s0 = 0, q0 = 0, s1 = 0, q1 = 0;
-                for (int r = 0; r < K; ++r) {
-                    const int x = ra[r * Wp + u], z = rb[r * Wp + u];
-                    s0 += x;
-                    q0 += x * x;
-                    s1 += z;
-                    q1 += z * z;
-                }
-                cs[u] = s0;
-                cs[W + u] = q0;
-                cs[2 * W + u] = s1;
-                cs[3 * W + u] = q1;
-            }
-        } else {
+        if (v < vb) {
             // row v + RHO + 1 leaves the window, row v - RHO enters (same ring slot)
-            const int y = v - RHO, slot = y % K;
-            for (int u = tid; u < W; u += kSrpThreads) {
-                const int xo = ra[slot * Wp + u], zo = rb[slot * Wp + u];
-                const int xn = A[(size_t)y * W + u], zn = B[(size_t)y * W + u];
-                ra[slot * Wp + u] = (uint8_t)xn;
-                rb[slot * Wp + u] = (uint8_t)zn;
-                cs[u] += xn - xo;
-                cs[W + u] += xn * xn - xo * xo;
-                cs[2 * W + u] += zn - zo;
-                cs[3 * W + u] += zn * zn - zo * zo;
+            const int slot = (v - RHO) % K;
+#pragma unroll
+            for (int k = 0; k < kMaxColsPerThread; ++k) {
+                const int u = tid + k * nthr;
+                if (u < W) {
+                    const int xo = ca8[u * 8 + slot], zo = cb8[u * 8 + slot];
+                    const int xn = na[k], zn = nb[k];
+                    ca8[u * 8 + slot] = (uint8_t)xn;
+                    cb8[u * 8 + slot] = (uint8_t)zn;
+                    cs[u] += xn - xo;
+                    cs[W + u] += xn * xn - xo * xo;
+                    cs[2 * W + u] += zn - zo;
+                    cs[3 * W + u] += zn * zn - zo * zo;
+                }
+            }
+            const int y = v - RHO - 1;   // prefetch the next entering row
+#pragma unroll
+            for (int k = 0; k < kMaxColsPerThread; ++k) {
+                const int u = tid + k * nthr;
+                if (u < W && y >= 0) {
+                    na[k] = A[(size_t)y * W + u];
+                    nb[k] = B[(size_t)y * W + u];
+                }
             }
         }
         __syncthreads();
-        for (int u = RHO + tid; u <= W - 1 - RHO; u += kSrpThreads) {
+        for (int u = RHO + tid; u <= W - 1 - RHO; u += nthr) {
             int s0 = 0, q0 = 0, s1 = 0, q1 = 0;
 #pragma unroll
             for (int x = -RHO; x <= RHO; ++x) {
@@ -118,74 +170,82 @@ __global__ void __launch_bounds__(kSrpThreads, 1) k_srp(const SrpArgs a)
                 s1 += cs[2 * W + u + x];
                 q1 += cs[3 * W + u + x];
             }
-            rs[u] = s0;
-            rs[W + u] = NB * q0 - s0 * s0;
-            rs[2 * W + u] = s1;
-            rs[3 * W + u] = NB * q1 - s1 * s1;
+            ra2[u] = make_int2(s0, NB * q0 - s0 * s0);
+            rb2[u] = make_int2(s1, NB * q1 - s1 * s1);
         }
         __syncthreads();
         const int16_t *below = lv + (cur ^ 1) * W;
         int16_t *here = lv + cur * W;
-        for (int u = tid; u < W; u += kSrpThreads) {
-            int best = 0;
-            if (u >= RHO && u <= W - 1 - RHO) {
-                int dhi = dir == 0 ? u - RHO : W - 1 - RHO - u;
-                dhi = dhi < a.dmax ? dhi : a.dmax;
-                int lo = 0, hi = dhi, l0 = -1000, l1 = -1000, l2 = -1000;
-                if (v < vb) {
-                    if (u - 1 >= RHO)
-                        l0 = below[u - 1];
-                    l1 = below[u];
-                    if (u + 1 <= W - 1 - RHO)
-                        l2 = below[u + 1];
-                    int mn = l1, mx = l1;
-                    if (l0 > -1000) {
-                        mn = min(mn, l0);
-                        mx = max(mx, l0);
-                    }
-                    if (l2 > -1000) {
-                        mn = min(mn, l2);
-                        mx = max(mx, l2);
-                    }
-                    lo = max(0, mn - a.tau);
-                    hi = min(dhi, mx + a.tau);
-                }
-                // this pixel's block of A, kept in registers
-                int blk[NB];
+        const int umax = W - 1 - RHO;
+        for (int u = RHO + tid; u <= umax; u += nthr) {
+            int dhi = dir == 0 ? u - RHO : W - 1 - RHO - u;
+            dhi = dhi < a.dmax ? dhi : a.dmax;
+            // the search range as up to three intervals in ascending order: [0, dhi] on the first row, else
+            // [l - tau, l + tau] around the sorted estimates below (duplicates skipped by starting each
+            // interval after the previous one's end)
+            int c0 = 0, c1 = -1000, c2 = -1000, span = dhi;   // centres (interval = [c - span, c + span])
+            bool first = v == vb;
+            if (!first) {
+                int l0 = u - 1 >= RHO ? below[u - 1] : -1000, l1 = below[u], l2 = u + 1 <= umax ? below[u + 1] : -1000;
+                // sort three values (missing ones, -1000, first)
+                if (l0 > l1) { const int t = l0; l0 = l1; l1 = t; }
+                if (l1 > l2) { const int t = l1; l1 = l2; l2 = t; }
+                if (l0 > l1) { const int t = l0; l0 = l1; l1 = t; }
+                c0 = l0;
+                c1 = l1;
+                c2 = l2;
+                span = a.tau;
+            }
+            // this pixel's block of A: its K columns, each the K ring rows in 8 bytes
+            uint2 acol[K];
 #pragma unroll
-                for (int r = 0; r < K; ++r)
+            for (int x = 0; x < K; ++x)
+                acol[x] = ca[u - RHO + x];
+            const int2 sa2 = ra2[u];
+            const int sa = sa2.x, Da = sa2.y;
+            long long bN = 0;
+            int bD = 0, best = -1, next = 0;   // next: smallest disparity not yet searched
+            for (int iv = first ? 2 : 0; iv < 3; ++iv) {
+                const int c = first ? span / 2 : (iv == 0 ? c0 : (iv == 1 ? c1 : c2));
+                if (c <= -1000)
+                    continue;
+                const int from = max(next, first ? 0 : c - span), to = min(dhi, first ? dhi : c + span);
+                if (from > to)
+                    continue;
+                for (int d = from; d <= to; ++d) {
+                    const int ub = dir == 0 ? u - d : u + d;
+                    uint2 bw[K];
 #pragma unroll
                     for (int x = 0; x < K; ++x)
-                        blk[r * K + x] = ra[r * Wp + u - RHO + x];
-                const int sa = rs[u], Da = rs[W + u];
-                long long bN = 0;
-                int bD = 0;
-                bool have = false;
-                for (int d = lo; d <= hi; ++d) {
-                    if (v < vb && abs(d - l0) > a.tau && abs(d - l1) > a.tau && abs(d - l2) > a.tau)
-                        continue;
-                    const int ub = dir == 0 ? u - d : u + d;
-                    int P = 0;
+                        bw[x] = cb[ub - RHO + x];
+                    unsigned p4[4] = {0u, 0u, 0u, 0u};   // four independent dp4a chains
 #pragma unroll
-                    for (int r = 0; r < K; ++r)
-#pragma unroll
-                        for (int x = 0; x < K; ++x)
-                            P += blk[r * K + x] * (int)rb[r * Wp + ub - RHO + x];
-                    long long N = (long long)NB * P - (long long)sa * rs[2 * W + ub];
+                    for (int x = 0; x < K; ++x) {
+                        p4[(2 * x) & 3] = __dp4a(acol[x].x, bw[x].x, p4[(2 * x) & 3]);
+                        p4[(2 * x + 1) & 3] = __dp4a(acol[x].y, bw[x].y, p4[(2 * x + 1) & 3]);
+                    }
+                    const unsigned P = (p4[0] + p4[1]) + (p4[2] + p4[3]);
+                    const int2 sb2 = rb2[ub];
+                    long long N = (long long)NB * (long long)P - (long long)sa * sb2.x;
                     if (Da == 0)
                         N = 0;
-                    const int Db = rs[3 * W + ub];
-                    if (!have || ncc_better(N, Db, bN, bD)) {
-                        have = true;
+                    if (best < 0 || ncc_better(N, sb2.y, bN, bD)) {
                         best = d;
                         bN = N;
-                        bD = Db;
+                        bD = sb2.y;
                     }
                 }
+                next = max(next, to + 1);
             }
-            here[u] = (int16_t)best;
-            out[(size_t)v * W + u] = (int16_t)best;
+            const int16_t val = (int16_t)(best < 0 ? 0 : best);
+            here[u] = val;
+            out[(size_t)v * W + u] = val;
         }
+        for (int u = tid; u < W; u += nthr)   // columns without a block
+            if (u < RHO || u > umax) {
+                here[u] = 0;
+                out[(size_t)v * W + u] = 0;
+            }
         __syncthreads();
         cur ^= 1;
     }
@@ -206,8 +266,8 @@ __global__ void k_lrc(const int16_t *lf, const int16_t *rt, int W, int H, int n,
 
 size_t srp_smem(int W, int rho)
 {
-    const int K = 2 * rho + 1, Wp = (W + 15) & ~15;
-    return (size_t)2 * K * Wp + sizeof(int) * 8 * (size_t)W + sizeof(int16_t) * 2 * (size_t)W;
+    (void)rho;
+    return sizeof(uint2) * 2 * (size_t)W + sizeof(int) * 8 * (size_t)W + sizeof(int16_t) * 2 * (size_t)W;
 }
 
 }  // namespace
@@ -262,7 +322,7 @@ cudaError_t launch_srp(const ld::SrpArgs &a, int n, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(ld::k_srp<RHO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    ld::k_srp<RHO><<<dim3(n, 2), ld::kSrpThreads, smem, s>>>(a);
+    ld::k_srp<RHO><<<dim3(n, 2), ld::srp_threads(a.W, RHO), smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -274,7 +334,7 @@ int enqueue_stereo(ld_stereo *st, const uint8_t *left, const uint8_t *right, int
     cudaError_t e = cudaSuccess;
     if (timed && (e = cudaEventRecord(st->ev[0], s)) != cudaSuccess)
         return scuda(st, e, "event");
-    ld::SrpArgs a{left, right, st->lf, st->rt, w, hh, st->sp.d_max, st->sp.tau, (w + 15) & ~15};
+    ld::SrpArgs a{left, right, st->lf, st->rt, w, hh, st->sp.d_max, st->sp.tau};
     switch (st->sp.rho) {
     case 1: e = launch_srp<1>(a, n, s); break;
     case 2: e = launch_srp<2>(a, n, s); break;

@@ -3,11 +3,13 @@ that a profiler attached to the process sees every kernel of every call as a sep
 
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4 learned 64
+    python -m paper_1807_02752_gb300.run_workload batch64_1242x375 3 stereo
 
 Each call launches the nine kernels of the path once, in order, on the handle's stream, and times each
 with CUDA events; the per-kernel times of the last call are printed.  With `learned [top_k]` each call is
 the learned form instead (the network with the package's trained weights ranks the starts; exact
-energies for the top_k coarse starts), timed as a whole.
+energies for the top_k coarse starts), timed as a whole.  With `stereo` each call is the stereo stage on
+the workload's stereo pairs (search range propagation for both maps, then the consistency check).
 """
 from __future__ import annotations
 
@@ -25,13 +27,25 @@ def main(argv=None):
     name = argv[0] if argv else "batch64_1242x375"
     calls = int(argv[1]) if len(argv) > 1 else 4
     learned = len(argv) > 2 and argv[2] == "learned"
+    stereo = len(argv) > 2 and argv[2] == "stereo"
     top_k = int(argv[3]) if len(argv) > 3 else 64
     if name not in scenes.WORKLOADS:
         raise SystemExit(f"unknown workload {name!r}; known: {', '.join(scenes.WORKLOADS)}")
     cfg, n = scenes.WORKLOADS[name]
-    disp, img, _ = scenes.make_batch(cfg, n)
     p = ld.default_params(n_disp=cfg.n_disp)
     det = ld.Detector(cfg.width, cfg.height, n, p)
+    if stereo:
+        pairs = [scenes.make_stereo_frame(cfg, k) for k in range(n)]
+        lt = torch.from_numpy(np.stack([x[0] for x in pairs])).cuda()
+        rt = torch.from_numpy(np.stack([x[1] for x in pairs])).cuda()
+        st = ld.Stereo(det)
+        out = torch.empty((n, cfg.height, cfg.width), dtype=torch.float32, device="cuda")
+        ms = [st.run_timed(lt, rt, out) for _ in range(calls)]
+        print(name, n, "frames, stereo: ms per call (propagation, check):", [list(map(float, m)) for m in ms])
+        st.close()
+        det.close()
+        return
+    disp, img, _ = scenes.make_batch(cfg, n)
     d = torch.from_numpy(disp).cuda()
     i = torch.from_numpy(img).cuda()
     out = det.alloc_lanes(n)
