@@ -27,6 +27,7 @@ if ROOT not in sys.path:
 METRIC = "frames/s @1242x375 batch 64 (plain vs learned proposal @≥99% agree); p99 ms"
 UNIT = "frames/s"
 WORKLOAD = "batch64_1242x375"
+STEREO_BASE = 5_000_000   # frame indices of the stereo pairs
 DTYPE = "u8/i32 (f32 decisions, f64 solves)"
 INT_OPS_PER_TAP = 4  # bilateral tap: Q15 weight product with rounding, shift, w*I accumulate, w accumulate
 
@@ -54,6 +55,16 @@ def _oracle_worker(args):
     t0 = time.perf_counter()
     r = oracle.detect(d, im, p, dumps=False)
     return time.perf_counter() - t0, r["n_lanes"]
+
+
+def _stereo_worker(k):
+    """One stereo pair of the workload's recipe and what scoring it needs (no detector arithmetic)."""
+    from paper_1807_02752_gb300 import scenes
+
+    cfg, _ = scenes.WORKLOADS[WORKLOAD]
+    left, right, clean, truth = scenes.make_stereo_frame(cfg, STEREO_BASE + k)
+    disp, _, _ = scenes.make_frame(cfg, STEREO_BASE + k)
+    return left, right, clean, disp, (truth.v_horizon, truth.lane_starts, truth.lane_widths, truth.lane_visible_rows)
 
 
 def oracle_pool(n_workers):
@@ -176,6 +187,78 @@ def bilateral_pixels(det, disp, W, H, n):
 WEIGHTS = os.path.join(ROOT, "paper_1807_02752_gb300", "proposal_weights.npy")
 
 
+def _recall(lanes, truths, W, S0):
+    tp = fn = 0
+    for r, (_, starts, widths, vis) in zip(lanes, truths):
+        det = np.asarray(r["start_u"])
+        used = np.zeros(len(det), bool)
+        for s_, w_, v_ in sorted(zip(starts, widths, vis), key=lambda x: x[0]):
+            if v_ < 40 or not -S0 <= s_ < W + S0:
+                continue
+            free = np.where(~used)[0]
+            k = free[np.argmin(np.abs(det[free] - s_))] if len(free) else -1
+            if k >= 0 and abs(det[k] - s_) <= w_ / 2 + 3:
+                tp += 1
+                used[k] = True
+            else:
+                fn += 1
+    return tp / max(1, tp + fn)
+
+
+def measure_stereo(args, pairs_async, det, stream, n):
+    """Stereo (Sec. 2.1) on n rendered pairs of the workload: the disparity alone and the whole path from
+    the pairs, timed with CUDA events on the handle's stream; the disparity against the planted one and
+    the lanes against the planted markings (beside the lanes from the generator's own disparity)."""
+    import torch
+
+    from paper_1807_02752_gb300 import ld
+
+    if pairs_async is None:
+        return None
+    pairs = pairs_async.get()
+    W, H = pairs[0][0].shape[1], pairs[0][0].shape[0]
+    L = torch.from_numpy(np.stack([p_[0] for p_ in pairs])).cuda()
+    R = torch.from_numpy(np.stack([p_[1] for p_ in pairs])).cuda()
+    G = torch.from_numpy(np.stack([p_[3] for p_ in pairs])).cuda()
+    clean = np.stack([p_[2] for p_ in pairs])
+    truths = [p_[4] for p_ in pairs]
+    reps = max(5, min(args.steps, 50))
+    with torch.cuda.stream(stream):
+        st = ld.Stereo(det)
+        disp = torch.empty((n, H, W), dtype=torch.float32, device="cuda")
+        lanes = det.alloc_lanes(n)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for _ in range(3):
+            st.run(L, R, disp)
+            st.detect(L, R, lanes)
+        ev[0].record(stream)
+        for _ in range(reps):
+            st.run(L, R, disp)
+        ev[1].record(stream)
+        for _ in range(reps):
+            st.detect(L, R, lanes)
+        ev[2].record(stream)
+        stream.synchronize()
+        d = disp.cpu().numpy()
+        from_pairs = ld.lanes_to_dicts(ld.Detector.lanes(lanes))
+        given = ld.lanes_to_dicts(ld.Detector.lanes(det.detect(G, L)))
+        stream.synchronize()
+        st.close()
+    ms_st, ms_all = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+    road = np.zeros(d.shape, bool)
+    for f, t in enumerate(truths):
+        road[f, int(t[0]) + 6:] = True
+    ok = road & (d > 0)
+    S0 = (det.n_starts(W) - W) // 2
+    return {"value": round(n / ms_st * 1e3, 1), "unit": UNIT, "ms_per_batch": round(ms_st, 4), "frames": n,
+            "from_pairs": {"value": round(n / ms_all * 1e3, 1), "ms_per_batch": round(ms_all, 4)},
+            "road_valid_fraction": round(float(ok.sum() / max(1, road.sum())), 4),
+            "road_within_1px": round(float(np.mean(np.abs(d[ok] - clean[ok]) <= 1.0)), 4),
+            "lane_recall_from_pairs": round(_recall(from_pairs, truths, W, S0), 4),
+            "lane_recall_given_disparity": round(_recall(given, truths, W, S0), 4),
+            "rho": 3, "tau": 1, "tr_lrc": 3}
+
+
 def measure_learned(args, dets, streams, disp, img, n, world):
     """The learned form (network-ranked starts, exact energies of the top-k) on the same handles, streams,
     inputs and step count as the plain form; agreement of its lanes with the plain lanes on both input
@@ -261,6 +344,9 @@ def run_ours(args):
     # the oracle pool starts before the first CUDA work so no process forks after it
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     pool = oracle_pool(min(16, host_cores())) if want_cpu else None
+    # stereo pairs render on host cores while the GPU runs (a spawn pool, started before any CUDA work)
+    spool = mp.get_context("spawn").Pool(min(16, host_cores())) if rank == 0 and not args.no_stereo else None
+    pairs_async = spool.map_async(_stereo_worker, range(64), chunksize=2) if spool else None
 
     cfg, n = scenes.WORKLOADS[WORKLOAD]
     W, H = cfg.width, cfg.height
@@ -375,6 +461,9 @@ def run_ours(args):
     e2e_s = replicas.max_over_ranks(e2e_s)
 
     learned = measure_learned(args, dets, streams, disp, img, n, world)
+    stereo = measure_stereo(args, pairs_async, dets[0], streams[0], n) if rank == 0 else None
+    if spool:
+        spool.close()
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -432,6 +521,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(n * H * W * 5), "d2h_bytes_per_step": int(n * ld.LANES_DTYPE.itemsize)},
             "gpu_launches": int(ld.load().ld_launches_per_detect() * args.steps),
             "learned": None if learned is None else dict(learned, vs_plain=round(learned["value"] / value, 4)),
+            "stereo": stereo,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -489,6 +579,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in tile shapes")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal form")
+    ap.add_argument("--no-stereo", action="store_true", help="skip the stereo stage measurement")
     ap.add_argument("--top-k", type=int, default=96, help="coarse starts the learned form evaluates per frame")
     ap.add_argument("--streams", type=int, default=4, help="library handles on separate streams, batches rotate over them")
     args = ap.parse_args()
