@@ -39,6 +39,7 @@ extern "C" {
 #define LD_E_NOMEM (-3)    /* device or pinned-host allocation failed in ld_create */
 #define LD_E_STATE (-4)    /* call not valid in the handle's current state (e.g. no detect yet) */
 #define LD_E_BUSY (-5)     /* serving: no slot of the frame's size class can take it now (admission) */
+#define LD_E_TIMEOUT (-6)  /* a bounded device-side wait ran out; the kernel stopped and released what it held */
 
 /* per-frame flags (ld_lanes.flags) */
 #define LD_F_NO_ROAD 1     /* no bottom run of rows with f(v) > 0 and f'(v) > 0 */
@@ -355,6 +356,10 @@ int ld_detect_learned(ld_net *net, const float *heatmap, const float *disp, cons
 /* Intermediate results of the last learned detection (synchronises the stream), as ld_debug_get. */
 size_t ld_net_debug_size(ld_net *net, int32_t stage);
 int ld_net_debug_get(ld_net *net, int32_t frame, int32_t stage, void *host_dst, size_t bytes);
+/* LD_OK, or LD_E_TIMEOUT when a tensor-core wait of a network kernel ran out since the last call (the
+ * kernel then stopped issuing work and released its tensor memory; results of that call are invalid).
+ * Synchronises the device. */
+int ld_net_status(ld_net *net);
 const char *ld_net_last_error(const ld_net *net);
 void ld_net_destroy(ld_net *net);
 

@@ -5,12 +5,13 @@
 // operands with FP32 accumulation, a per-cell logit z (the per-row heatmap is sigmoid(z)), top-k = 32.
 //
 //   k_conv1     layer 1 (one input channel) from the integer block sums; writes the bf16 input and A1
-//   k_conv      layers 2-4 as implicit GEMMs on the tensor cores (mma.sync m16n8k16, bf16 -> f32):
-//               an 8 x 16-cell output tile per CTA, its 10 x 18 halo in shared memory, one m16 tile per
-//               tile row, K = 9 taps x C_in; epilogues: bias + ReLU (+ the 1x1 head), or the backward
-//               data pass (transposed, flipped weights) times the ReLU mask of the layer below
-//   k_wgrad     weight and bias gradients of a layer: M = C_out, N = 9 C_in + 1 (a column of ones gives
-//               the bias), K = cells; per-CTA partial sums, then k_wreduce adds them in a fixed order
+//   k_conv_tc   layers 2-4 as implicit GEMMs on the tcgen05 tensor cores (bf16 -> f32 in tensor memory):
+//               a 16 x 8-cell output tile per MMA (M 128), K = 9 taps x C_in straight from the halo in
+//               shared memory; epilogues: bias + ReLU (+ the 1x1 head), or the backward data pass
+//               (transposed, flipped weights) times the ReLU mask of the layer below
+//   k_wgrad     weight and bias gradients of a layer (mma.sync m16n8k16): M = C_out, N = 9 C_in + 1 (a
+//               column of ones gives the bias), K = cells; per-CTA partial sums, then k_wreduce adds them
+//               in a fixed order
 //   k_loss      head, weighted logistic loss, dz, dS_4 and the head's gradient partials
 //   k_adam      Adam (Kingma & Ba, Algorithm 1) on the FP32 master weights, then the bf16 operand copies
 //   k_labels    training targets: cells crossed by the Eq. 25 tracks of the selected lanes
@@ -142,134 +143,257 @@ struct ConvIO {
 };
 
 
+// ---------------------------------------------------------------------------------------------------
+// layers 2-4 and the backward data pass on the 5th-generation tensor cores (tcgen05, accumulators in
+// tensor memory)
+//
+// Tile: 16 x 8 output cells = the 128 rows (M) of one MMA.  The tile's 18 x 10-cell halo sits in shared
+// memory as planes of 8 channels, 16 bytes per cell (plane stride 2880 B, halo row 160 B), which is the
+// no-swizzle K-major operand layout for every tap at once: for tap (dy, dx) and 16 input channels the A
+// operand starts at the tap's cell of the first plane, its two K halves are one plane apart (leading byte
+// offset 2880) and its 16 groups of 8 rows are the tile rows, one halo row apart (stride byte offset 160).
+// The weights sit in the matching layout for B (N = C_out rows): per K step of 16 channels, K halves
+// C_out x 16 B apart, groups of 8 output channels 128 B apart.  One thread issues the 9 C_in / 16 MMAs of a
+// tile (M 128, N C_out, K 16, bf16 -> f32) into one of two accumulators in tensor memory and commits them to
+// an mbarrier; meanwhile the CTA reads the other accumulator (tcgen05.ld, one tensor-memory lane quarter per
+// warp: a thread gets all C_out channels of one cell) for the previous tile's epilogue and copies the next
+// tile's halo in with cp.async (zero-filled outside the map).  Waits are bounded: on a timeout the kernel
+// records it in err and stops issuing work.
+// ---------------------------------------------------------------------------------------------------
+constexpr int kTcRows = 16, kTcCols = 8;                       // output tile (cells)
+constexpr int kTcHR = kTcRows + 2, kTcHC = kTcCols + 2;         // halo
+constexpr int kTcPlane = kTcHR * kTcHC * 16;                    // bytes of one 8-channel plane of the halo
+constexpr unsigned kTcSpin = 1u << 26;                           // wait limit (iterations)
+
 template <int CIN, int COUT>
-struct ConvSmem {
-    static constexpr int CINP = CIN + 8;           // padded cell stride (bank-conflict-free fragment loads)
-    static constexpr int KP = 9 * CIN + 8;         // padded weight row
-    static constexpr int in_elems = kHaloR * kHaloC * CINP;
-    static constexpr int w_elems = COUT * KP;
-    static constexpr size_t bytes = sizeof(__nv_bfloat16) * (size_t)(in_elems + w_elems);
+struct TcSmem {
+    static constexpr int halo = (CIN / 8) * kTcPlane;            // one halo buffer
+    static constexpr int wts = 9 * CIN * COUT * 2;               // B operand, all taps
+    static constexpr size_t bytes = 2 * (size_t)halo + wts + 128;
 };
 
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(kConvThreads) k_conv(const ConvIO io)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
 {
-    using S = ConvSmem<CIN, COUT>;
-    constexpr int NT = COUT / 8;
-    extern __shared__ __align__(16) __nv_bfloat16 csm[];
-    __nv_bfloat16 *sin = csm;
-    __nv_bfloat16 *sw = csm + S::in_elems;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    // weights once per CTA: row co holds 9 CIN values (a multiple of 8: 16-byte chunks)
-    for (int i = tid; i < COUT * (9 * CIN / 8); i += kConvThreads) {
-        const int co = i / (9 * CIN / 8), ch = i % (9 * CIN / 8);
-        *reinterpret_cast<uint4 *>(sw + co * S::KP + ch * 8) =
-            __ldg(reinterpret_cast<const uint4 *>(io.wt + (size_t)co * 9 * CIN + ch * 8));
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);   // no swizzle, base offset 0
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+{
+    for (unsigned it = 0; it < kTcSpin; ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done)
+            return true;
     }
+    return false;
+}
+
+template <int N>
+__device__ __forceinline__ void tc_load(uint32_t taddr, uint32_t (&r)[N]);
+
+template <>
+__device__ __forceinline__ void tc_load<16>(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <>
+__device__ __forceinline__ void tc_load<32>(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(kConvThreads) k_conv_tc(const ConvIO io, int *err)
+{
+    using S = TcSmem<CIN, COUT>;
+    extern __shared__ __align__(1024) unsigned char tsm_raw[];
+    __shared__ uint32_t taddr_s;
+    __shared__ __align__(8) uint64_t mbar[2];
+    unsigned char *halo[2] = {tsm_raw, tsm_raw + S::halo};
+    unsigned char *wsm = tsm_raw + 2 * S::halo;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mh = io.mh, mw = io.mw;
-    const int per_frame = io.tiles_r * io.tiles_c;
-    const int total = io.n * per_frame;
-    float hw[NT][2];
+    const int per_frame = io.tiles_r * io.tiles_c, total = io.n * per_frame;
+    // weights -> B layout: K step kk = tap (CIN/16) + c16, half h: 16-byte row n at
+    // kk (COUT 32) + h (COUT 16) + (n / 8) 128 + (n % 8) 16; a row holds the 8 input channels c16 16 + 8 h ..
+    for (int i = tid; i < COUT * 9 * (CIN / 8); i += kConvThreads) {
+        const int n = i / (9 * CIN / 8), rem = i % (9 * CIN / 8), tap = rem / (CIN / 8), c8 = rem % (CIN / 8);
+        const int kk = tap * (CIN / 16) + (c8 >> 1), h = c8 & 1;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(io.wt + (size_t)n * 9 * CIN + tap * CIN + c8 * 8));
+        *reinterpret_cast<uint4 *>(wsm + kk * COUT * 32 + h * COUT * 16 + (n >> 3) * 128 + (n & 7) * 16) = v;
+    }
+    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]), mb1 = (uint32_t)__cvta_generic_to_shared(&mbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&taddr_s);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(dst));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = taddr_s;
+    // the tiles this CTA owns: blockIdx.x, + gridDim.x, ...; those above the road rows are skipped
+    auto next_tile = [&](int t) {
+        for (; t < total; t += gridDim.x) {
+            const int f = t / per_frame, rem = t % per_frame;
+            if ((rem / io.tiles_c) * kTcRows + kTcRows - 1 >= first_needed_row(io.fs, f, io.depth))
+                return t;
+        }
+        return total;
+    };
+    auto load_halo = [&](int t, unsigned char *buf) {
+        const int f = t / per_frame, rem = t % per_frame;
+        const int y0 = (rem / io.tiles_c) * kTcRows - 1, x0 = (rem % io.tiles_c) * kTcCols - 1;
+        for (int i = tid; i < kTcHR * kTcHC * (CIN / 8); i += kConvThreads) {
+            const int p = i / (kTcHR * kTcHC), cell = i % (kTcHR * kTcHC);
+            const int yy = y0 + cell / kTcHC, xx = x0 + cell % kTcHC;
+            const bool in = yy >= 0 && yy < mh && xx >= 0 && xx < mw;
+            const __nv_bfloat16 *src = io.in + (((size_t)f * mh + (in ? yy : 0)) * mw + (in ? xx : 0)) * CIN + p * 8;
+            const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf + p * kTcPlane + cell * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float hw[16], bias[COUT];
     if (EPI == kEpiHead) {
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            hw[nt][0] = __bfloat162float(io.wh[nt * 8 + 2 * t]);
-            hw[nt][1] = __bfloat162float(io.wh[nt * 8 + 2 * t + 1]);
-        }
+        for (int c = 0; c < 16; ++c)
+            hw[c] = __bfloat162float(io.wh[c]);
     }
-    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int f = tile / per_frame, rem = tile % per_frame;
-        const int y0 = (rem / io.tiles_c) * kTileR, x0 = (rem % io.tiles_c) * kTileC;
-        if (y0 + kTileR - 1 < first_needed_row(io.fs, f, io.depth))
-            continue;   // uniform over the CTA
-        __syncthreads();   // previous tile's reads of sin are done (and the weights are in place)
-        constexpr int kChunks = CIN / 8;    // 16-byte chunks per cell
-        for (int i = tid; i < kHaloR * kHaloC * kChunks; i += kConvThreads) {
-            const int cell = i / kChunks, ch = i % kChunks;
-            const int yy = y0 - 1 + cell / kHaloC, xx = x0 - 1 + cell % kHaloC;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (yy >= 0 && yy < mh && xx >= 0 && xx < mw)
-                v = __ldg(reinterpret_cast<const uint4 *>(io.in + (((size_t)f * mh + yy) * mw + xx) * CIN) + ch);
-            *reinterpret_cast<uint4 *>(sin + cell * S::CINP + ch * 8) = v;
-        }
-        __syncthreads();
-        float acc[2][NT][4];
+    if (EPI != kEpiMask) {
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
+        for (int c = 0; c < COUT; ++c)
+            bias[c] = io.bias[c];
+    }
+    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((128u >> 4) << 24);
+    const uint32_t wbase = (uint32_t)__cvta_generic_to_shared(wsm);
+    bool ok = true;
+    int cur = next_tile(blockIdx.x), prev = total, it = 0;
+    uint32_t phase[2] = {0u, 0u};
+    if (cur < total)
+        load_halo(cur, halo[0]);
+    while (cur < total || prev < total) {
+        const int b = it & 1;
+        if (cur < total) {
+            // the halo of `cur` has landed: make it visible to the tensor cores and issue its MMAs
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (tid == 0 && ok) {
+                const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(halo[b]);
+                const uint32_t dacc = tbase + (uint32_t)(b * 32);
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
+                for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    acc[mt][nt][q] = 0.0f;
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;
-#pragma unroll
-            for (int kc = 0; kc < CIN / 16; ++kc) {
-                uint32_t af[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int hp = (2 * warp + mt + dy) * kHaloC + dx;   // halo cell of output column 0
-                    const __nv_bfloat16 *r0 = sin + (hp + g) * S::CINP + kc * 16 + 2 * t;
-                    const __nv_bfloat16 *r1 = sin + (hp + g + 8) * S::CINP + kc * 16 + 2 * t;
-                    af[mt][0] = *reinterpret_cast<const uint32_t *>(r0);
-                    af[mt][1] = *reinterpret_cast<const uint32_t *>(r1);
-                    af[mt][2] = *reinterpret_cast<const uint32_t *>(r0 + 8);
-                    af[mt][3] = *reinterpret_cast<const uint32_t *>(r1 + 8);
-                }
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    const __nv_bfloat16 *wr = sw + (nt * 8 + g) * S::KP + tap * CIN + kc * 16 + 2 * t;
-                    const uint32_t b0 = *reinterpret_cast<const uint32_t *>(wr);
-                    const uint32_t b1 = *reinterpret_cast<const uint32_t *>(wr + 8);
-#pragma unroll
-                    for (int mt = 0; mt < 2; ++mt)
-                        mma16816(acc[mt][nt], af[mt][0], af[mt][1], af[mt][2], af[mt][3], b0, b1);
-                }
+                    for (int c16 = 0; c16 < CIN / 16; ++c16) {
+                        const int kk = tap * (CIN / 16) + c16;
+                        const uint64_t ad = tc_desc(hbase + (2 * c16) * kTcPlane + ((tap / 3) * kTcHC + tap % 3) * 16,
+                                                    kTcPlane, kTcHC * 16);
+                        const uint64_t bd = tc_desc(wbase + kk * COUT * 32, COUT * 16, 128);
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                                     ::"r"(dacc), "l"(ad), "l"(bd), "r"(kIdesc), "r"(kk));
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(b ? mb1 : mb0) : "memory");
             }
         }
-        // epilogue: thread holds, for tile row 2 warp + mt, cells x0 + g (+8) and channels nt 8 + 2t (+1)
+        if (prev < total) {
+            // the previous tile: wait for its MMAs, then read its accumulator and store the cells
+            const int pb = b ^ 1;
+            if (ok && !__all_sync(0xffffffffu, tc_wait(pb ? mb1 : mb0, phase[pb]))) {
+                ok = false;   // uniform over the warp (tcgen05.ld is a warp-wide instruction)
+                if (lane == 0)
+                    atomicExch(err, 1);
+            }
+            phase[pb] ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int f = prev / per_frame, rem = prev % per_frame;
+            const int y = (rem / io.tiles_c) * kTcRows + warp * 4 + (lane >> 3), x = (rem % io.tiles_c) * kTcCols + (lane & 7);
+            uint32_t r[COUT];
+            if (ok)
+                tc_load<COUT>(tbase + (uint32_t)(pb * 32) + ((uint32_t)(warp * 32) << 16), r);
+            if (ok && y < mh && x < mw) {
+                const size_t cell = ((size_t)f * mh + y) * mw + x;
+                if (EPI == kEpiMask) {
+                    const uint4 *mk = reinterpret_cast<const uint4 *>(io.mask + cell * COUT);
+                    uint4 *dst = reinterpret_cast<uint4 *>(io.out + cell * COUT);
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int y = y0 + 2 * warp + mt;
+                    for (int q = 0; q < COUT / 8; ++q) {
+                        const uint4 m4 = __ldg(mk + q);
+                        const uint32_t mw4[4] = {m4.x, m4.y, m4.z, m4.w};
+                        uint32_t o[4];
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int x = x0 + g + 8 * half;
-                const bool in_map = y < mh && x < mw;
-                const size_t cell = ((size_t)f * mh + (y < mh ? y : 0)) * mw + (x < mw ? x : 0);
-                float zpart = 0.0f;
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    const int co = nt * 8 + 2 * t;
-                    float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                    if (EPI == kEpiMask) {
-                        if (in_map) {
-                            const uint32_t m = *reinterpret_cast<const uint32_t *>(io.mask + cell * COUT + co);
-                            v0 = bf_lo(m) > 0.0f ? v0 : 0.0f;
-                            v1 = bf_hi(m) > 0.0f ? v1 : 0.0f;
-                            *reinterpret_cast<uint32_t *>(io.out + cell * COUT + co) = pack2(v0, v1);
+                        for (int k = 0; k < 4; ++k) {
+                            const float v0 = bf_lo(mw4[k]) > 0.0f ? __uint_as_float(r[q * 8 + 2 * k]) : 0.0f;
+                            const float v1 = bf_hi(mw4[k]) > 0.0f ? __uint_as_float(r[q * 8 + 2 * k + 1]) : 0.0f;
+                            o[k] = pack2(v0, v1);
                         }
-                    } else {
-                        v0 = fmaxf(__fadd_rn(v0, io.bias[co]), 0.0f);
-                        v1 = fmaxf(__fadd_rn(v1, io.bias[co + 1]), 0.0f);
-                        const uint32_t pk = pack2(v0, v1);
-                        if (in_map && io.out)
-                            *reinterpret_cast<uint32_t *>(io.out + cell * COUT + co) = pk;
-                        if (EPI == kEpiHead)
-                            zpart = __fmaf_rn(hw[nt][1], bf_hi(pk), __fmaf_rn(hw[nt][0], bf_lo(pk), zpart));
+                        dst[q] = make_uint4(o[0], o[1], o[2], o[3]);
                     }
-                }
-                if (EPI == kEpiHead) {
-                    zpart += __shfl_xor_sync(0xffffffffu, zpart, 1);
-                    zpart += __shfl_xor_sync(0xffffffffu, zpart, 2);
-                    if (t == 0 && in_map) {
-                        const float zc = __fadd_rn(zpart, io.bh[0]);
+                } else {
+                    float zc = 0.0f;
+                    uint4 *dst = io.out ? reinterpret_cast<uint4 *>(io.out + cell * COUT) : nullptr;
+#pragma unroll
+                    for (int q = 0; q < COUT / 8; ++q) {
+                        uint32_t o[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int c = q * 8 + 2 * k;
+                            const float v0 = fmaxf(__fadd_rn(__uint_as_float(r[c]), bias[c]), 0.0f);
+                            const float v1 = fmaxf(__fadd_rn(__uint_as_float(r[c + 1]), bias[c + 1]), 0.0f);
+                            o[k] = pack2(v0, v1);
+                            if (EPI == kEpiHead)
+                                zc = __fmaf_rn(hw[c + 1], bf_hi(o[k]), __fmaf_rn(hw[c], bf_lo(o[k]), zc));
+                        }
+                        if (dst)
+                            dst[q] = make_uint4(o[0], o[1], o[2], o[3]);
+                    }
+                    if (EPI == kEpiHead) {
+                        zc = __fadd_rn(zc, io.bh[0]);
                         io.z[cell] = io.heat ? __frcp_rn(__fadd_rn(1.0f, expf(-zc))) : zc;
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;");
         }
+        // the next tile's halo goes into the buffer the previous tile's MMAs have finished with
+        prev = cur;
+        if (cur < total) {
+            cur = next_tile(cur + gridDim.x);
+            if (cur < total && ok)
+                load_halo(cur, halo[b ^ 1]);
+        }
+        ++it;
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tbase));
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -773,11 +897,28 @@ static int grid_for(int tiles, int per_sm)
     return tiles < g ? tiles : g;
 }
 
+__device__ int g_tc_error;   // set when a tensor-core wait ran out (read and cleared by net_tc_status)
+
 template <int CIN, int COUT, int EPI>
-static cudaError_t conv(const ConvIO &io, cudaStream_t s)
+static cudaError_t conv(ConvIO io, cudaStream_t s)
 {
+    using S = TcSmem<CIN, COUT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S::bytes);
+        if (e != cudaSuccess)
+            return e;
+        attr = true;
+    }
+    io.tiles_r = (io.mh + kTcRows - 1) / kTcRows;
+    io.tiles_c = (io.mw + kTcCols - 1) / kTcCols;
+    int *err = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&err, g_tc_error);
+    if (e != cudaSuccess)
+        return e;
     const int tiles = io.n * io.tiles_r * io.tiles_c;
-    k_conv<CIN, COUT, EPI><<<grid_for(tiles, 8), kConvThreads, ConvSmem<CIN, COUT>::bytes, s>>>(io);
+    k_conv_tc<CIN, COUT, EPI><<<grid_for(tiles, 4), kConvThreads, S::bytes, s>>>(io, err);
     return cudaGetLastError();
 }
 
@@ -900,6 +1041,16 @@ cudaError_t net_backward(const NetArgs &a, const uint8_t *labels, int n, float p
     if ((e = conv<32, 16, kEpiMask>(io, s)) != cudaSuccess)    // dS_1 (16)
         return e;
     return wgrad<1, 16>(a, a.dS[1], a.X, n, gw(0), gb(0), s);
+}
+
+int net_tc_status()
+{
+    int v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)) != cudaSuccess)
+        return -1;
+    if (v)
+        cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
+    return v;
 }
 
 cudaError_t net_pack(const NetArgs &a, cudaStream_t s)

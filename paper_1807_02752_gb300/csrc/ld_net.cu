@@ -458,6 +458,19 @@ int ld_net_debug_get(ld_net *net, int32_t frame, int32_t stage, void *host_dst, 
     return e == cudaSuccess ? LD_OK : ncuda(net, e, "debug copy");
 }
 
+int ld_net_status(ld_net *net)
+{
+    if (!net)
+        return LD_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(ld::handle_stream(net->h));
+    if (e != cudaSuccess)
+        return ncuda(net, e, "sync");
+    const int v = ld::net_tc_status();
+    if (v < 0)
+        return nfail(net, LD_E_CUDA, "status read");
+    return v ? nfail(net, LD_E_TIMEOUT, "a tensor-core wait ran out") : LD_OK;
+}
+
 const char *ld_net_last_error(const ld_net *net) { return net ? net->err.c_str() : g_net_error.c_str(); }
 
 void ld_net_destroy(ld_net *net)

@@ -41,6 +41,9 @@ cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, 
 cudaError_t net_backward(const NetArgs &a, const uint8_t *labels, int n, float pw, float *grad, float *loss,
                          cudaStream_t s);
 cudaError_t net_pack(const NetArgs &a, cudaStream_t s);
+// 1 when a tensor-core wait of a network kernel ran out since the last call (then cleared), 0 otherwise,
+// -1 when the flag could not be read (synchronous)
+int net_tc_status();
 cudaError_t net_adam(const NetArgs &a, const float *grad, float lr, float b1, float b2, float eps, float c1, float c2,
                      cudaStream_t s);
 cudaError_t net_labels(const KParams &kp, const Work &w, const ld_lanes *lanes, uint8_t *labels, int mh, int mw,

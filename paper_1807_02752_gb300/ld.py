@@ -144,6 +144,8 @@ def load():
     L.ld_net_debug_get.argtypes = [p, i32, i32, p, C.c_size_t]
     L.ld_net_debug_size.argtypes = [p, i32]
     L.ld_net_debug_size.restype = C.c_size_t
+    L.ld_net_status.argtypes = [p]
+    L.ld_net_status.restype = C.c_int
     L.ld_net_last_error.argtypes = [p]
     L.ld_net_last_error.restype = C.c_char_p
     L.ld_net_destroy.argtypes = [p]
@@ -175,7 +177,7 @@ EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_de
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
             "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
-            "ld_detect_learned", "ld_net_debug_size", "ld_net_debug_get", "ld_net_last_error", "ld_net_destroy",
+            "ld_detect_learned", "ld_net_debug_size", "ld_net_debug_get", "ld_net_status", "ld_net_last_error", "ld_net_destroy",
             "ld_stereo_params_default", "ld_stereo_create", "ld_stereo_run", "ld_stereo_run_timed", "ld_detect_stereo",
             "ld_stereo_maps", "ld_stereo_last_error", "ld_stereo_destroy"]
 
@@ -487,6 +489,10 @@ class Net:
         self._check(self.L.ld_detect_learned(self.h, None if heatmap is None else heatmap.data_ptr(),
                                              disp.data_ptr(), img.data_ptr(), W, H, n, top_k, out.data_ptr()))
         return out
+
+    def status(self):
+        """Raise if a tensor-core wait of the network kernels ran out (synchronises the device)."""
+        self._check(self.L.ld_net_status(self.h))
 
     def debug(self, frame: int, stage: int):
         size = int(self.L.ld_net_debug_size(self.h, stage))

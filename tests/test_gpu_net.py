@@ -98,6 +98,7 @@ def test_forward_matches_oracle(torch_cuda, name, n):
     theta = init_params(5)
     net.set_params(torch.from_numpy(theta).cuda())
     z = net.forward(xs, cfg.width, cfg.height).cpu().numpy()
+    net.status()   # no tensor-core wait ran out
     params = P.unpack(theta.astype(np.float64))
     op = oracle.default_params(n_disp=cfg.n_disp)
     for f, r in enumerate(_oracle_frames(disp, img, op)):
@@ -122,6 +123,7 @@ def test_gradient_matches_oracle(torch_cuda, name, n):
     rng = np.random.default_rng(7)
     labels = lb.cpu().numpy() | (rng.random(lb.shape) < 0.02).astype(np.uint8)
     g, loss = net.grad(xs, torch.from_numpy(labels).cuda(), cfg.width, cfg.height)
+    net.status()
     g, loss = g.cpu().numpy().astype(np.float64), float(loss.cpu().numpy()[0])
     op = oracle.default_params(n_disp=cfg.n_disp)
     X = np.stack([P.xmap_input(P.xmap_sums(r["Gw"])) for r in _oracle_frames(disp, img, op)])
