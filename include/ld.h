@@ -86,6 +86,8 @@ typedef struct ld_params {
                                  Sec. 2.4 text names, exp(-p^2 / sigma_g^2); p = dtheta / (pi / 36) */
     int32_t pad0;             /* 0 */
     int64_t thr_abs;          /* 0: relative lane threshold (thr_num / thr_den); < 0: absolute, H < thr_abs */
+    int32_t dp_literal;       /* 1: Eq. 12 as printed (the row v - tau, a -lambda_y tau reward); 0: the reading */
+    int32_t pad1;             /* 0 */
 } ld_params;
 
 /* Result of one frame (caller-allocated; device memory for ld_detect, host memory for ld_detect_host). */

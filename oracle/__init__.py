@@ -43,7 +43,7 @@ class Params(C.Structure):
         ("lambda_g", C.c_int32), ("xi_num", C.c_int32), ("xi_den", C.c_int32), ("thr_num", C.c_int32),
         ("thr_den", C.c_int32), ("near_px", C.c_int32), ("max_lanes", C.c_int32), ("ransac_hyps", C.c_int32),
         ("ransac_rounds", C.c_int32), ("seed", C.c_uint64), ("wg_gaussian", C.c_int32), ("pad0", C.c_int32),
-        ("thr_abs", C.c_int64),
+        ("thr_abs", C.c_int64), ("dp_literal", C.c_int32), ("pad1", C.c_int32),
     ]
 
     def as_dict(self):
@@ -81,6 +81,8 @@ def lib():
         L.or_vdisparity.argtypes = [p, i32, i32, i32, p]
         L.or_dp_vdisp.argtypes = [p, i32, i32, i32, i32, p]
         L.or_dp_vdisp.restype = C.c_int64
+        L.or_dp_vdisp_literal.argtypes = [p, i32, i32, i32, i32, p]
+        L.or_dp_vdisp_literal.restype = C.c_int64
         L.or_lsf.argtypes = [p, p, p, i32, i32, i32, i32, p]
         L.or_lsf.restype = i32
         L.or_hypothesis.argtypes = [p, p, p, i32, i32, C.c_float, i32, i32, i32, C.POINTER(Params), i32, i32, p, p]
@@ -169,6 +171,14 @@ def dp_vdisp(m_y: np.ndarray, tau: int = 6, lam: int = 1):
     H, D = m.shape
     path = np.zeros(D, np.int16)
     e = lib().or_dp_vdisp(_ptr(m), H, D, tau, lam, _ptr(path))
+    return int(e), path
+
+
+def dp_vdisp_literal(m_y: np.ndarray, tau: int = 6, lam: int = 1):
+    m = np.ascontiguousarray(m_y, np.int32)
+    H, D = m.shape
+    path = np.zeros(D, np.int16)
+    e = lib().or_dp_vdisp_literal(_ptr(m), H, D, tau, lam, _ptr(path))
     return int(e), path
 
 

@@ -55,6 +55,8 @@ void or_default_params(or_params *p)
     p->wg_gaussian = 0;
     p->pad0 = 0;
     p->thr_abs = 0;
+    p->dp_literal = 0;
+    p->pad1 = 0;
 }
 
 /* Sec. 2.4 and Alg. 7: the histogram H spans starts u in [-xi W, (1 + xi) W) (xi = 0.5). */
@@ -196,6 +198,53 @@ int64_t or_dp_vdisp(const int32_t *m_y, int32_t H, int32_t D, int32_t tau, int32
     path_v[1] = (int16_t)vbest;
     for (int32_t d = 1; d <= D - 2; d++)
         path_v[d + 1] = (int16_t)(path_v[d] + bt[(size_t)d * H + path_v[d]]);
+    free(Ep);
+    free(Ec);
+    free(bt);
+    return emin;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Eq. 12 as printed (dp_literal): E(v)_d = -m_y(d, v) + min_{tau in [0, tau_y], v - tau >= 0}          */
+/* [E(v - tau)_{d+1} - lambda tau], the link to the row v - tau and a reward for the jump.  Ties take  */
+/* the smaller tau; the path starts at the smallest v minimising E_1, then v_{d+1} = v_d - tau.       */
+/* ------------------------------------------------------------------------------------------------ */
+int64_t or_dp_vdisp_literal(const int32_t *m_y, int32_t H, int32_t D, int32_t tau, int32_t lambda, int16_t *path_v)
+{
+    int64_t *Ep = (int64_t *)malloc(sizeof(int64_t) * H);
+    int64_t *Ec = (int64_t *)malloc(sizeof(int64_t) * H);
+    uint8_t *bt = (uint8_t *)calloc((size_t)D * H, 1);
+    for (int32_t v = 0; v < H; v++)
+        Ep[v] = -(int64_t)m_y[(size_t)v * D + (D - 1)];
+    for (int32_t d = D - 2; d >= 1; d--) {
+        for (int32_t v = 0; v < H; v++) {
+            int64_t best = INT64_MAX;
+            int32_t arg = 0;
+            for (int32_t t = 0; t <= tau; t++) {
+                if (v - t < 0)
+                    break;
+                int64_t cand = Ep[v - t] - (int64_t)lambda * t;
+                if (cand < best) {
+                    best = cand;
+                    arg = t;
+                }
+            }
+            Ec[v] = -(int64_t)m_y[(size_t)v * D + d] + best;
+            bt[(size_t)d * H + v] = (uint8_t)arg;
+        }
+        int64_t *tmp = Ep;
+        Ep = Ec;
+        Ec = tmp;
+    }
+    int32_t vbest = 0;
+    for (int32_t v = 1; v < H; v++)
+        if (Ep[v] < Ep[vbest])
+            vbest = v;
+    int64_t emin = Ep[vbest];
+    path_v[0] = -1;
+    path_v[1] = (int16_t)vbest;
+    for (int32_t d = 1; d <= D - 2; d++)
+        path_v[d + 1] = (int16_t)(path_v[d] - bt[(size_t)d * H + path_v[d]]);
     free(Ep);
     free(Ec);
     free(bt);
@@ -718,7 +767,10 @@ int32_t or_detect(const float *disp, const uint8_t *img, int32_t W, int32_t H, c
     int32_t *m_y = (int32_t *)malloc(sizeof(int32_t) * (size_t)H * D);
     or_vdisparity(disp, W, H, D, m_y);
     int16_t *path_y = (int16_t *)malloc(sizeof(int16_t) * D);
-    or_dp_vdisp(m_y, H, D, p->tau_y, p->lambda_y, path_y);
+    if (p->dp_literal)
+        or_dp_vdisp_literal(m_y, H, D, p->tau_y, p->lambda_y, path_y);
+    else
+        or_dp_vdisp(m_y, H, D, p->tau_y, p->lambda_y, path_y);
     /* Reading: a path point whose cell holds no count carries no observation (the path crosses empty */
     /* bins beyond the largest road disparity, for instance); M_y keeps the points with m_y > 0.        */
     int32_t cap = D > H ? D : H, k = 0;

@@ -56,6 +56,8 @@ typedef struct or_params {
                                 exp(-p^2 / sigma_g^2); p = dtheta / (pi / 36) */
     int32_t pad0;
     int64_t thr_abs;         /* 0: t = ceil(thr * min H); < 0: the absolute threshold t = thr_abs */
+    int32_t dp_literal;      /* 1: Eq. 12 as printed (links to row v - tau, reward -lambda tau) */
+    int32_t pad1;
 } or_params;
 
 typedef struct or_lanes {
@@ -98,6 +100,7 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 
 void or_vdisparity(const float *disp, int32_t W, int32_t H, int32_t D, int32_t *m_y);
 int64_t or_dp_vdisp(const int32_t *m_y, int32_t H, int32_t D, int32_t tau, int32_t lambda, int16_t *path_v);
+int64_t or_dp_vdisp_literal(const int32_t *m_y, int32_t H, int32_t D, int32_t tau, int32_t lambda, int16_t *path_v);
 int32_t or_lsf(const int32_t *x, const int32_t *y, const uint8_t *use, int32_t n, int32_t m,
                int32_t centre, int32_t e, double *coef);
 int32_t or_hypothesis(const int32_t *x, const int32_t *y, const uint8_t *member, int32_t n, int32_t m,

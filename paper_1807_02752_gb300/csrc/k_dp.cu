@@ -10,7 +10,7 @@
 //
 // Readings: Eq. 12 as printed draws on E(v - tau)_{d+1} with -lambda tau; with rows counted from the top and
 // road disparity growing downwards, the consistent form links (d, v) to (d+1, v + tau) with a +lambda tau
-// penalty.  Eq. 18's "+lambda_x tau" is read as lambda_x |tau|.  Ties take the smaller |tau|, then the
+// penalty (the printed form is kept as the dp_literal switch, k_road_dp_lit).  Eq. 18's "+lambda_x tau" is read as lambda_x |tau|.  Ties take the smaller |tau|, then the
 // negative one; a path starts at the smallest index minimising its last row.  Alg. 5 is read from the text
 // around it: m_x(u, j) = -varrho * (votes in column u of rows [j - chi, j + chi] within [v_top, H-1]).
 // A path point whose cell holds no count carries no observation; the kernels hand the points with data to
@@ -221,6 +221,89 @@ __global__ void __launch_bounds__(1024) k_road_dp(const KParams kp, const Work w
         const uint8_t *row = bt + Hp;
         for (int d = 1; d <= D - 2; ++d, row += Hp) {
             v += (row[v >> 1] >> (4 * (v & 1))) & 15;
+            path[d + 1] = (int16_t)v;
+        }
+    }
+    __syncthreads();
+    for (int d = tid; d < D; d += nt) {
+        flag[d] = d >= 1 && my[(size_t)d * H + path[d]] > 0;
+        w.path_y[(size_t)f * D + d] = path[d];
+    }
+    __syncthreads();
+    const int k = block_compact(flag, D, pid, sh);
+    int16_t *gp = w.pts + (size_t)f * 2 * 3 * w.pmax;
+    for (int j = tid; j < k; j += nt) {
+        gp[j] = path[pid[j]];
+        gp[w.pmax + j] = pid[j];
+        gp[2 * w.pmax + j] = pid[j];
+    }
+    if (tid == 0)
+        w.npts[f * 2] = k;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// k_road_dp_lit: Eq. 12 as printed (dp_literal), for A/B against the reading above:
+//   E_d(v) = -m_y(d, v) + min_{tau in [0, tau_y], v - tau >= 0} [E_{d+1}(v - tau) - lambda_y tau],
+// ties to the smaller tau; the path starts at the smallest v minimising E_1 and steps to v - tau.  Plain
+// per-row loops (a thread per pair of rows, 4-bit backtrack entries of the pair in one byte); the same
+// shared-memory layout and outputs as k_road_dp.
+// ---------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_road_dp_lit(const KParams kp, const Work w)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int f = blockIdx.x, H = kp.H, D = kp.D, Hp = (H + 1) >> 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int32_t *my = w.myT + (size_t)f * D * H;
+    unsigned char *p = smem;
+    int *Ep = carve<int>(p, 2 * Hp + kPadY);
+    int *Ec = carve<int>(p, 2 * Hp + kPadY);
+    int *sh = carve<int>(p, kMaxChunks + 64);
+    int16_t *path = carve<int16_t>(p, D);
+    uint8_t *flag = carve<uint8_t>(p, D);
+    int16_t *pid = carve<int16_t>(p, D);
+    uint8_t *bt = carve<uint8_t>(p, (size_t)D * Hp);
+    for (int v = tid; v < H; v += nt)
+        Ep[v] = -my[(size_t)(D - 1) * H + v];
+    __syncthreads();
+    const int tau = kp.tau_y, lam = kp.lambda_y;
+    for (int d = D - 2; d >= 1; --d) {
+        for (int i = tid; i < Hp; i += nt) {
+            uint32_t code = 0;
+            for (int c = 0; c < 2; ++c) {
+                const int v = 2 * i + c;
+                if (v >= H)
+                    break;
+                int best = 0x7fffffff, arg = 0;
+                for (int t = 0; t <= tau && v - t >= 0; ++t) {
+                    const int cand = Ep[v - t] - lam * t;
+                    if (cand < best) {
+                        best = cand;
+                        arg = t;
+                    }
+                }
+                Ec[v] = -my[(size_t)d * H + v] + best;
+                code |= (uint32_t)arg << (4 * c);
+            }
+            bt[(size_t)d * Hp + i] = (uint8_t)code;
+        }
+        __syncthreads();
+        int *tmp = Ep;
+        Ep = Ec;
+        Ec = tmp;
+    }
+    int bv = 0x7fffffff, bi = 0x7fffffff;
+    for (int v = tid; v < H; v += nt)
+        if (Ep[v] < bv) {
+            bv = Ep[v];
+            bi = v;
+        }
+    const int vstar = block_argmin(bv, bi, sh + kMaxChunks);
+    if (tid == 0) {
+        path[0] = -1;
+        int v = vstar;
+        path[1] = (int16_t)v;
+        for (int d = 1; d <= D - 2; ++d) {
+            v -= (bt[(size_t)d * Hp + (v >> 1)] >> (4 * (v & 1))) & 15;
             path[d + 1] = (int16_t)v;
         }
     }
@@ -771,6 +854,8 @@ cudaError_t setup_dp(int smem_optin)
 {
     cudaError_t e = allow_max_smem(k_road_dp<6>, smem_optin);
     if (e == cudaSuccess)
+        e = allow_max_smem(k_road_dp_lit, smem_optin);
+    if (e == cudaSuccess)
         e = allow_max_smem(k_road_dp<15>, smem_optin);
     for (int t = 0; t <= 7 && e == cudaSuccess; ++t) {
         e = allow_max_smem(vpx_kernel_np<1>(t), smem_optin);
@@ -782,7 +867,10 @@ cudaError_t setup_dp(int smem_optin)
 
 cudaError_t launch_road(const KParams &kp, const Work &w, cudaStream_t s)
 {
-    road_kernel(kp.tau_y)<<<kp.n_frames, road_threads(kp.H), road_smem_bytes(kp), s>>>(kp, w);
+    if (kp.dp_literal)
+        k_road_dp_lit<<<kp.n_frames, road_threads(kp.H), road_smem_bytes(kp), s>>>(kp, w);
+    else
+        road_kernel(kp.tau_y)<<<kp.n_frames, road_threads(kp.H), road_smem_bytes(kp), s>>>(kp, w);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ struct KParams {
     int32_t S0, n_starts;
     int32_t thr_num, thr_den, near_px, max_lanes;
     long long thr_abs;                 // 0: relative threshold; < 0: lanes need H < thr_abs
+    int32_t dp_literal;                // 1: Eq. 12 as printed (k_road_dp_lit)
     int32_t hyps, rounds;
     uint32_t key0, key1;
     int32_t centre, e;                 // polynomial basis tau = (v - centre) / 2^e

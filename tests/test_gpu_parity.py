@@ -110,7 +110,8 @@ def test_param_variants(torch_cuda):
                {"chi": 5, "tau_x": 7, "lambda_x": 3}, {"thr_den": 4, "near_px": 5, "max_lanes": 2},
                {"ransac_rounds": 1}, {"box_nu": 0, "box_vs": 0}, {"box_nu": 3, "box_vs": 8},
                {"box_nu": 8, "box_vs": 1}, {"bilateral": 2}, {"bilateral": 2, "bf_rho": 2}, {"wg_gaussian": 1},
-               {"thr_abs": -(1 << 22)}, {"thr_abs": -(1 << 22), "wg_gaussian": 1, "bilateral": 2}):
+               {"thr_abs": -(1 << 22)}, {"thr_abs": -(1 << 22), "wg_gaussian": 1, "bilateral": 2},
+               {"dp_literal": 1}, {"dp_literal": 1, "tau_y": 3, "lambda_y": 2}):
         p = ld.default_params(n_disp=cfg.n_disp, **kw)
         det = ld.Detector(cfg.width, cfg.height, 3, p)
         res = _run(torch_cuda, det, disp, img)

@@ -60,3 +60,35 @@ def test_absolute_threshold_selection():
     assert ab["start_u"] == [2, 6] and ab["energy"] == [-90, -40]
     none = oracle.select(he, 0, oracle.default_params(near_px=1, thr_abs=-100))
     assert none["n_lanes"] == 0 and none["flags"] & oracle.F_NO_LANES
+
+
+def _brute_dp_literal(my, tau, lam):
+    """Every path of Eq. 12 as printed: v_{d+1} = v_d - tau_d, energy sum(-m_y) - lam sum(tau); ties to the
+    smaller start row, then the smaller steps in order."""
+    import itertools
+
+    H, D = my.shape
+    best = None
+    for v1 in range(H):
+        for steps in itertools.product(range(tau + 1), repeat=D - 2):
+            path = [v1]
+            for st in steps:
+                path.append(path[-1] - st)
+            if min(path) < 0:
+                continue
+            e = sum(-int(my[path[i], i + 1]) for i in range(D - 1)) - lam * sum(steps)
+            key = (e, v1, steps)
+            if best is None or key < best[0]:
+                best = (key, path)
+    return best[0][0], best[1]
+
+
+def test_literal_road_dp_matches_brute_force():
+    rng = np.random.default_rng(21)
+    for trial in range(30):
+        H, D, tau = 7, 5, int(rng.integers(1, 4))
+        lam = int(rng.integers(0, 3))
+        my = rng.integers(0, 4 if trial % 2 else 2, size=(H, D)).astype(np.int32)
+        e, path = oracle.dp_vdisp_literal(my, tau, lam)
+        be, bpath = _brute_dp_literal(my, tau, lam)
+        assert e == be and path[1:].tolist() == bpath, (trial, e, be, path, bpath)
