@@ -87,7 +87,7 @@ typedef struct ld_params {
     int32_t pad0;             /* 0 */
     int64_t thr_abs;          /* 0: relative lane threshold (thr_num / thr_den); < 0: absolute, H < thr_abs */
     int32_t dp_literal;       /* 1: Eq. 12 as printed (the row v - tau, a -lambda_y tau reward); 0: the reading */
-    int32_t pad1;             /* 0 */
+    int32_t band_literal_bottom; /* 1: Alg. 5's listing for the bottom rows j > v_max - chi - 1 (band [j, v_max]) */
 } ld_params;
 
 /* Result of one frame (caller-allocated; device memory for ld_detect, host memory for ld_detect_host). */

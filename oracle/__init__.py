@@ -43,7 +43,7 @@ class Params(C.Structure):
         ("lambda_g", C.c_int32), ("xi_num", C.c_int32), ("xi_den", C.c_int32), ("thr_num", C.c_int32),
         ("thr_den", C.c_int32), ("near_px", C.c_int32), ("max_lanes", C.c_int32), ("ransac_hyps", C.c_int32),
         ("ransac_rounds", C.c_int32), ("seed", C.c_uint64), ("wg_gaussian", C.c_int32), ("pad0", C.c_int32),
-        ("thr_abs", C.c_int64), ("dp_literal", C.c_int32), ("pad1", C.c_int32),
+        ("thr_abs", C.c_int64), ("dp_literal", C.c_int32), ("band_literal_bottom", C.c_int32),
     ]
 
     def as_dict(self):
@@ -99,7 +99,7 @@ def lib():
         L.or_lrc.argtypes = [p, p, i32, i32, i32, p]
         L.or_stereo.argtypes = [p, p, i32, i32, i32, i32, i32, i32, p, p, p]
         L.or_sobel.argtypes = [p, i32, i32, p, p]
-        L.or_band.argtypes = [p, i32, i32, i32, i32, i32, p]
+        L.or_band.argtypes = [p, i32, i32, i32, i32, i32, i32, p]
         L.or_dp_vpx.argtypes = [p, i32, i32, i32, i32, i32, p]
         L.or_dp_vpx.restype = C.c_int64
         L.or_box_sobel.argtypes = [p, i32, i32, i32, i32, p, p]
@@ -285,11 +285,11 @@ def sobel(I: np.ndarray):
     return gx, gy
 
 
-def band(votes: np.ndarray, v_top: int, chi: int = 25, rho: int = 1) -> np.ndarray:
+def band(votes: np.ndarray, v_top: int, chi: int = 25, rho: int = 1, literal_bottom: bool = False) -> np.ndarray:
     c = np.ascontiguousarray(votes, np.int32)
     H, W = c.shape
     m = np.zeros((H, W), np.int32)
-    lib().or_band(_ptr(c), W, H, v_top, chi, rho, _ptr(m))
+    lib().or_band(_ptr(c), W, H, v_top, chi, rho, 1 if literal_bottom else 0, _ptr(m))
     return m
 
 

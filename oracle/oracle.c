@@ -56,7 +56,7 @@ void or_default_params(or_params *p)
     p->pad0 = 0;
     p->thr_abs = 0;
     p->dp_literal = 0;
-    p->pad1 = 0;
+    p->band_literal_bottom = 0;
 }
 
 /* Sec. 2.4 and Alg. 7: the histogram H spans starts u in [-xi W, (1 + xi) W) (xi = 0.5). */
@@ -542,11 +542,15 @@ void or_sobel(const uint8_t *I, int32_t W, int32_t H, int16_t *gx, int16_t *gy)
 /* around it: row j holds minus rho times the votes of the band of rows [j - chi, j + chi], clipped to */
 /* the road rows [v_top, H - 1] (so the band is thinner at both ends).                               */
 /* ------------------------------------------------------------------------------------------------ */
-void or_band(const int32_t *votes, int32_t W, int32_t H, int32_t v_top, int32_t chi, int32_t rho, int32_t *m_x)
+void or_band(const int32_t *votes, int32_t W, int32_t H, int32_t v_top, int32_t chi, int32_t rho, int32_t literal_bottom,
+             int32_t *m_x)
 {
     memset(m_x, 0, sizeof(int32_t) * (size_t)W * H);
     for (int32_t j = v_top; j < H; j++) {
         int32_t lo = j - chi < v_top ? v_top : j - chi;
+        /* band_literal_bottom: the bottom rows j > v_max - chi - 1 use the band [j, v_max] of Alg. 5's listing */
+        if (literal_bottom && j > H - 1 - chi - 1)
+            lo = j;
         int32_t hi = j + chi > H - 1 ? H - 1 : j + chi;
         for (int32_t u = 0; u < W; u++) {
             int32_t s = 0;
@@ -880,7 +884,7 @@ int32_t or_detect(const float *disp, const uint8_t *img, int32_t W, int32_t H, c
 
         /* ---- Sec. 2.3.2-2.3.3: band accumulator, DP, RANSAC quartic, V_px ---- */
         int32_t *m_x = (int32_t *)malloc(sizeof(int32_t) * WH);
-        or_band(votes, W, H, v_top, p->chi, p->vote_rho, m_x);
+        or_band(votes, W, H, v_top, p->chi, p->vote_rho, p->band_literal_bottom, m_x);
         if (dumps->m_x)
             memcpy(dumps->m_x, m_x, sizeof(int32_t) * WH);
         int16_t *path_x = (int16_t *)calloc(H, sizeof(int16_t));

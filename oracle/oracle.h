@@ -57,7 +57,7 @@ typedef struct or_params {
     int32_t pad0;
     int64_t thr_abs;         /* 0: t = ceil(thr * min H); < 0: the absolute threshold t = thr_abs */
     int32_t dp_literal;      /* 1: Eq. 12 as printed (links to row v - tau, reward -lambda tau) */
-    int32_t pad1;
+    int32_t band_literal_bottom; /* 1: Alg. 5's listing for the bottom rows j > v_max - chi - 1: band [j, v_max] */
 } or_params;
 
 typedef struct or_lanes {
@@ -113,7 +113,7 @@ void or_bilateral(const uint8_t *img, int32_t W, int32_t H, const or_params *p, 
 void or_median(const uint8_t *img, int32_t W, int32_t H, int32_t rho, uint8_t *out);
 void or_sobel(const uint8_t *I, int32_t W, int32_t H, int16_t *gx, int16_t *gy);
 void or_band(const int32_t *votes, int32_t W, int32_t H, int32_t v_top, int32_t chi, int32_t rho,
-             int32_t *m_x);
+             int32_t literal_bottom, int32_t *m_x);
 int64_t or_dp_vpx(const int32_t *m_x, int32_t W, int32_t H, int32_t v_top, int32_t tau, int32_t lambda,
                   int16_t *path_u);
 void or_box_sobel(const int32_t *gw, int32_t W, int32_t H, int32_t nu, int32_t vs, int32_t *m0, int32_t *m1);

@@ -13,7 +13,8 @@ the batch time (eager launches, CUDA events).  One JSON line per workload and va
 Variants: the default readings; Sobel on the raw image (no pre-filter); the 11x11 median pre-filter of
 the authors' previous system (Sec. 2.3.1); w_g as the Gaussian the Sec. 2.4 text names instead of the
 printed exponential; one RANSAC hypothesis per round (the literal loop of Alg. 4 / Alg. 6); an absolute
-lane threshold instead of the relative one; Eq. 12 as printed (the road DP linked to the row above).
+lane threshold instead of the relative one; Eq. 12 as printed (the road DP linked to the row above);
+Alg. 5's listing for the bottom rows of the V_px accumulator.
 """
 from __future__ import annotations
 
@@ -32,6 +33,7 @@ VARIANTS = {
     "ransac_one_hypothesis": {"ransac_hyps": 1},
     "threshold_absolute": {"thr_abs": -(1 << 26)},
     "dp_literal": {"dp_literal": 1},
+    "band_literal_bottom": {"band_literal_bottom": 1},
 }
 
 

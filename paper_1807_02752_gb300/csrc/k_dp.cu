@@ -381,6 +381,22 @@ __device__ __forceinline__ void scatter_delta(const KParams &kp, const Work &w, 
                                               bool staged, uint32_t delta, int t0, int stride)
 {
     const int vmax = kp.H - 1, chi = kp.chi;
+    if (kp.band_literal && v >= vmax - chi - 1) {
+        // band_literal_bottom: rows j > vmax - chi - 1 use the band [j, vmax], so there row v enters and
+        // nothing leaves; at v = vmax - chi - 1 the band [v - chi, v + chi] replaces [v + 1, vmax]
+        const int r_lo = v >= vmax - chi ? v : max(vtop, v - chi);
+        for (int r = max(r_lo, vtop); r <= v; ++r) {
+            const VoteRow vr = vote_row(kp, w, S, f, r, staged);
+            for (int q = t0; q < vr.n; q += stride)
+                atoms_add(delta + 4u * (uint32_t)vr.p[q], 1);
+        }
+        if (v == vmax - chi - 1) {
+            const VoteRow vr = vote_row(kp, w, S, f, vmax, staged);
+            for (int q = t0; q < vr.n; q += stride)
+                atoms_add(delta + 4u * (uint32_t)vr.p[q], -1);
+        }
+        return;
+    }
     if (v - chi >= vtop) {
         const VoteRow vr = vote_row(kp, w, S, f, v - chi, staged);
         for (int q = t0; q < vr.n; q += stride)
@@ -531,7 +547,7 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
     uint8_t *gbt = w.gbt + (size_t)f * w.max_h * vpx_row_bytes(w.max_w);
     // ---- counts of row vmax: the votes of rows [max(vtop, vmax - chi), vmax], gathered in D0 ----
     {
-        const int r0 = max(vtop, vmax - chi);
+        const int r0 = kp.band_literal ? vmax : max(vtop, vmax - chi);   // the literal bottom band of row vmax is [vmax, vmax]
         if (staged) {
             for (int q = S.voff[r0] + tid; q < S.voff[vmax + 1]; q += nt)
                 atoms_add(d0 + 4u * (uint32_t)S.vb[q], 1);
@@ -731,7 +747,7 @@ __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
         __syncthreads();
         for (int v = R0 + tid; v < R1; v += nt) {
             const uint32_t *col = cb + (size_t)S.path[v] * HB;
-            const int lo = max(vtop, v - chi) - rb, hi = min(vmax, v + chi) - rb;
+            const int lo = (kp.band_literal && v > vmax - chi - 1 ? v : max(vtop, v - chi)) - rb, hi = min(vmax, v + chi) - rb;
             uint8_t sp = 0;
             for (int wd = lo >> 5; wd <= hi >> 5; ++wd) {
                 uint32_t m = col[wd];

@@ -138,8 +138,9 @@ const char *check_params(const ld_params *p)
         return "ransac_hyps must be in [1, 256] and ransac_rounds >= 1";
     if (p->bilateral < 0 || p->bilateral > 2)
         return "bilateral must be 0 (none), 1 (bilateral) or 2 (median)";
-    if (p->wg_gaussian < 0 || p->wg_gaussian > 1 || p->thr_abs > 0 || p->dp_literal < 0 || p->dp_literal > 1)
-        return "wg_gaussian and dp_literal must be 0 or 1 and thr_abs <= 0";
+    if (p->wg_gaussian < 0 || p->wg_gaussian > 1 || p->thr_abs > 0 || p->dp_literal < 0 || p->dp_literal > 1 ||
+        p->band_literal_bottom < 0 || p->band_literal_bottom > 1)
+        return "wg_gaussian, dp_literal and band_literal_bottom must be 0 or 1 and thr_abs <= 0";
     return nullptr;
 }
 
@@ -176,6 +177,7 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
     k.max_lanes = p.max_lanes;
     k.thr_abs = p.thr_abs;
     k.dp_literal = p.dp_literal;
+    k.band_literal = p.band_literal_bottom;
     k.hyps = p.ransac_hyps;
     k.rounds = p.ransac_rounds;
     k.key0 = (uint32_t)p.seed;

@@ -34,6 +34,7 @@ struct KParams {
     int32_t thr_num, thr_den, near_px, max_lanes;
     long long thr_abs;                 // 0: relative threshold; < 0: lanes need H < thr_abs
     int32_t dp_literal;                // 1: Eq. 12 as printed (k_road_dp_lit)
+    int32_t band_literal;              // 1: Alg. 5's bottom rows j > vmax - chi - 1 use the band [j, vmax]
     int32_t hyps, rounds;
     uint32_t key0, key1;
     int32_t centre, e;                 // polynomial basis tau = (v - centre) / 2^e

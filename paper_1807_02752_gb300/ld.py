@@ -34,7 +34,7 @@ class Params(C.Structure):
         ("lambda_g", C.c_int32), ("xi_num", C.c_int32), ("xi_den", C.c_int32), ("thr_num", C.c_int32),
         ("thr_den", C.c_int32), ("near_px", C.c_int32), ("max_lanes", C.c_int32), ("ransac_hyps", C.c_int32),
         ("ransac_rounds", C.c_int32), ("seed", C.c_uint64), ("wg_gaussian", C.c_int32), ("pad0", C.c_int32),
-        ("thr_abs", C.c_int64), ("dp_literal", C.c_int32), ("pad1", C.c_int32),
+        ("thr_abs", C.c_int64), ("dp_literal", C.c_int32), ("band_literal_bottom", C.c_int32),
     ]
 
     def as_dict(self):

@@ -53,7 +53,8 @@ def test_invalid_params_rejected_without_device(ldmod):
     L = ldmod.load()
     h = ctypes.c_void_p()
     for kw in ({"bf_rho": 6}, {"tau_x": 8}, {"n_disp": 300}, {"ransac_hyps": 0}, {"max_lanes": 9}, {"bilateral": 3},
-               {"wg_gaussian": 2}, {"thr_abs": 5}, {"dp_literal": 2}):
+               {"wg_gaussian": 2}, {"thr_abs": 5}, {"dp_literal": 2},
+               {"band_literal_bottom": 2}):
         p = ldmod.default_params(**kw)
         assert L.ld_create(ctypes.byref(p), 1242, 375, 4, None, ctypes.byref(h)) == ldmod.E_ARG
         assert h.value is None

@@ -111,7 +111,8 @@ def test_param_variants(torch_cuda):
                {"ransac_rounds": 1}, {"box_nu": 0, "box_vs": 0}, {"box_nu": 3, "box_vs": 8},
                {"box_nu": 8, "box_vs": 1}, {"bilateral": 2}, {"bilateral": 2, "bf_rho": 2}, {"wg_gaussian": 1},
                {"thr_abs": -(1 << 22)}, {"thr_abs": -(1 << 22), "wg_gaussian": 1, "bilateral": 2},
-               {"dp_literal": 1}, {"dp_literal": 1, "tau_y": 3, "lambda_y": 2}):
+               {"dp_literal": 1}, {"dp_literal": 1, "tau_y": 3, "lambda_y": 2}, {"band_literal_bottom": 1},
+               {"band_literal_bottom": 1, "chi": 5}, {"band_literal_bottom": 1, "chi": 0}):
         p = ld.default_params(n_disp=cfg.n_disp, **kw)
         det = ld.Detector(cfg.width, cfg.height, 3, p)
         res = _run(torch_cuda, det, disp, img)
@@ -123,7 +124,7 @@ def test_paper_literal_variants_full_size(torch_cuda):
     """The median pre-filter (ragged 8 x 32 tiles at 1242x375) and the Gaussian w_g at the full size."""
     cfg = scenes.SINGLE_1242x375
     disp, img, _ = scenes.make_batch(cfg, 2, first_frame=61)
-    for kw in ({"bilateral": 2}, {"wg_gaussian": 1}):
+    for kw in ({"bilateral": 2}, {"wg_gaussian": 1}, {"band_literal_bottom": 1}):
         p = ld.default_params(n_disp=cfg.n_disp, **kw)
         det = ld.Detector(cfg.width, cfg.height, 2, p)
         res = _run(torch_cuda, det, disp, img)

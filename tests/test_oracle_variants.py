@@ -92,3 +92,21 @@ def test_literal_road_dp_matches_brute_force():
         e, path = oracle.dp_vdisp_literal(my, tau, lam)
         be, bpath = _brute_dp_literal(my, tau, lam)
         assert e == be and path[1:].tolist() == bpath, (trial, e, be, path, bpath)
+
+
+def test_literal_bottom_band_matches_brute_force():
+    """Alg. 5 with the listing's bottom rows: band [j, v_max] for j > v_max - chi - 1, else [j - chi, j + chi],
+    clipped to [v_top, v_max]."""
+    rng = np.random.default_rng(31)
+    for trial in range(20):
+        H, W = int(rng.integers(10, 40)), int(rng.integers(5, 20))
+        chi, rho, v_top = int(rng.integers(0, 8)), int(rng.integers(1, 4)), int(rng.integers(0, 6))
+        votes = rng.integers(0, 3, (H, W)).astype(np.int32)
+        got = oracle.band(votes, v_top, chi, rho, literal_bottom=True)
+        want = np.zeros((H, W), np.int64)
+        for j in range(v_top, H):
+            lo, hi = (j, H - 1) if j > H - 1 - chi - 1 else (max(v_top, j - chi), min(H - 1, j + chi))
+            want[j] = -rho * votes[lo:hi + 1].sum(axis=0)
+        assert np.array_equal(got, want), trial
+        assert np.array_equal(oracle.band(votes, v_top, chi, rho)[:max(v_top, H - 1 - chi)],
+                              got[:max(v_top, H - 1 - chi)])
