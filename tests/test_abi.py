@@ -63,3 +63,18 @@ def test_invalid_params_rejected_without_device(ldmod):
     for size in ((8, 375, 1), (1242, 2000, 1), (1242, 375, 0), (5000, 375, 1)):
         assert L.ld_create(ctypes.byref(p), *size, None, ctypes.byref(h)) == ldmod.E_ARG
     assert L.ld_destroy(None) is None
+
+
+def test_object_entry_points_reject_null_handles_without_device(ldmod):
+    """The network and stereo objects refuse a missing handle before touching the device."""
+    L = ldmod.load()
+    out = ctypes.c_void_p()
+    assert L.ld_net_create(None, 0, ctypes.byref(out)) == ldmod.E_ARG and out.value is None
+    assert L.ld_net_last_error(None)
+    sp = ldmod.stereo_params()
+    assert (sp.rho, sp.tau, sp.d_max, sp.tr_lrc) == (3, 1, -1, 3)
+    assert L.ld_stereo_create(None, ctypes.byref(sp), ctypes.byref(out)) == ldmod.E_ARG and out.value is None
+    assert L.ld_stereo_last_error(None)
+    assert L.ld_net_param_count() == ldmod.NET_PARAMS
+    for fn in (L.ld_net_status, L.ld_net_destroy, L.ld_stereo_destroy):
+        fn(None)

@@ -294,3 +294,35 @@ def test_captured_split_learned_form_equals_eager(torch_cuda):
         net.close()
         det.close()
     assert results[0] == results[1]
+
+
+def test_network_argument_and_state_errors(torch_cuda):
+    torch = torch_cuda
+    cfg = scenes.SMALL_320x120
+    det = ld.Detector(cfg.width, cfg.height, 2, ld.default_params(n_disp=cfg.n_disp))
+    net = ld.Net(det)                       # inference only
+    d = torch.zeros((2, cfg.height, cfg.width), dtype=torch.float32, device="cuda")
+    i = torch.zeros((2, cfg.height, cfg.width), dtype=torch.uint8, device="cuda")
+    mh, mw = P.map_shape(cfg.height, cfg.width)
+    xs = torch.zeros((2, mh, mw), dtype=torch.int32, device="cuda")
+    lb = torch.zeros((2, mh, mw), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ld.LDError) as e:
+        net.grad(xs, lb, cfg.width, cfg.height)      # no training memory
+    assert e.value.code == ld.E_STATE
+    for k in (0, ld.NET_TOPK_MAX + 1):
+        with pytest.raises(ld.LDError) as e:
+            net.detect(d, i, top_k=k)
+        assert e.value.code == ld.E_ARG
+    with pytest.raises(ld.LDError) as e:
+        net.forward(torch.zeros((3, mh, mw), dtype=torch.int32, device="cuda"), cfg.width, cfg.height)  # > max batch
+    assert e.value.code == ld.E_ARG
+    with pytest.raises(ld.LDError) as e:
+        net.debug(0, ld.NET_STAGE_HEATMAP)            # no learned detection yet
+    assert e.value.code == ld.E_STATE
+    out = net.detect(d, i, top_k=4)                  # empty frames: no road, no lanes, no fallback
+    torch.cuda.synchronize()
+    lanes = ld.Detector.lanes(out)
+    assert (lanes["n_lanes"] == 0).all() and not (lanes["flags"] & ld.F_FALLBACK).any()
+    net.status()
+    net.close()
+    det.close()

@@ -89,3 +89,27 @@ def test_detect_from_stereo_pairs_matches_oracle(torch_cuda):
             assert got[f][k] == ref[k], (f, k, got[f][k], ref[k])
     st.close()
     det.close()
+
+
+def test_stereo_argument_errors(torch_cuda):
+    torch = torch_cuda
+    cfg = scenes.SMALL_320x120
+    det = ld.Detector(cfg.width, cfg.height, 2, ld.default_params(n_disp=cfg.n_disp))
+    for kw in ({"rho": 4}, {"rho": 0}, {"tau": -1}, {"d_max": -2}, {"tr_lrc": -1}):
+        with pytest.raises(ld.LDError) as e:
+            ld.Stereo(det, ld.stereo_params(**kw))
+        assert e.value.code == ld.E_ARG
+    st = ld.Stereo(det)
+    with pytest.raises(ld.LDError) as e:
+        st.maps(0, cfg.width, cfg.height)             # no call yet
+    assert e.value.code == ld.E_STATE
+    big = torch.zeros((3, cfg.height, cfg.width), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ld.LDError) as e:
+        st.run(big, big)                                # more frames than the handle's batch
+    assert e.value.code == ld.E_ARG
+    wide = torch.zeros((1, cfg.height, cfg.width + 1), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ld.LDError) as e:
+        st.run(wide, wide)
+    assert e.value.code == ld.E_ARG
+    st.close()
+    det.close()
