@@ -270,6 +270,14 @@ int ld_server_create(const ld_params *p, const ld_server_config *cfg, ld_server 
 int ld_server_submit(ld_server *s, int32_t stream_id, const float *disp, const uint8_t *img, int32_t w, int32_t h,
                      uint64_t tag);
 
+/* Switch the server's batches to the learned form (ld_detect_learned below, with the network run and the
+ * given top_k) or, with top_k = 0, back to the plain form.  params: DEVICE pointer to LD_NET_PARAMS floats,
+ * copied into an inference network on every slot's handle before the call returns (networks are created on
+ * the first call and kept; 168 bytes per 4 x 4 pixel block of a slot's batch).  Only while no frame
+ * is in the server.  Errors: LD_E_ARG (top_k outside [0, LD_NET_TOPK_MAX], null params with top_k > 0),
+ * LD_E_STATE (frames filling or in flight: drain first), LD_E_NOMEM, LD_E_CUDA. */
+int ld_server_set_learned(ld_server *s, const float *params, int32_t top_k);
+
 /* Move up to max_out completed results into out (host array); waits up to timeout_ms for the first one.
  * Returns the number moved (>= 0) or a negative LD_E_* code. */
 int ld_server_poll(ld_server *s, ld_result *out, int32_t max_out, int32_t timeout_ms);
@@ -312,8 +320,8 @@ void ld_server_destroy(ld_server *s);
  *
  * Parameters are a flat float32 vector of LD_NET_PARAMS values: for each convolution W[co][ci][3][3] then
  * b[co]; then the head's w[16] and b.  A network is created for a detector handle and uses its stream and
- * its largest frame and batch; it owns its activations (about 5 KB per cell of the largest batch while
- * training, 2.5 KB otherwise), its master weights and Adam state.  All buffer arguments are DEVICE
+ * its largest frame and batch; it owns its activations (168 bytes per cell of the largest batch, 330
+ * while training), its master weights and Adam state.  All buffer arguments are DEVICE
  * pointers owned by the caller; calls enqueue on the handle's stream and return without waiting.
  * Errors: LD_E_ARG, LD_E_NOMEM, LD_E_STATE (training call on an inference network), LD_E_CUDA.
  */

@@ -167,4 +167,6 @@ cudaError_t setup_grad(int smem_optin);
 cudaError_t setup_lpv(int smem_optin);
 int detect_eager(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
                  ld_lanes *out_lanes);
+int detect_learned_eager(ld_net *net, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+                         int32_t top_k, ld_lanes *out_lanes);
 }  // namespace ld

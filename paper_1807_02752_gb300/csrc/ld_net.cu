@@ -132,6 +132,23 @@ int enqueue_learned(ld_net *net, const float *heatmap, const float *disp, const 
     return e == cudaSuccess ? LD_OK : ncuda(net, e, "proposal");
 }
 
+// Argument checks and the bookkeeping of a learned detection, shared by the captured and the eager call.
+int start_learned(ld_net *net, const float *disp, const uint8_t *img, int w, int hh, int n, int top_k, ld_lanes *out)
+{
+    if (top_k < 1 || top_k > ld::kTopKMax)
+        return nfail(net, LD_E_ARG, "top_k outside [1, 256]");
+    ld_handle *h = net->h;
+    const int rc = ld::handle_check(h, disp, img, w, hh, n, out);
+    if (rc != LD_OK)
+        return nfail(net, rc, ld_last_error(h));
+    ld::handle_call(h, w, hh, n);
+    net->last_w = w;
+    net->last_h = hh;
+    net->last_n = n;
+    net->have_last = true;
+    return LD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -351,18 +368,10 @@ int ld_detect_learned(ld_net *net, const float *heatmap, const float *disp, cons
 {
     if (!net)
         return LD_E_ARG;
-    if (top_k < 1 || top_k > ld::kTopKMax)
-        return nfail(net, LD_E_ARG, "top_k outside [1, 256]");
-    ld_handle *h = net->h;
-    int rc = ld::handle_check(h, disp, img, w, hh, n, out);
+    int rc = start_learned(net, disp, img, w, hh, n, top_k, out);
     if (rc != LD_OK)
-        return nfail(net, rc, ld_last_error(h));
-    ld::handle_call(h, w, hh, n);
-    net->last_w = w;
-    net->last_h = hh;
-    net->last_n = n;
-    net->have_last = true;
-    cudaStream_t s = ld::handle_stream(h);
+        return rc;
+    cudaStream_t s = ld::handle_stream(net->h);
     for (LearnedGraph &g : net->graphs)
         if (g.exec && g.disp == disp && g.img == img && g.heat == heatmap && g.out == out && g.w == w && g.h == hh &&
             g.n == n && g.k == top_k) {
@@ -494,3 +503,19 @@ void ld_net_destroy(ld_net *net)
 }
 
 }  // extern "C"
+
+namespace ld {
+// ld_detect_learned without the graph cache: the launches are enqueued directly on the handle's stream
+// (the serving path, whose batch sizes vary from call to call).
+int detect_learned_eager(ld_net *net, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+                         int32_t top_k, ld_lanes *out_lanes)
+{
+    if (!net)
+        return LD_E_ARG;
+    const int rc = start_learned(net, disp, img, w, hh, n_frames, top_k, out_lanes);
+    if (rc != LD_OK)
+        return rc;
+    return enqueue_learned(net, nullptr, disp, img, w, hh, 0, n_frames, n_frames, top_k, out_lanes,
+                           handle_stream(net->h));
+}
+}  // namespace ld

@@ -2,7 +2,8 @@
 // several sizes from several camera streams over a fixed set of slots.
 //
 // A slot is one library handle with its own CUDA stream, pinned host staging for max_batch frames and the
-// device buffers the batch runs from.  Slots cycle FREE -> FILLING (frames copied in by submit) ->
+// device buffers the batch runs from (plus, once the learned form is switched on, an inference network on
+// that handle).  Slots cycle FREE -> FILLING (frames copied in by submit) ->
 // IN_FLIGHT (copies, the nine kernels, the result copy and a host callback enqueued on the slot's stream)
 // -> FREE (the callback has moved the results to the completion queue).  A scheduler thread launches a
 // filling slot whose oldest frame has waited max_wait_us.  After each batch the slot's stream also
@@ -42,6 +43,7 @@ struct Slot {
     ld_server *server = nullptr;
     int cls = 0;
     ld_handle *h = nullptr;
+    ld_net *net = nullptr;            // the learned form's network on h (created by ld_server_set_learned)
     cudaStream_t stream = nullptr;
     float *h_disp = nullptr;          // pinned [max_batch][h][w]
     uint8_t *h_img = nullptr;
@@ -92,6 +94,7 @@ struct ld_server {
     std::condition_variable cv_sched;  // the scheduler's wake-up
     std::deque<ld_result> results;
     std::vector<double> latencies;
+    int top_k = 0;                     // > 0: batches run the learned form with this top_k
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, batched_frames = 0;
     int in_flight = 0;
     bool stop = false;
@@ -132,9 +135,15 @@ int launch_slot(ld_server *s, Slot &sl)
         e = cudaMemcpyAsync(sl.d_meta, sl.h_meta, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, sl.stream);
     if (e != cudaSuccess)
         return sfail(s, LD_E_CUDA, std::string("batch input copy: ") + cudaGetErrorString(e));
-    int rc = ld::detect_eager(sl.h, sl.d_disp, sl.d_img, w, hh, n, sl.d_lanes);
-    if (rc != LD_OK)
-        return sfail(s, rc, std::string("batch detect: ") + ld_last_error(sl.h));
+    if (s->top_k > 0) {
+        const int rc = ld::detect_learned_eager(sl.net, sl.d_disp, sl.d_img, w, hh, n, s->top_k, sl.d_lanes);
+        if (rc != LD_OK)
+            return sfail(s, rc, std::string("batch detect (learned): ") + ld_net_last_error(sl.net));
+    } else {
+        const int rc = ld::detect_eager(sl.h, sl.d_disp, sl.d_img, w, hh, n, sl.d_lanes);
+        if (rc != LD_OK)
+            return sfail(s, rc, std::string("batch detect: ") + ld_last_error(sl.h));
+    }
     e = cudaMemcpyAsync(sl.h_lanes, sl.d_lanes, sizeof(ld_lanes) * n, cudaMemcpyDeviceToHost, sl.stream);
     if (e == cudaSuccess)
         e = cudaEventRecord(sl.done, sl.stream);
@@ -209,6 +218,8 @@ void scheduler_loop(ld_server *s)
 
 void free_slot(Slot &sl)
 {
+    if (sl.net)
+        ld_net_destroy(sl.net);
     if (sl.h)
         ld_destroy(sl.h);
     if (sl.stream)
@@ -366,6 +377,34 @@ int ld_server_submit(ld_server *s, int32_t stream_id, const float *disp, const u
     else if (target->n == 1)
         s->cv_sched.notify_one();  // a new deadline
     return rc;
+}
+
+int ld_server_set_learned(ld_server *s, const float *params, int32_t top_k)
+{
+    if (!s)
+        return LD_E_ARG;
+    if (top_k < 0 || top_k > LD_NET_TOPK_MAX || (top_k > 0 && !params))
+        return sfail(s, LD_E_ARG, "top_k outside [0, LD_NET_TOPK_MAX] or null parameters");
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->in_flight > 0 || s->submitted != s->completed)
+        return sfail(s, LD_E_STATE, "frames are in the server: drain it first");
+    // nothing is filling or in flight, so no callback needs the lock while the slots are set up
+    if (top_k > 0)
+        for (Slot &sl : s->slots) {
+            if (!sl.net) {
+                const int rc = ld_net_create(sl.h, 0, &sl.net);
+                if (rc != LD_OK)
+                    return sfail(s, rc, std::string("slot network: ") + ld_net_last_error(nullptr));
+            }
+            int rc = ld_net_set_params(sl.net, params);
+            if (rc != LD_OK)
+                return sfail(s, rc, std::string("slot network parameters: ") + ld_net_last_error(sl.net));
+            const cudaError_t e = cudaStreamSynchronize(sl.stream);   // the caller may release params now
+            if (e != cudaSuccess)
+                return sfail(s, LD_E_CUDA, std::string("slot network parameters: ") + cudaGetErrorString(e));
+        }
+    s->top_k = top_k;
+    return LD_OK;
 }
 
 int ld_server_poll(ld_server *s, ld_result *out, int32_t max_out, int32_t timeout_ms)

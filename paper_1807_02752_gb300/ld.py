@@ -130,6 +130,8 @@ def load():
     L.ld_server_last_error.restype = C.c_char_p
     L.ld_server_destroy.argtypes = [p]
     L.ld_server_destroy.restype = None
+    L.ld_server_set_learned.argtypes = [p, p, i32]
+    L.ld_server_set_learned.restype = C.c_int
     L.ld_net_param_count.argtypes = []
     L.ld_net_param_count.restype = i32
     L.ld_net_create.argtypes = [p, i32, C.POINTER(p)]
@@ -175,7 +177,7 @@ EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_de
             "ld_debug_get", "ld_debug_size", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
             "ld_destroy", "ld_road_path_static", "ld_tune", "ld_server_create", "ld_server_submit", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
-            "ld_server_destroy", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
+            "ld_server_destroy", "ld_server_set_learned", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
             "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
             "ld_detect_learned", "ld_net_debug_size", "ld_net_debug_get", "ld_net_status", "ld_net_last_error", "ld_net_destroy",
             "ld_stereo_params_default", "ld_stereo_create", "ld_stereo_run", "ld_stereo_run_timed", "ld_detect_stereo",
@@ -371,6 +373,17 @@ class Server:
         if rc != 0:
             raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
         return True
+
+    def set_learned(self, theta=None, top_k: int = 0):
+        """Run the batches in the learned form (theta: float32 device tensor of NET_PARAMS values, copied in)
+        or, with top_k = 0, in the plain form.  Only while no frame is in the server."""
+        if top_k > 0:
+            assert theta is not None and theta.is_cuda and theta.numel() == NET_PARAMS
+            assert theta.dtype.itemsize == 4 and theta.is_contiguous()
+        ptr = None if theta is None else theta.data_ptr()
+        rc = self.L.ld_server_set_learned(self.s, ptr, top_k)
+        if rc != 0:
+            raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
 
     def poll(self, max_out: int = 256, timeout_ms: int = 0) -> np.ndarray:
         out = np.zeros(max_out, RESULT_DTYPE)

@@ -2,13 +2,16 @@
 
     python -m paper_1807_02752_gb300.serve --streams 8 --fps 60 --seconds 10
     python -m paper_1807_02752_gb300.serve --streams 8 --saturate --seconds 5
+    python -m paper_1807_02752_gb300.serve --streams 8 --fps 60 --seconds 10 --learned 96
 
 Each camera stream has a fixed resolution (stream k takes size k mod the number of sizes) and submits
 frames at exponential inter-arrival times of mean 1/fps (or back to back with --saturate, a closed loop
 that resubmits as soon as the server admits a frame).  Frames are seeded synthetic scenes of the size's
 workload, generated before the clock starts and reused round-robin.  One JSON line reports the frames/s
 completed, p50/p99 latency from submit to result in host memory (overall and per size), the mean batch
-size and the admissions refused (a refused frame is retried after the next poll).
+size and the admissions refused (a refused frame is retried after the next poll).  --learned K runs
+every batch in the learned form with top_k = K and the package's trained network weights; the line then
+also counts the frames that fell back to the exhaustive search.
 """
 from __future__ import annotations
 
@@ -44,6 +47,8 @@ def main(argv=None):
     ap.add_argument("--max-wait-us", type=int, default=2000)
     ap.add_argument("--frames-per-size", type=int, default=8)
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--learned", type=int, default=0, metavar="TOP_K",
+                    help="learned form with this top_k (0: plain form)")
     args = ap.parse_args(argv)
 
     sizes = [tuple(int(x) for x in s.split("x")) for s in args.sizes.split(",")]
@@ -54,6 +59,13 @@ def main(argv=None):
     p = ld.default_params(n_disp=args.n_disp)
     srv = ld.Server(sizes, p, slots_per_size=args.slots, max_batch=args.max_batch, max_wait_us=args.max_wait_us,
                     n_streams=args.streams)
+    if args.learned > 0:
+        import os
+
+        import torch
+
+        theta = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "proposal_weights.npy"))
+        srv.set_learned(torch.from_numpy(theta.astype(np.float32)).cuda(), args.learned)
     size_of = [sizes[k % len(sizes)] for k in range(args.streams)]
     rng = np.random.default_rng(args.seed)
     results = []
@@ -117,8 +129,10 @@ def main(argv=None):
         "p99_ms": round(float(np.percentile(lat, 99)), 3) if len(lat) else None,
         "mean_batch": round(st["mean_batch"], 2), "batches": st["batches"], "refused_submits": refused,
         "sizes": per_size, "n_disp": args.n_disp, "max_batch": args.max_batch, "slots_per_size": args.slots,
-        "max_wait_us": args.max_wait_us,
+        "max_wait_us": args.max_wait_us, "form": f"learned top_k={args.learned}" if args.learned > 0 else "plain",
     }
+    if args.learned > 0:
+        line["fallback_frames"] = int(sum((int(r["lanes"]["flags"]) & ld.F_FALLBACK) != 0 for r in results))
     print(json.dumps(line), flush=True)
 
 

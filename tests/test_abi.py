@@ -78,3 +78,4 @@ def test_object_entry_points_reject_null_handles_without_device(ldmod):
     assert L.ld_net_param_count() == ldmod.NET_PARAMS
     for fn in (L.ld_net_status, L.ld_net_destroy, L.ld_stereo_destroy):
         fn(None)
+    assert L.ld_server_set_learned(None, None, 0) == ldmod.E_ARG

@@ -149,3 +149,73 @@ def test_concurrent_submitters(torch_cuda):
             assert r["lanes"].tobytes() == alone[tag].tobytes()
     finally:
         srv.close()
+
+
+def test_learned_form_matches_alone(torch_cuda):
+    """With the learned form switched on, every result is the frame's learned result alone (ld_detect_learned
+    on a one-frame handle, the package's trained weights, the same top_k), byte for byte; switching it off
+    again gives the plain results; switching while a frame waits in a slot is refused."""
+    import os
+
+    torch = torch_cuda
+    p = ld.default_params(n_disp=48)
+    w = np.load(os.path.join(os.path.dirname(ld.__file__), "proposal_weights.npy")).astype(np.float32)
+    theta = torch.from_numpy(w).cuda()
+    top_k = 16
+    frames = _frames()
+    dets = {wh: ld.Detector(wh[0], wh[1], 1, p) for wh in SIZES}
+    nets = {wh: ld.Net(det) for wh, det in dets.items()}
+    alone = []
+    for net in nets.values():
+        net.set_params(theta)
+    for sid, k, wh, d, i in frames:
+        out = nets[wh].detect(torch.from_numpy(d[None]).cuda(), torch.from_numpy(i[None]).cuda(), top_k=top_k)
+        torch.cuda.synchronize()
+        alone.append(ld.Detector.lanes(out)[0].copy())
+    for wh in SIZES:
+        nets[wh].close()
+        dets[wh].close()
+    plain = _alone(frames, p)
+
+    srv = ld.Server(SIZES, p, n_streams=N_STREAMS, slots_per_size=2, max_batch=4, max_wait_us=200)
+    try:
+        srv.set_learned(theta, top_k)
+        got = []
+        for tag, (sid, k, wh, d, i) in enumerate(frames):
+            while not srv.submit(sid, d, i, tag):
+                got.extend(srv.poll(timeout_ms=100))
+        srv.drain()
+        while len(r := srv.poll()):
+            got.extend(r)
+        assert sorted(int(r["tag"]) for r in got) == list(range(len(frames)))
+        for r in got:
+            tag = int(r["tag"])
+            assert r["lanes"].tobytes() == alone[tag].tobytes(), f"frame {tag} differs from its learned result alone"
+
+        srv.set_learned(None, 0)
+        got = []
+        for tag, (sid, k, wh, d, i) in enumerate(frames):
+            while not srv.submit(sid, d, i, tag):
+                got.extend(srv.poll(timeout_ms=100))
+        srv.drain()
+        while len(r := srv.poll()):
+            got.extend(r)
+        for r in got:
+            assert r["lanes"].tobytes() == plain[int(r["tag"])].tobytes()
+    finally:
+        srv.close()
+
+    # a frame waiting in a filling slot (max_batch 3, ten-second wait): the form cannot change
+    srv = ld.Server(SIZES, p, n_streams=N_STREAMS, slots_per_size=1, max_batch=3, max_wait_us=10_000_000)
+    try:
+        sid, k, wh, d, i = frames[0]
+        assert srv.submit(sid, d, i, 0)
+        with pytest.raises(ld.LDError) as e:
+            srv.set_learned(theta, top_k)
+        assert e.value.code == ld.E_STATE
+        with pytest.raises(ld.LDError) as e:
+            srv.set_learned(theta, ld.NET_TOPK_MAX + 1)
+        assert e.value.code == ld.E_ARG
+        srv.drain()
+    finally:
+        srv.close()
