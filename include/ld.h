@@ -143,6 +143,29 @@ int ld_tune(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int3
             ld_lanes *out_lanes, int32_t *chosen);
 
 /*
+ * Frames of several sizes in one call.  A group is n_frames frames of one size, [n_frames][h][w] contiguous
+ * in DEVICE memory (disp float32, img uint8), with its own DEVICE array of n_frames ld_lanes.  The groups
+ * together hold at most max_batch frames, each size within [16, max_w] x [16, max_h].  Every frame gets the
+ * result ld_detect gives it.  Group g works in the handle's workspace from frame F_g on, F_g being the
+ * frames of the groups before it, counted in frames of the largest size; the groups run on two streams
+ * forked from the handle's stream (larger groups first, each to the stream with fewer pixels so far), so
+ * that one group's per-frame serial kernels overlap another group's dense ones.  On a stream of the
+ * handle's own the call is captured as one CUDA graph and replayed when the same group list (pointers and
+ * sizes) comes back; on the legacy default stream, or inside the caller's capture, the groups are enqueued
+ * one after another.  ld_debug_get reports on no group of it.  The paper processes one frame at a time and
+ * has no counterpart.  Errors: LD_E_ARG (groups NULL, n_groups outside [1, LD_MAX_GROUPS], a group as
+ * ld_detect's arguments, more than max_batch frames in all), LD_E_CUDA.
+ */
+#define LD_MAX_GROUPS 16
+typedef struct ld_group {
+    const float *disp;      /* DEVICE [n_frames][h][w] */
+    const uint8_t *img;     /* DEVICE [n_frames][h][w] */
+    ld_lanes *out_lanes;    /* DEVICE [n_frames] */
+    int32_t w, h, n_frames, pad;
+} ld_group;
+int ld_detect_groups(ld_handle *h, const ld_group *groups, int32_t n_groups);
+
+/*
  * Same as ld_detect with HOST buffers: copies the inputs to device staging owned by the handle, runs the
  * path, copies the results to out_lanes (host, n_frames entries) and waits for the stream.  Page-locked
  * (pinned) inputs give the fastest copies.  Errors as ld_detect.

@@ -1,7 +1,9 @@
 // Host runtime behind include/ld.h: parameter checks, lookup tables, workspace, the launch sequence of
 // one ld_detect call (replayed from a captured CUDA graph when the same buffers come back; a call of at
 // least kSplitMin frames is captured as two concurrent half-batches, so one half's per-frame serial kernels
-// overlap the other half's dense kernels), the host-buffer path and the debug getters.
+// overlap the other half's dense kernels), calls over groups of frames of several sizes, the host-buffer
+// path and the debug getters.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -9,6 +11,8 @@
 #include <vector>
 
 #include "ld_internal.cuh"
+
+static_assert(sizeof(ld_group) == 40, "C-ABI group layout");
 
 namespace {
 
@@ -25,6 +29,12 @@ struct GraphSlot {
     const void *disp = nullptr, *img = nullptr;
     void *out = nullptr;
     int w = 0, h = 0, n = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+// a captured ld_detect_groups call, replayed when the same group list comes back
+struct GroupGraph {
+    std::vector<ld_group> groups;
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -48,6 +58,8 @@ struct ld_handle {
     bool have_last = false;
     GraphSlot graphs[kGraphSlots];
     int next_slot = 0;
+    GroupGraph group_graphs[kGraphSlots];
+    int next_group_slot = 0;
     cudaEvent_t ev[kLaunches + 1] = {};
     // two half-batches forked onto their own streams inside a captured call (joined before it ends)
     cudaStream_t sub[2] = {};
@@ -324,6 +336,73 @@ int enqueue_split(ld_handle *h, int w, int hh, int n, const float *disp, const u
             return cuda_fail(h, e, "join");
     }
     return LD_OK;
+}
+
+// The groups of one ld_detect_groups call.  Group g runs on the workspace seen from frame F_g on, counted
+// in frames of the handle's largest size: each per-frame array's stride for a smaller frame is at most
+// its stride for the largest one, so the group's frames stay inside [F_g, F_g + n_g) of those frames.
+// With `fork`, the groups go to the handle's two sub-streams (forked from and joined back to its stream),
+// largest first, each to the sub-stream with fewer pixels so far; otherwise they follow one another on the
+// handle's stream.
+int enqueue_groups(ld_handle *h, const ld_group *g, int ng, bool fork)
+{
+    const ld::KParams kmax = make_kparams(h, h->max_w, h->max_h, h->max_batch);
+    std::vector<int> first(ng), order(ng);
+    for (int i = 0, f = 0; i < ng; f += g[i].n_frames, ++i) {
+        first[i] = f;
+        order[i] = i;
+    }
+    auto px = [&](int i) { return (size_t)g[i].w * g[i].h * g[i].n_frames; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return px(a) > px(b); });
+    cudaError_t e = cudaSuccess;
+    if (fork) {
+        if ((e = cudaEventRecord(h->fork, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "fork");
+        for (int k = 0; k < 2; ++k)
+            if ((e = cudaStreamWaitEvent(h->sub[k], h->fork, 0)) != cudaSuccess)
+                return cuda_fail(h, e, "fork wait");
+    }
+    size_t load[2] = {0, 0};
+    for (int i : order) {
+        const int k = load[0] <= load[1] ? 0 : 1;
+        load[k] += px(i);
+        const ld::KParams kp = make_kparams(h, g[i].w, g[i].h, g[i].n_frames);
+        const int rc = enqueue_on(h, kp, work_from(h->w, kmax, first[i]), g[i].disp, g[i].img, g[i].out_lanes,
+                                  fork ? h->sub[k] : h->stream, false);
+        if (rc != LD_OK)
+            return rc;
+    }
+    if (fork)
+        for (int k = 0; k < 2; ++k)
+            if ((e = cudaEventRecord(h->join[k], h->sub[k])) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(h->stream, h->join[k], 0)) != cudaSuccess)
+                return cuda_fail(h, e, "join");
+    return LD_OK;
+}
+
+bool same_groups(const std::vector<ld_group> &a, const ld_group *b, int n)
+{
+    if ((int)a.size() != n)
+        return false;
+    for (int i = 0; i < n; ++i)
+        if (a[i].disp != b[i].disp || a[i].img != b[i].img || a[i].out_lanes != b[i].out_lanes || a[i].w != b[i].w ||
+            a[i].h != b[i].h || a[i].n_frames != b[i].n_frames)
+            return false;
+    return true;
+}
+
+void drop_graphs(ld_handle *h)
+{
+    for (GraphSlot &g : h->graphs)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g = GraphSlot();
+        }
+    for (GroupGraph &g : h->group_graphs)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g = GroupGraph();
+        }
 }
 
 void release_sync_objects(ld_handle *h)
@@ -648,6 +727,61 @@ int ld_detect(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, in
     return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
 }
 
+int ld_detect_groups(ld_handle *h, const ld_group *groups, int32_t n_groups)
+{
+    if (!h)
+        return LD_E_ARG;
+    if (!groups || n_groups < 1 || n_groups > LD_MAX_GROUPS)
+        return fail(h, LD_E_ARG, "groups is NULL or n_groups outside [1, LD_MAX_GROUPS]");
+    int64_t total = 0;
+    for (int i = 0; i < n_groups; ++i) {
+        const ld_group &g = groups[i];
+        const int rc = check_call(h, g.disp, g.img, g.w, g.h, g.n_frames, g.out_lanes);
+        if (rc != LD_OK)
+            return rc;
+        total += g.n_frames;
+    }
+    if (total > h->max_batch)
+        return fail(h, LD_E_ARG, "the groups hold more than max_batch frames");
+    h->have_last = false;   // the workspace now holds frames of several sizes
+    for (GroupGraph &g : h->group_graphs)
+        if (g.exec && same_groups(g.groups, groups, n_groups)) {
+            cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
+            return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
+        }
+    cudaStreamCaptureStatus st;
+    cudaError_t e = cudaStreamIsCapturing(h->stream, &st);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "stream query");
+    if (st != cudaStreamCaptureStatusNone || h->stream == nullptr)  // caller captures, or legacy stream
+        return enqueue_groups(h, groups, n_groups, false);
+    if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(h, e, "begin capture");
+    const int rc = enqueue_groups(h, groups, n_groups, true);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (rc != LD_OK) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "graph instantiate");
+    GroupGraph &g = h->group_graphs[h->next_group_slot];
+    h->next_group_slot = (h->next_group_slot + 1) % kGraphSlots;
+    if (g.exec)
+        cudaGraphExecDestroy(g.exec);
+    g.exec = exec;
+    g.groups.assign(groups, groups + n_groups);
+    e = cudaGraphLaunch(exec, h->stream);
+    return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
+}
+
 int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
                     ld_lanes *out_lanes, float *ms_out)
 {
@@ -709,11 +843,7 @@ int ld_tune(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int3
     }
     // launch shapes changed: drop the captured graphs
     cudaError_t e = cudaStreamSynchronize(h->stream);
-    for (GraphSlot &g : h->graphs)
-        if (g.exec) {
-            cudaGraphExecDestroy(g.exec);
-            g = GraphSlot();
-        }
+    drop_graphs(h);
     if (chosen)
         for (int t = 0; t < 3; ++t)
             chosen[t] = h->tile[t];
@@ -842,9 +972,7 @@ void ld_destroy(ld_handle *h)
     if (!h)
         return;
     cudaStreamSynchronize(h->stream);
-    for (GraphSlot &g : h->graphs)
-        if (g.exec)
-            cudaGraphExecDestroy(g.exec);
+    drop_graphs(h);
     release_sync_objects(h);
     cudaFree(h->ws);
     delete h;

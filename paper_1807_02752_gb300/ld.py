@@ -63,6 +63,14 @@ class ServerConfig(C.Structure):
                 ("max_batch", C.c_int32), ("max_wait_us", C.c_int32), ("n_streams", C.c_int32)]
 
 
+class Group(C.Structure):
+    _fields_ = [("disp", C.c_void_p), ("img", C.c_void_p), ("out_lanes", C.c_void_p), ("w", C.c_int32),
+                ("h", C.c_int32), ("n_frames", C.c_int32), ("pad", C.c_int32)]
+
+
+assert C.sizeof(Group) == 40
+
+
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64), ("batches", C.c_int64),
                 ("mean_batch", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
@@ -112,6 +120,8 @@ def load():
     L.ld_destroy.restype = None
     L.ld_road_path_static.argtypes = [P, p, i32, i32, i32, p, p]
     L.ld_road_path_static.restype = C.c_int
+    L.ld_detect_groups.argtypes = [p, p, i32]
+    L.ld_detect_groups.restype = C.c_int
     L.ld_tune.argtypes = [p, p, p, i32, i32, i32, p, p]
     L.ld_tune.restype = C.c_int
     L.ld_server_create.argtypes = [P, C.POINTER(ServerConfig), C.POINTER(p)]
@@ -175,7 +185,7 @@ def load():
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
             "ld_debug_get", "ld_debug_size", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
-            "ld_destroy", "ld_road_path_static", "ld_tune", "ld_server_create", "ld_server_submit", "ld_server_poll",
+            "ld_destroy", "ld_road_path_static", "ld_tune", "ld_detect_groups", "ld_server_create", "ld_server_submit", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_server_set_learned", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
             "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
@@ -274,6 +284,19 @@ class Detector:
     @staticmethod
     def lanes(out) -> np.ndarray:
         return np.frombuffer(out.cpu().numpy().tobytes(), dtype=LANES_DTYPE)
+
+    def detect_groups(self, groups, outs=None):
+        """Frames of several sizes in one call: groups is a list of (disp, img) device tensors [n,H,W], one
+        size per group.  Returns the device result buffers, one per group (see lanes())."""
+        arr = (Group * max(1, len(groups)))()
+        outs = [self.alloc_lanes(d.shape[0]) for d, _ in groups] if outs is None else outs
+        for k, ((d, i), o) in enumerate(zip(groups, outs)):
+            assert d.is_cuda and i.is_cuda and d.dtype.itemsize == 4 and i.dtype.itemsize == 1
+            assert d.is_contiguous() and i.is_contiguous() and d.shape == i.shape
+            n, H, W = d.shape
+            arr[k] = Group(d.data_ptr(), i.data_ptr(), o.data_ptr(), W, H, n, 0)
+        self._check(self.L.ld_detect_groups(self.h, arr, len(groups)))
+        return outs
 
     def detect_host(self, disp: np.ndarray, img: np.ndarray) -> np.ndarray:
         """Host buffers in, host results out (copies and kernels on the handle's stream, synchronous)."""

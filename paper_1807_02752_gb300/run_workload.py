@@ -4,17 +4,61 @@ that a profiler attached to the process sees every kernel of every call as a sep
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4 learned 64
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 3 stereo
+    python -m paper_1807_02752_gb300.run_workload mixed 20
 
 Each call launches the nine kernels of the path once, in order, on the handle's stream, and times each
 with CUDA events; the per-kernel times of the last call are printed.  With `learned [top_k]` each call is
 the learned form instead (the network with the package's trained weights ranks the starts; exact
 energies for the top_k coarse starts), timed as a whole.  With `stereo` each call is the stereo stage on
 the workload's stereo pairs (search range propagation for both maps, then the consistency check).
+`mixed` times frames of three camera sizes (16 x 1242x375, 8 x 1280x720, 8 x 1920x1080, D = 256) as one
+ld_detect_groups call and as three ld_detect calls in a row on the same stream (captured graphs,
+replayed; CUDA events; median of the calls).
 """
 from __future__ import annotations
 
 import os
 import sys
+
+
+def mixed(calls: int):
+    import numpy as np
+    import torch
+
+    from . import ld, scenes
+
+    hd = scenes.HD_1920x1080
+    spec = ((scenes.with_size(scenes.BATCH64_1242x375, n_disp=256), 16),
+            (scenes.with_size(hd, width=1280, height=720, n_disp=256), 8), (scenes.with_size(hd, n_disp=256), 8))
+    groups = []
+    for g, (cfg, n) in enumerate(spec):
+        fr = [scenes.make_frame(cfg, 900 + 10 * g + k)[:2] for k in range(4)]   # four scenes, repeated
+        groups.append((torch.from_numpy(np.stack([fr[k % 4][0] for k in range(n)])).cuda(),
+                       torch.from_numpy(np.stack([fr[k % 4][1] for k in range(n)])).cuda()))
+    s = torch.cuda.Stream()
+    det = ld.Detector(1920, 1080, sum(n for _, n in spec), ld.default_params(n_disp=256), stream=s)
+    outs = [det.alloc_lanes(d.shape[0]) for d, _ in groups]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                fn()
+            ms = []
+            for _ in range(calls):
+                e0.record(s)
+                fn()
+                e1.record(s)
+                s.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    one = timed(lambda: det.detect_groups(groups, outs))
+    three = timed(lambda: [det.detect(d, i, o) for (d, i), o in zip(groups, outs)])
+    n = sum(n for _, n in spec)
+    print({"frames": n, "groups_ms": round(one, 4), "groups_fps": round(n / one * 1e3, 1),
+           "three_calls_ms": round(three, 4), "three_calls_fps": round(n / three * 1e3, 1)})
+    det.close()
 
 
 def main(argv=None):
@@ -26,6 +70,8 @@ def main(argv=None):
     argv = sys.argv[1:] if argv is None else argv
     name = argv[0] if argv else "batch64_1242x375"
     calls = int(argv[1]) if len(argv) > 1 else 4
+    if name == "mixed":
+        return mixed(calls)
     learned = len(argv) > 2 and argv[2] == "learned"
     stereo = len(argv) > 2 and argv[2] == "stereo"
     top_k = int(argv[3]) if len(argv) > 3 else 64

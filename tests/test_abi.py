@@ -79,3 +79,5 @@ def test_object_entry_points_reject_null_handles_without_device(ldmod):
     for fn in (L.ld_net_status, L.ld_net_destroy, L.ld_stereo_destroy):
         fn(None)
     assert L.ld_server_set_learned(None, None, 0) == ldmod.E_ARG
+    assert L.ld_detect_groups(None, None, 1) == ldmod.E_ARG
+    assert ctypes.sizeof(ldmod.Group) == 40

@@ -1,0 +1,126 @@
+"""Frames of several sizes in one call (ld_detect_groups): every group's results must be the ones
+ld_detect gives its frames, byte for byte, on a stream of the handle's own (one captured graph, the groups
+on two forked streams, then replays) and on the legacy default stream (groups one after another)."""
+import numpy as np
+import pytest
+
+from paper_1807_02752_gb300 import ld, scenes
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [((320, 120), 3), ((256, 96), 2), ((400, 150), 1), ((320, 120), 2)]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_02752_gb300 import build
+    build.build()
+    return torch
+
+
+def _groups(torch, sizes, n_disp, first=300):
+    out = []
+    for g, ((w, h), n) in enumerate(sizes):
+        cfg = scenes.with_size(scenes.SMALL_320x120, width=w, height=h, n_disp=n_disp)
+        fr = [scenes.make_frame(cfg, first + 10 * g + k)[:2] for k in range(n)]
+        d = torch.from_numpy(np.stack([f[0] for f in fr])).cuda()
+        i = torch.from_numpy(np.stack([f[1] for f in fr])).cuda()
+        out.append((d, i))
+    return out
+
+
+def _alone(torch, groups, p):
+    res = []
+    for d, i in groups:
+        n, H, W = d.shape
+        det = ld.Detector(W, H, n, p)
+        out = det.detect(d, i)
+        torch.cuda.synchronize()
+        res.append(ld.Detector.lanes(out).tobytes())
+        det.close()
+    return res
+
+
+@pytest.mark.parametrize("own_stream", [True, False])
+def test_groups_match_ld_detect(torch_cuda, own_stream):
+    torch = torch_cuda
+    p = ld.default_params(n_disp=48)
+    groups = _groups(torch, SIZES, 48)
+    want = _alone(torch, groups, p)
+    stream = torch.cuda.Stream() if own_stream else None
+    det = ld.Detector(400, 150, sum(n for _, n in SIZES), p, stream=stream)
+    try:
+        with torch.cuda.stream(stream or torch.cuda.current_stream()):
+            outs = [det.alloc_lanes(d.shape[0]) for d, _ in groups]
+            for rep in range(3):            # capture, then replays of the same list
+                for o in outs:
+                    o.zero_()
+                det.detect_groups(groups, outs)
+                torch.cuda.synchronize()
+                got = [ld.Detector.lanes(o).tobytes() for o in outs]
+                assert got == want, f"call {rep}"
+            # another list (reversed order, so other workspace offsets and stream choices): a new graph
+            rev, routs = groups[::-1], outs[::-1]
+            for o in routs:
+                o.zero_()
+            det.detect_groups(rev, routs)
+            torch.cuda.synchronize()
+            assert [ld.Detector.lanes(o).tobytes() for o in outs] == want
+            # a plain single-size call on the same handle afterwards is unaffected
+            d, i = groups[0]
+            o = det.detect(d, i)
+            torch.cuda.synchronize()
+            assert ld.Detector.lanes(o).tobytes() == want[0]
+    finally:
+        det.close()
+
+
+def test_groups_full_sizes(torch_cuda):
+    """Three camera sizes at D = 256 (1242x375, 1280x720, 1920x1080) in one captured call."""
+    torch = torch_cuda
+    p = ld.default_params(n_disp=256)
+    groups = []
+    for g, (cfg, n) in enumerate(((scenes.with_size(scenes.BATCH64_1242x375, n_disp=256), 4),
+                                  (scenes.with_size(scenes.HD_1920x1080, width=1280, height=720, n_disp=256), 2),
+                                  (scenes.with_size(scenes.HD_1920x1080, n_disp=256), 2))):
+        fr = [scenes.make_frame(cfg, 700 + 10 * g + k)[:2] for k in range(n)]
+        groups.append((torch.from_numpy(np.stack([f[0] for f in fr])).cuda(),
+                       torch.from_numpy(np.stack([f[1] for f in fr])).cuda()))
+    want = _alone(torch, groups, p)
+    stream = torch.cuda.Stream()
+    det = ld.Detector(1920, 1080, 8, p, stream=stream)
+    try:
+        with torch.cuda.stream(stream):
+            outs = det.detect_groups(groups)
+            outs = det.detect_groups(groups, outs)
+            torch.cuda.synchronize()
+            assert [ld.Detector.lanes(o).tobytes() for o in outs] == want
+    finally:
+        det.close()
+
+
+def test_group_argument_errors(torch_cuda):
+    torch = torch_cuda
+    p = ld.default_params(n_disp=48)
+    det = ld.Detector(320, 120, 4, p)
+    try:
+        d = torch.zeros((3, 120, 320), dtype=torch.float32, device="cuda")
+        i = torch.zeros((3, 120, 320), dtype=torch.uint8, device="cuda")
+        d2 = torch.zeros((2, 96, 256), dtype=torch.float32, device="cuda")
+        i2 = torch.zeros((2, 96, 256), dtype=torch.uint8, device="cuda")
+        big = torch.zeros((1, 150, 400), dtype=torch.float32, device="cuda")
+        bigi = torch.zeros((1, 150, 400), dtype=torch.uint8, device="cuda")
+        for groups in ([(d, i), (d2, i2)],          # 5 frames > max_batch 4
+                       [(big, bigi)],               # larger than the handle's frames
+                       []):                         # no group
+            with pytest.raises(ld.LDError) as e:
+                det.detect_groups(groups)
+            assert e.value.code == ld.E_ARG
+        outs = det.detect_groups([(d[:2], i[:2]), (d2, i2)])   # exactly max_batch: accepted
+        torch.cuda.synchronize()
+        assert len(outs) == 2
+    finally:
+        det.close()
