@@ -3,15 +3,20 @@
 // A pixel counts when its disparity l is finite and > 0 (0 marks pixels invalidated by the left-right
 // check, Eq. 10); its bin is floor(l + 0.5) in float32 and bins >= D are dropped.
 //
-// One CTA covers kRows consecutive rows of one frame (16 unless ld_tune chose another count).  Those rows are one contiguous range of memory, so
-// the CTA streams it as 16-byte loads of the aligned chunks inside it (several in flight per thread) plus
-// single loads of its head and tail; each warp streams one contiguous span.  Counts go to a shared-memory
+// One CTA covers kRows consecutive rows of one frame (16 unless ld_tune chose another count).  Those
+// rows are one contiguous range of memory, so the CTA streams it as 16-byte loads of the aligned chunks
+// inside it (several in flight per thread) plus single loads of its head and tail; each warp streams one
+// contiguous span.  Counts go to a shared-memory
 // histogram per row.  Disparity is locally smooth (a road row holds one or two bins, an obstacle one), so
 // each thread counts a run of equal (row, bin) keys in registers and adds the run with one shared-memory
 // atomic when the key changes: fewer atomics than pixels, and few 32-way conflicts on the dominant bin.
 // The run update is branch-free (the flush is a predicated add; invalid pixels keep the run going), so
-// warps do not diverge on the data.  The histogram is written transposed, [D][H] per frame, so that each step of the road DP (Eq. 12)
-// reads one contiguous row.
+// warps do not diverge on the data.  The bin takes two float adds instead of a float-to-integer
+// conversion: for 0 <= x < 2^23, x + 2^23 rounded toward -infinity is 2^23 + floor(x) exactly (the
+// float spacing there is 1), so its bit pattern minus that of 2^23 is floor(x); any other x leaves a
+// difference >= D (as unsigned), which the bin test rejects.  The shared histogram rows are D + 1 words
+// apart, so the transposed write-out ([D][H] per frame, so that each step of the road DP (Eq. 12) reads
+// one contiguous row) reads it without bank conflicts.
 #include "ld_internal.cuh"
 
 namespace ld {
@@ -20,6 +25,7 @@ namespace {
 constexpr int kRowsDefault = 16;  // rows per CTA unless tuned
 constexpr int kThreads = 256;
 constexpr int kUnroll = 4;  // 16-byte loads in flight per thread
+constexpr uint32_t kTwo23Bits = 0x4B000000u;  // bit pattern of 2^23 in float32
 
 // Shared-memory add of v at address a when p holds, as one predicated instruction (no branch).
 __device__ __forceinline__ void red_add_if(bool p, uint32_t a, int v)
@@ -31,13 +37,13 @@ __device__ __forceinline__ void red_add_if(bool p, uint32_t a, int v)
 __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *__restrict__ myT,
                                                     const float *__restrict__ disp, int kRows)
 {
-    extern __shared__ int32_t hist[];  // [kRows][D]
-    const int W = kp.W, H = kp.H, D = kp.D;
+    extern __shared__ int32_t hist[];  // [kRows][D + 1]
+    const int W = kp.W, H = kp.H, D = kp.D, Dp = D + 1;
     const int f = blockIdx.y;
     const int r0 = blockIdx.x * kRows;
     const int nr = min(kRows, H - r0);
     const int tid = threadIdx.x;
-    for (int i = tid; i < kRows * D; i += kThreads)
+    for (int i = tid; i < kRows * Dp; i += kThreads)
         hist[i] = 0;
     __syncthreads();
 
@@ -55,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
         const int off = tid < head ? tid : tail0 + (tid - head);
         const int b = bin_of(__ldg(src + off));
         if (b >= 0)
-            atomicAdd(&hist[(off / W) * D + b], 1);
+            atomicAdd(&hist[(off / W) * Dp + b], 1);
     }
     // each warp takes one contiguous span of the 16-byte chunks (about one row), so a lane's successive
     // loads (128 pixels apart) mostly stay in one row and its run key changes only with the bin
@@ -80,12 +86,12 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             const float l[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
-            const int rb = row * D, rw = W - col;  // pixels e >= rw of this chunk are on the next row
+            const int rb = row * Dp, rw = W - col;  // pixels e >= rw of this chunk are on the next row
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int b = __float2int_rd(__fadd_rn(l[e], 0.5f));
-                const bool ok = l[e] > 0.0f && b < D;
-                const int key = ok ? (e < rw ? rb : rb + D) + b : run_key;
+                const uint32_t b = __float_as_uint(__fadd_rd(__fadd_rn(l[e], 0.5f), 8388608.0f)) - kTwo23Bits;
+                const bool ok = l[e] > 0.0f && b < (uint32_t)D;
+                const int key = ok ? (e < rw ? rb : rb + Dp) + (int)b : run_key;
                 const bool nk = key != run_key;
                 red_add_if(nk, hbase + 4u * (uint32_t)run_key, run_cnt);
                 run_cnt = (nk ? 0 : run_cnt) + (int)ok;
@@ -100,19 +106,21 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
     }
     red_add_if(run_cnt != 0, hbase + 4u * (uint32_t)run_key, run_cnt);
     __syncthreads();
+    // thread t writes row r = t mod nr of bins d = t / nr, t / nr + step, ... (one division per thread)
     int32_t *dst = myT + (size_t)f * D * H;
-    for (int i = tid; i < D * nr; i += kThreads) {
-        const int d = i / nr, r = i - d * nr;
-        dst[(size_t)d * H + r0 + r] = hist[r * D + d];
-    }
+    const int step = kThreads / nr, r = tid % nr;
+    if (tid < step * nr)
+        for (int d = tid / nr; d < D; d += step)
+            dst[(size_t)d * H + r0 + r] = hist[r * Dp + d];
 }
 }  // namespace
 
-// Rows per CTA: the tuned value when set, kept within 48 KB of histogram shared memory.
+// Rows per CTA: the tuned value when set, at most one per thread (the write-out gives each row at least
+// one thread), kept within 48 KB of histogram shared memory.
 int vdisp_rows(const KParams &kp)
 {
-    int r = kp.tile_vdisp > 0 ? kp.tile_vdisp : kRowsDefault;
-    while (r > 1 && sizeof(int32_t) * (size_t)r * kp.D > 48 * 1024)
+    int r = kp.tile_vdisp > 0 ? min(kp.tile_vdisp, kThreads) : kRowsDefault;
+    while (r > 1 && sizeof(int32_t) * (size_t)r * (kp.D + 1) > 48 * 1024)
         r >>= 1;
     return r;
 }
@@ -121,7 +129,7 @@ cudaError_t launch_vdisp(const KParams &kp, const Work &w, const float *disp, cu
 {
     const int kRows = vdisp_rows(kp);
     dim3 grid((kp.H + kRows - 1) / kRows, kp.n_frames);
-    const size_t smem = sizeof(int32_t) * kRows * kp.D;
+    const size_t smem = sizeof(int32_t) * kRows * (kp.D + 1);
     k_vdisp<<<grid, kThreads, smem, s>>>(kp, w.myT, disp, kRows);
     return cudaGetLastError();
 }
