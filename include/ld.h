@@ -187,8 +187,8 @@ enum ld_stage {
 };
 /*
  * Copy stage `stage` of frame `frame` (host buffer host_dst of `bytes` bytes, which must equal the
- * stage's size) after synchronising the handle's stream.  Errors: LD_E_ARG, LD_E_STATE (no detect yet),
- * LD_E_CUDA.
+ * stage's size) after synchronising the handle's stream.  Errors: LD_E_ARG, LD_E_STATE (no single-size
+ * detection yet, or ld_detect_groups ran after the last one), LD_E_CUDA.
  */
 int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, size_t bytes);
 

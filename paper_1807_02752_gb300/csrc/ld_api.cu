@@ -895,7 +895,7 @@ int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, siz
     if (!h)
         return LD_E_ARG;
     if (!h->have_last)
-        return fail(h, LD_E_STATE, "no detect call yet");
+        return fail(h, LD_E_STATE, "no single-size detect call to report on (none yet, or ld_detect_groups since)");
     if (frame < 0 || frame >= h->last_n || !host_dst)
         return fail(h, LD_E_ARG, "frame out of range or null destination");
     const size_t want = ld_debug_size(h, stage);

@@ -69,6 +69,10 @@ def test_groups_match_ld_detect(torch_cuda, own_stream):
             det.detect_groups(rev, routs)
             torch.cuda.synchronize()
             assert [ld.Detector.lanes(o).tobytes() for o in outs] == want
+            # the workspace held several sizes: ld_debug_get refuses until the next single-size call
+            with pytest.raises(ld.LDError) as e:
+                det.debug(0, ld.STAGE_VDISP, 320, 120)
+            assert e.value.code == ld.E_STATE
             # a plain single-size call on the same handle afterwards is unaffected
             d, i = groups[0]
             o = det.detect(d, i)
