@@ -259,6 +259,55 @@ def measure_stereo(args, pairs_async, det, stream, n):
             "rho": 3, "tau": 1, "tr_lrc": 3}
 
 
+def measure_single(args, stream):
+    """Latency of one frame of the single-frame 1242x375 workload (5 % outlier disparities) on a one-frame
+    handle: the captured graph timed with CUDA events on the handle's stream, L2 flushed by a 160 MiB write
+    before each call, and end to end through ld_detect_host from pinned host buffers (host clock: the
+    copies, the kernels, the result copy and the wait)."""
+    import torch
+
+    from paper_1807_02752_gb300 import ld, scenes
+
+    if args.no_single:
+        return None
+    cfg, _ = scenes.WORKLOADS["single_1242x375"]
+    d, i, _ = scenes.make_frame(cfg, 0)
+    W, H = cfg.width, cfg.height
+    reps = max(20, min(args.steps, 200))
+    with torch.cuda.stream(stream):
+        det = ld.Detector(W, H, 1, ld.default_params(n_disp=cfg.n_disp), stream=stream)
+        dd, ii = torch.from_numpy(d[None]).cuda(), torch.from_numpy(i[None]).cuda()
+        out = det.alloc_lanes(1)
+        flush = torch.empty(40 * 2 ** 20, dtype=torch.float32, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(5):
+            det.detect(dd, ii, out)
+        dev = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a.record(stream)
+            det.detect(dd, ii, out)
+            b.record(stream)
+            stream.synchronize()
+            dev.append(a.elapsed_time(b))
+        hd, hi = torch.from_numpy(d[None]).pin_memory(), torch.from_numpy(i[None]).pin_memory()
+        res = np.zeros(1, ld.LANES_DTYPE)
+        for _ in range(5):
+            det.detect_host_ptr(hd.data_ptr(), hi.data_ptr(), W, H, 1, res)
+        host = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            stream.synchronize()
+            t = time.perf_counter()
+            det.detect_host_ptr(hd.data_ptr(), hi.data_ptr(), W, H, 1, res)
+            host.append((time.perf_counter() - t) * 1e3)
+        det.close()
+    pct = lambda x, q: round(float(np.percentile(x, q)), 4)
+    return {"workload": "single_1242x375 (one frame, 5 % outlier disparities)", "calls": reps,
+            "p50_ms": pct(dev, 50), "p99_ms": pct(dev, 99), "e2e_p50_ms": pct(host, 50), "e2e_p99_ms": pct(host, 99),
+            "l2": "flushed before each call (160 MiB write)"}
+
+
 def measure_learned(args, dets, streams, disp, img, n, world):
     """The learned form (network-ranked starts, exact energies of the top-k) on the same handles, streams,
     inputs and step count as the plain form; agreement of its lanes with the plain lanes on both input
@@ -462,6 +511,7 @@ def run_ours(args):
 
     learned = measure_learned(args, dets, streams, disp, img, n, world)
     stereo = measure_stereo(args, pairs_async, dets[0], streams[0], n) if rank == 0 else None
+    single = measure_single(args, streams[0]) if rank == 0 else None
     if spool:
         spool.close()
 
@@ -522,6 +572,7 @@ def run_ours(args):
             "gpu_launches": int(ld.load().ld_launches_per_detect() * args.steps),
             "learned": None if learned is None else dict(learned, vs_plain=round(learned["value"] / value, 4)),
             "stereo": stereo,
+            "single_frame": single,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -580,6 +631,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in tile shapes")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal form")
     ap.add_argument("--no-stereo", action="store_true", help="skip the stereo stage measurement")
+    ap.add_argument("--no-single", action="store_true", help="skip the single-frame latency measurement")
     ap.add_argument("--top-k", type=int, default=96, help="coarse starts the learned form evaluates per frame")
     ap.add_argument("--streams", type=int, default=4, help="library handles on separate streams, batches rotate over them")
     args = ap.parse_args()
