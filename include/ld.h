@@ -36,7 +36,7 @@ extern "C" {
 #define LD_OK 0
 #define LD_E_ARG (-1)      /* bad argument (null pointer, size out of range, invalid parameter) */
 #define LD_E_CUDA (-2)     /* a CUDA runtime call failed; the message names it */
-#define LD_E_NOMEM (-3)    /* device or pinned-host allocation failed in ld_create */
+#define LD_E_NOMEM (-3)    /* device or pinned-host allocation failed (the *_create calls, ld_server_set_learned) */
 #define LD_E_STATE (-4)    /* call not valid in the handle's current state (e.g. no detect yet) */
 #define LD_E_BUSY (-5)     /* serving: no slot of the frame's size class can take it now (admission) */
 #define LD_E_TIMEOUT (-6)  /* a bounded device-side wait ran out; the kernel stopped and released what it held */
