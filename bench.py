@@ -548,7 +548,8 @@ def run_ours(args):
         pool.close()
         cpu = {"value": round(len(frames) / wall, 3), "unit": UNIT, "cores": min(16, host_cores()), "kind": "oracle",
                "sample": f"{len(frames)} frames of the {WORKLOAD} workload, one frame per process "
-                         f"({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)"}
+                         f"({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)",
+               "single_thread_ms_per_frame": round(1e3 * cpu_s / len(frames), 2)}
 
     if rank == 0:
         frames_total = world * n * args.steps
@@ -615,7 +616,8 @@ def run_reference(args):
                    "height": cfg.height, "n_disp": cfg.n_disp, "parallelism": "host processes"},
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} frames of the {WORKLOAD} workload per step, one frame per process "
-                                   f"({cpu_total:.1f} s of CPU work)"},
+                                   f"({cpu_total:.1f} s of CPU work)",
+                         "single_thread_ms_per_frame": round(1e3 * cpu_total / (args.steps * per_step), 2)},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
