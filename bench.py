@@ -44,17 +44,24 @@ def load_peaks():
 # ----------------------------------------------------------------------------------------------------
 # oracle arm (host cores)
 # ----------------------------------------------------------------------------------------------------
-def _oracle_worker(args):
-    cfg_name, frame, pdict = args
+def _oracle_chunk(args):
+    """Render a chunk of frames, then run the oracle on each of them.  Returns the start and the end of the
+    oracle section (time.perf_counter: the system-wide monotonic clock, comparable across processes) and
+    the summed per-frame oracle time; rendering stays outside both."""
+    cfg_name, frames, pdict = args
     import oracle
     from paper_1807_02752_gb300 import scenes
 
     cfg, _ = scenes.WORKLOADS[cfg_name]
-    d, im, _ = scenes.make_frame(cfg, frame)
+    inputs = [scenes.make_frame(cfg, f)[:2] for f in frames]
     p = oracle.default_params(**pdict)
-    t0 = time.perf_counter()
-    r = oracle.detect(d, im, p, dumps=False)
-    return time.perf_counter() - t0, r["n_lanes"]
+    t_start = time.perf_counter()
+    cpu = 0.0
+    for d, im in inputs:
+        t0 = time.perf_counter()
+        oracle.detect(d, im, p, dumps=False)
+        cpu += time.perf_counter() - t0
+    return t_start, time.perf_counter(), cpu
 
 
 def _stereo_worker(k):
@@ -74,11 +81,13 @@ def oracle_pool(n_workers):
     return ctx.Pool(n_workers)
 
 
-def run_oracle_frames(pool, frames, pdict):
-    t0 = time.perf_counter()
-    res = pool.map(_oracle_worker, [(WORKLOAD, f, pdict) for f in frames], chunksize=1)
-    wall = time.perf_counter() - t0
-    return wall, sum(r[0] for r in res)
+def run_oracle_frames(pool, frames, pdict, n_chunks):
+    """The oracle over `frames` split into n_chunks tasks (one per process of the pool).  Returns the wall
+    time of the oracle sections (latest end - earliest start; each task renders its frames before its
+    section) and the summed single-thread time per frame."""
+    chunks = [frames[k::n_chunks] for k in range(n_chunks) if frames[k::n_chunks]]
+    res = pool.map(_oracle_chunk, [(WORKLOAD, c, pdict) for c in chunks], chunksize=1)
+    return max(r[1] for r in res) - min(r[0] for r in res), sum(r[2] for r in res)
 
 
 def host_cores():
@@ -542,13 +551,14 @@ def run_ours(args):
     cpu = None
     if pool is not None:
         # a bounded sample: 16 frames per process (about 20 s of CPU work on 16 cores)
-        frames = list(range(base, base + 16 * min(16, host_cores())))
-        run_oracle_frames(pool, frames[:2], p.as_dict())  # warm the workers
-        wall, cpu_s = run_oracle_frames(pool, frames, p.as_dict())
+        workers = min(16, host_cores())
+        frames = list(range(base, base + 16 * workers))
+        run_oracle_frames(pool, frames[:workers], p.as_dict(), workers)  # warm the workers
+        wall, cpu_s = run_oracle_frames(pool, frames, p.as_dict(), workers)
         pool.close()
         cpu = {"value": round(len(frames) / wall, 3), "unit": UNIT, "cores": min(16, host_cores()), "kind": "oracle",
-               "sample": f"{len(frames)} frames of the {WORKLOAD} workload, one frame per process "
-                         f"({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)",
+               "sample": f"{len(frames)} frames of the {WORKLOAD} workload, {len(frames) // workers} per process, "
+                         f"rendered before the timed section ({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)",
                "single_thread_ms_per_frame": round(1e3 * cpu_s / len(frames), 2)}
 
     if rank == 0:
@@ -598,13 +608,12 @@ def run_reference(args):
     pdict = oracle.default_params(n_disp=cfg.n_disp).as_dict()
     per_step = cores  # one frame per process per step
     for s in range(max(args.warmup, 1)):
-        run_oracle_frames(pool, [(s * per_step + k) % n for k in range(per_step)], pdict)
-    t0 = time.perf_counter()
-    cpu_total = 0.0
+        run_oracle_frames(pool, [(s * per_step + k) % n for k in range(per_step)], pdict, cores)
+    wall = cpu_total = 0.0   # each step's oracle sections; every process renders its frame before its section
     for s in range(args.steps):
-        wall, cpu_s = run_oracle_frames(pool, [(s * per_step + k) % n for k in range(per_step)], pdict)
+        w, cpu_s = run_oracle_frames(pool, [(s * per_step + k) % n for k in range(per_step)], pdict, cores)
+        wall += w
         cpu_total += cpu_s
-    wall = time.perf_counter() - t0
     pool.close()
     value = args.steps * per_step / wall
     line = {
@@ -615,8 +624,8 @@ def run_reference(args):
         "config": {"workload": f"{WORKLOAD} plain form", "frames_per_step": per_step, "width": cfg.width,
                    "height": cfg.height, "n_disp": cfg.n_disp, "parallelism": "host processes"},
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} frames of the {WORKLOAD} workload per step, one frame per process "
-                                   f"({cpu_total:.1f} s of CPU work)",
+                         "sample": f"{per_step} frames of the {WORKLOAD} workload per step, one frame per process, "
+                                   f"rendered before the timed section ({cpu_total:.1f} s of CPU work)",
                          "single_thread_ms_per_frame": round(1e3 * cpu_total / (args.steps * per_step), 2)},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
