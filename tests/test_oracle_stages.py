@@ -12,6 +12,8 @@ import numpy as np
 import pytest
 from scipy import ndimage
 
+from paper_1807_02752_gb300 import scenes
+
 
 # ---------------------------------------------------------------------------------------------- a1
 def test_vdisparity_counts_valid_pixels(oracle_mod):
@@ -156,6 +158,32 @@ def test_sobel_vertical_step(oracle_mod):
     gx, gy = oracle_mod.sobel(img)
     assert (gx[1:-1, 5] == 4 * 77).all() and (gx[1:-1, 6] == 4 * 77).all()
     assert (gy == 0).all() and (gx[1:-1, :5] == 0).all()
+
+
+def test_edge_map_is_road_mask_and_threshold_on_sobel(oracle_mod):
+    """The edge map of a whole detection, rebuilt independently: the road mask (finite l > 0,
+    |l - f(v)| <= varpi in float32, interior pixels of rows >= v_top) and G_x^2 + G_y^2 > thr^2 with G from
+    scipy's correlation of the bilateral output.  The edge count falls as the threshold rises."""
+    cfg = scenes.SMALL_320x120
+    d, im, _ = scenes.make_frame(cfg, 3)
+    kx = np.array([[-1, 0, 1], [-2, 0, 2], [-1, 0, 1]])
+    counts = []
+    for thr in (50, 100, 150):
+        p = oracle_mod.default_params(n_disp=cfg.n_disp, edge_thresh=thr)
+        r = oracle_mod.detect(d, im, p)
+        I = r["Ibf"].astype(np.int64)
+        gx = ndimage.correlate(I, kx, mode="constant")
+        gy = ndimage.correlate(I, kx.T, mode="constant")
+        H, W = I.shape
+        v, u = np.arange(H)[:, None], np.arange(W)[None, :]
+        with np.errstate(invalid="ignore"):
+            road = (d > 0) & (np.abs(d - r["F"][:, None]) <= np.float32(p.varpi))
+        road &= (v >= r["v_top"]) & (v >= 1) & (v <= H - 2) & (u >= 1) & (u <= W - 2)
+        want = road & (gx * gx + gy * gy > thr * thr)
+        assert (r["edge"].astype(bool) == want).all()
+        assert (r["Gx"][want] == gx[want]).all() and (r["Gy"][want] == gy[want]).all()
+        counts.append(int(want.sum()))
+    assert counts[0] > counts[1] > counts[2] > 0
 
 
 # ---------------------------------------------------------------------------------------------- b4
