@@ -29,7 +29,10 @@ UNIT = "frames/s"
 WORKLOAD = "batch64_1242x375"
 STEREO_BASE = 5_000_000   # frame indices of the stereo pairs
 DTYPE = "u8/i32 (f32 decisions, f64 solves)"
-INT_OPS_PER_TAP = 4  # bilateral tap: Q15 weight product with rounding, shift, w*I accumulate, w accumulate
+# Integer operations of one bilateral tap as the method defines it (Eq. 15-16 in Q15 integers): the weight
+# product ws * wr, its rounding add and shift, the accumulation of w * I (one multiply-add) and of w.  The
+# kernel does the same work in fewer instructions (one table load replaces the weight's three operations).
+INT_OPS_PER_TAP = 5
 
 
 def load_peaks():
@@ -44,10 +47,20 @@ def load_peaks():
 # ----------------------------------------------------------------------------------------------------
 # oracle arm (host cores)
 # ----------------------------------------------------------------------------------------------------
+_BARRIER = None
+
+
+def _init_worker(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
 def _oracle_chunk(args):
-    """Render a chunk of frames, then run the oracle on each of them.  Returns the start and the end of the
-    oracle section (time.perf_counter: the system-wide monotonic clock, comparable across processes) and
-    the summed per-frame oracle time; rendering stays outside both."""
+    """Render a chunk of frames, wait until every process of the pool has rendered its own chunk, then run
+    the oracle on each frame.  Returns the process id, the start and the end of the oracle section
+    (time.perf_counter: the system-wide monotonic clock, comparable across processes) and the summed
+    per-frame oracle time; rendering stays outside all of them.  The barrier holds each process on its one
+    chunk, so no process renders a second chunk while others are timed."""
     cfg_name, frames, pdict = args
     import oracle
     from paper_1807_02752_gb300 import scenes
@@ -55,13 +68,15 @@ def _oracle_chunk(args):
     cfg, _ = scenes.WORKLOADS[cfg_name]
     inputs = [scenes.make_frame(cfg, f)[:2] for f in frames]
     p = oracle.default_params(**pdict)
+    if _BARRIER is not None:
+        _BARRIER.wait(timeout=900)
     t_start = time.perf_counter()
     cpu = 0.0
     for d, im in inputs:
         t0 = time.perf_counter()
         oracle.detect(d, im, p, dumps=False)
         cpu += time.perf_counter() - t0
-    return t_start, time.perf_counter(), cpu
+    return os.getpid(), t_start, time.perf_counter(), cpu
 
 
 def _stereo_worker(k):
@@ -75,19 +90,25 @@ def _stereo_worker(k):
 
 
 def oracle_pool(n_workers):
+    """A spawned pool of n_workers processes that share one barrier of n_workers parties."""
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
-    return ctx.Pool(n_workers)
+    return ctx.Pool(n_workers, initializer=_init_worker, initargs=(ctx.Barrier(n_workers),))
 
 
 def run_oracle_frames(pool, frames, pdict, n_chunks):
-    """The oracle over `frames` split into n_chunks tasks (one per process of the pool).  Returns the wall
+    """The oracle over `frames` split into n_chunks tasks, n_chunks being the size of an oracle_pool (at
+    least one frame per task).  The pool's barrier puts every task on its own process.  Returns the wall
     time of the oracle sections (latest end - earliest start; each task renders its frames before its
     section) and the summed single-thread time per frame."""
-    chunks = [frames[k::n_chunks] for k in range(n_chunks) if frames[k::n_chunks]]
+    chunks = [frames[k::n_chunks] for k in range(n_chunks)]
+    if any(not c for c in chunks):
+        raise ValueError("fewer frames than processes")
     res = pool.map(_oracle_chunk, [(WORKLOAD, c, pdict) for c in chunks], chunksize=1)
-    return max(r[1] for r in res) - min(r[0] for r in res), sum(r[2] for r in res)
+    if len({r[0] for r in res}) != len(res):
+        raise RuntimeError("two oracle chunks ran on one process")
+    return max(r[2] for r in res) - min(r[1] for r in res), sum(r[3] for r in res)
 
 
 def host_cores():
@@ -401,9 +422,9 @@ def run_ours(args):
 
     # the oracle pool starts before the first CUDA work so no process forks after it
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
-    pool = oracle_pool(min(16, host_cores())) if want_cpu else None
+    pool = oracle_pool(host_cores()) if want_cpu else None
     # stereo pairs render on host cores while the GPU runs (a spawn pool, started before any CUDA work)
-    spool = mp.get_context("spawn").Pool(min(16, host_cores())) if rank == 0 and not args.no_stereo else None
+    spool = mp.get_context("spawn").Pool(host_cores()) if rank == 0 and not args.no_stereo else None
     pairs_async = spool.map_async(_stereo_worker, range(64), chunksize=2) if spool else None
 
     cfg, n = scenes.WORKLOADS[WORKLOAD]
@@ -536,11 +557,12 @@ def run_ours(args):
         ops = INT_OPS_PER_TAP * taps * npx
         achieved = ops / (dom_ms * 1e-3) / 1e12
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # INT32 lanes x SMs x clock
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        peak = sms * 128 * sm_mhz * 1e6 / 1e12  # INT32 lanes x SMs x clock
         roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tops/s",
                 "frac": round(achieved / peak, 4), "traffic": profiled_traffic(dom_name, WORKLOAD), "kernel": dom_name,
                 "units_per_launch": {"bilateral_pixels": npx, "taps_per_pixel": taps, "int_ops_per_tap": INT_OPS_PER_TAP},
-                "peak_source": f"152 SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz ({peak_src} clock)"}
+                "peak_source": f"{sms} SMs x 128 INT32 lanes x {sm_mhz:.0f} MHz ({peak_src} clock)"}
     else:
         in_bytes = n * H * W * 5
         achieved = in_bytes / (dom_ms * 1e-3) / 1e9
@@ -550,13 +572,13 @@ def run_ours(args):
 
     cpu = None
     if pool is not None:
-        # a bounded sample: 16 frames per process (about 20 s of CPU work on 16 cores)
-        workers = min(16, host_cores())
+        # a bounded sample: 16 frames per process on every host core (about 1.3 s of work per process)
+        workers = host_cores()
         frames = list(range(base, base + 16 * workers))
         run_oracle_frames(pool, frames[:workers], p.as_dict(), workers)  # warm the workers
         wall, cpu_s = run_oracle_frames(pool, frames, p.as_dict(), workers)
         pool.close()
-        cpu = {"value": round(len(frames) / wall, 3), "unit": UNIT, "cores": min(16, host_cores()), "kind": "oracle",
+        cpu = {"value": round(len(frames) / wall, 3), "unit": UNIT, "cores": workers, "kind": "oracle",
                "sample": f"{len(frames)} frames of the {WORKLOAD} workload, {len(frames) // workers} per process, "
                          f"rendered before the timed section ({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)",
                "single_thread_ms_per_frame": round(1e3 * cpu_s / len(frames), 2)}
@@ -564,6 +586,11 @@ def run_ours(args):
     if rank == 0:
         frames_total = world * n * args.steps
         value = frames_total / (total_ms * 1e-3)
+        # the whole path against HBM: algorithmic input bytes (float32 disparity + uint8 image per pixel)
+        path_gbs = value * H * W * 5 / 1e9
+        roof["path"] = {"bound": "hbm", "achieved": round(path_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(path_gbs / peaks["hbm_gbs"], 4), "bytes_per_frame": H * W * 5,
+                        "peak_source": peak_src}
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
@@ -577,6 +604,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "per_kernel_ms": {nm: round(float(x), 4) for nm, x in zip(names, per)},
             "roofline": roof,
+            "hbm_frac": roof["path"]["frac"],
             "cpu_baseline": cpu,
             "e2e": {"value": round(world * n * e2e_steps / e2e_s, 2), "unit": UNIT,
                     "h2d_bytes_per_step": int(n * H * W * 5), "d2h_bytes_per_step": int(n * ld.LANES_DTYPE.itemsize)},
@@ -602,7 +630,7 @@ def run_reference(args):
 
     import oracle
     oracle.build()
-    cores = min(16, host_cores())
+    cores = host_cores()
     pool = oracle_pool(cores)
     cfg, n = scenes.WORKLOADS[WORKLOAD]
     pdict = oracle.default_params(n_disp=cfg.n_disp).as_dict()

@@ -184,16 +184,33 @@ enum ld_stage {
     LD_STAGE_INL_X = 7,    /* uint8 [h]     final RANSAC membership of the path point at row v */
     LD_STAGE_M1 = 8,       /* int32 [h][w]  M_1 on rows >= v_top (0 above) */
     LD_STAGE_HE = 9,       /* int64 [n_starts] energy histogram H */
+    LD_STAGE_MX = 10,      /* int32 [h][w]  dense V_px accumulator m_x of Alg. 5 on rows >= v_top (0 above), the
+                              values the V_px DP kernel forms in registers (needs ld_debug_capture) */
+    LD_STAGE_IBF = 11,     /* int16 [h][w]  bilateral output I^bf (Eq. 15-16; the median or raw image when
+                              bilateral is 2 or 0) at the pixels the gradient kernel filters, -1 at the others:
+                              every pixel of the 3x3 neighbourhood of a road pixel (needs ld_debug_capture) */
 };
 /*
  * Copy stage `stage` of frame `frame` (host buffer host_dst of `bytes` bytes, which must equal the
  * stage's size) after synchronising the handle's stream.  Errors: LD_E_ARG, LD_E_STATE (no single-size
- * detection yet, or ld_detect_groups ran after the last one), LD_E_CUDA.
+ * detection yet, ld_detect_groups ran after the last one, or LD_STAGE_MX / LD_STAGE_IBF of a call made
+ * without ld_debug_capture), LD_E_CUDA.
  */
 int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, size_t bytes);
 
 /* Size in bytes of stage `stage` for the last call's frame size (0 if unknown). */
 size_t ld_debug_size(ld_handle *h, int32_t stage);
+
+/*
+ * Stage capture of the two intermediates the kernels keep on chip: m_x (Alg. 5, formed inside the V_px
+ * DP kernel) and I^bf (Eq. 15-16, formed inside the gradient kernel).  With on != 0 the handle allocates
+ * a capture buffer for max_batch frames (6 bytes per pixel) and every later call also writes both there,
+ * from the same registers the path uses, so that LD_STAGE_MX and LD_STAGE_IBF report on the last call;
+ * on = 0 frees it.  Switching drops the captured CUDA graphs (their launches hold the workspace
+ * pointers) and synchronises the handle's stream.  It costs time and memory: for checking, not for
+ * production.  Errors: LD_E_ARG (h NULL), LD_E_NOMEM, LD_E_CUDA.
+ */
+int ld_debug_capture(ld_handle *h, int32_t on);
 
 /*
  * Host-only: the lookup tables the kernels use, built from p exactly as ld_create builds them.
@@ -221,12 +238,13 @@ int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t
  * all reserved at start-up (safety-certified driving stacks forbid allocation in the per-frame path) or a
  * plugin whose host application hands it only its input and output buffers.
  *
- * It computes, for n_frames frames, the v-disparity histogram (Sec. 2.2) and the DP path of Eq. 11-12 with
- * the same readings and tie rules as ld_detect, and writes the path row v_d of each bin d to
- * path_out[frame][d] (int16, n_disp entries per frame, entry 0 = -1) - the values ld_debug_get returns for
- * LD_STAGE_PATH_Y after ld_detect.  disp is a DEVICE pointer to float32 [n_frames][h][w], path_out a DEVICE
- * pointer; the caller owns both.  Only p->n_disp, p->tau_y and p->lambda_y are used.  The work is enqueued
- * on cuda_stream (NULL = default stream) and the call returns without waiting.
+ * For n_frames frames it computes the v-disparity histogram and the road DP path over it, with the same
+ * tie rules as ld_detect, and writes the path row of each disparity bin d to path_out[frame][d] (int16,
+ * n_disp entries per frame, entry 0 = -1): the values ld_debug_get returns for LD_STAGE_PATH_Y after
+ * ld_detect with the same parameters.  disp is a DEVICE pointer to float32 [n_frames][h][w], path_out a
+ * DEVICE pointer; the caller owns both.  Only p->n_disp, p->tau_y, p->lambda_y and p->dp_literal are
+ * read; the literal form of the DP (dp_literal = 1) is not offered here and returns LD_E_ARG.  The work
+ * is enqueued on cuda_stream (NULL = default stream) and the call returns without waiting.
  *
  * No cudaMalloc, cudaFree or allocating library routine is called.  The histogram scratch is a static
  * device array of LD_STATIC_SCRATCH_BYTES bytes inside the library, which every GPU that loads the library

@@ -527,6 +527,15 @@ __device__ void block_scan(int *a, int n, int *chunk)
     __syncthreads();
 }
 
+// Stage capture: m_x(u, v) = -varrho * (votes of the band of row v in column u) of cells u0, u0 + 1.
+__device__ __forceinline__ void store_mx(const KParams &kp, const Work &w, int f, int v, int u0, int b0, int b1)
+{
+    int32_t *row = w.dbg_mx + ((size_t)f * kp.H + v) * kp.W;
+    row[u0] = -kp.vote_rho * b0;
+    if (u0 + 1 < kp.W)
+        row[u0 + 1] = -kp.vote_rho * b1;
+}
+
 // Forward DP over rows vmax-1 .. vtop, then the backtrack.  Backtrack rows of the top seg_rows rows stay
 // in shared memory; lower rows go to the frame's global buffer and come back in blocks of seg_rows rows
 // for the backtrack.
@@ -575,6 +584,8 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
             for (int c = 0; c < 2; ++c)
                 e2[c] = 2 * j + c < W ? (PACKED ? 16 : 1) * -kp.vote_rho * band[p][c] : kSent;
             sts2(sa(S.E0) + 8u * (uint32_t)j, make_int2(e2[0], e2[1]));
+            if (w.dbg_mx)
+                store_mx(kp, w, f, vmax, 2 * j, band[p][0], band[p][1]);
         }
     }
     __syncthreads();
@@ -596,6 +607,8 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
                 sts2(dv + 8u * (uint32_t)j, make_int2(0, 0));
                 band[p][0] += dl.x;
                 band[p][1] += dl.y;
+                if (w.dbg_mx)
+                    store_mx(kp, w, f, v, 2 * j, band[p][0], band[p][1]);
                 const uint32_t code = dp_pair<TAU, PACKED>(kp, 2 * j, band[p][0], band[p][1], pen, sa(Ep), sa(Ec));
                 if (r < SR)
                     sts8(bt + (uint32_t)(r * RB + j), code);

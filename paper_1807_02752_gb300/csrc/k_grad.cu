@@ -361,6 +361,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad(const KParams kp, const Wo
                   ((uint32_t)(c[3] >> 1) << 24);
         }
         *reinterpret_cast<uint32_t *>(ibf + (size_t)br * L.IW + u0) = out;
+        const int v = r0 - 1 + br;
+        if (w.dbg_ibf && v >= 0 && v < H) {   // stage capture: the values this CTA computed (halo rows too)
+            int16_t *drow = w.dbg_ibf + ((size_t)f * H + v) * W;
+            for (int q = 0; q < 4 && u0 + q < W; ++q)
+                drow[u0 + q] = (int16_t)((out >> (8 * q)) & 0xffu);
+        }
     }
     __syncthreads();
 

@@ -893,7 +893,7 @@ __global__ void __launch_bounds__(kTopThreads) k_topk(const KParams kp, const Wo
 
 static int grid_for(int tiles, int per_sm)
 {
-    const int g = 152 * per_sm;
+    const int g = sm_count() * per_sm;
     return tiles < g ? tiles : g;
 }
 
@@ -927,7 +927,7 @@ cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, 
 {
     const long long cells = (long long)n * a.mh * a.mw;
     const int g1 = (int)((cells + kCellThreads - 1) / kCellThreads);
-    k_conv1<<<g1 < 152 * 8 ? g1 : 152 * 8, kCellThreads, 0, s>>>(a, xsum, n, road);
+    k_conv1<<<grid_for(g1, 8), kCellThreads, 0, s>>>(a, xsum, n, road);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -993,7 +993,7 @@ cudaError_t net_backward(const NetArgs &a, const uint8_t *labels, int n, float p
     const long long cells = (long long)n * a.mh * a.mw;
     const float inv_n = 1.0f / (float)cells;
     const int gl = (int)((cells + kCellThreads - 1) / kCellThreads);
-    const int GL = gl < 152 * 4 ? gl : 152 * 4;
+    const int GL = grid_for(gl, 4);
     k_loss<<<GL, kCellThreads, 0, s>>>(a, labels, n, inv_n, pw, a.part_head);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

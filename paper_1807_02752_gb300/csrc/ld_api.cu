@@ -66,6 +66,9 @@ struct ld_handle {
     cudaEvent_t fork = nullptr, join[2] = {};
     // tile sizes chosen by ld_tune for frames of tile_w x tile_h (0: the built-in rules)
     int tile_w = 0, tile_h = 0, tile[3] = {0, 0, 0};
+    // stage capture (ld_debug_capture): device buffer of m_x and I^bf for max_batch frames, or null
+    void *dbg = nullptr;
+    bool dbg_valid = false;      // the last single-size call ran with the capture on
     std::string err;
 };
 
@@ -241,6 +244,12 @@ int enqueue_range(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const 
     if (timed && (e = cudaEventRecord(h->ev[first], s)) != cudaSuccess)
         return cuda_fail(h, e, "event record");
     for (int k = first; k < last; ++k) {
+        // stage capture: I^bf starts at -1 (not computed), m_x at 0 (rows above v_top)
+        const size_t npx = (size_t)kp.n_frames * kp.H * kp.W;
+        if (k == 3 && w.dbg_ibf && (e = cudaMemsetAsync(w.dbg_ibf, 0xff, npx * 2, s)) != cudaSuccess)
+            return cuda_fail(h, e, "capture reset");
+        if (k == 4 && w.dbg_mx && (e = cudaMemsetAsync(w.dbg_mx, 0, npx * 4, s)) != cudaSuccess)
+            return cuda_fail(h, e, "capture reset");
         switch (k) {
         case 0: e = ld::launch_vdisp(kp, w, disp, s); break;
         case 1: e = ld::launch_road(kp, w, s); break;
@@ -308,6 +317,10 @@ ld::Work work_from(const ld::Work &w, const ld::KParams &kp, int f0)
     if (v.xsum)
         v.xsum += f * (size_t)((H + 3) / 4) * ((W + 3) / 4);
     v.HE += f * (size_t)kp.n_starts;
+    if (v.dbg_mx)
+        v.dbg_mx += f * H * W;
+    if (v.dbg_ibf)
+        v.dbg_ibf += f * H * W;
     return v;
 }
 
@@ -462,6 +475,7 @@ KParams handle_call(ld_handle *h, int w, int hh, int n)
     h->last_h = hh;
     h->last_n = n;
     h->have_last = true;
+    h->dbg_valid = h->dbg != nullptr;
     return make_kparams(h, w, hh, n);
 }
 KParams handle_kparams(const ld_handle *h, int w, int hh, int n) { return make_kparams(h, w, hh, n); }
@@ -680,6 +694,7 @@ int ld_detect(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, in
     h->last_h = hh;
     h->last_n = n_frames;
     h->have_last = true;
+    h->dbg_valid = h->dbg != nullptr;
     // replay a captured graph when the same buffers and sizes come back
     for (GraphSlot &g : h->graphs)
         if (g.exec && g.disp == disp && g.img == img && g.out == out_lanes && g.w == w && g.h == hh && g.n == n_frames) {
@@ -795,6 +810,7 @@ int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t
     h->last_h = hh;
     h->last_n = n_frames;
     h->have_last = true;
+    h->dbg_valid = h->dbg != nullptr;
     rc = enqueue(h, kp, disp, img, out_lanes, true);
     if (rc != LD_OK)
         return rc;
@@ -886,6 +902,8 @@ size_t ld_debug_size(ld_handle *h, int32_t stage)
     case LD_STAGE_INL_X: return H;
     case LD_STAGE_M1: return H * W * 4;
     case LD_STAGE_HE: return (size_t)ld_n_starts(&h->p, (int32_t)W) * 8;
+    case LD_STAGE_MX: return H * W * 4;
+    case LD_STAGE_IBF: return H * W * 2;
     default: return 0;
     }
 }
@@ -901,6 +919,8 @@ int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, siz
     const size_t want = ld_debug_size(h, stage);
     if (want == 0 || bytes != want)
         return fail(h, LD_E_ARG, "unknown stage or wrong byte count");
+    if ((stage == LD_STAGE_MX || stage == LD_STAGE_IBF) && !h->dbg_valid)
+        return fail(h, LD_E_STATE, "m_x and I^bf are recorded only while ld_debug_capture is on");
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess)
         return cuda_fail(h, e, "stream sync");
@@ -960,9 +980,41 @@ int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, siz
             e = cudaMemcpy(dst, h->w.HE + f * ns, ns * 8, cudaMemcpyDeviceToHost);
         break;
     }
+    case LD_STAGE_MX: e = cudaMemcpy(dst, h->w.dbg_mx + f * H * W, H * W * 4, cudaMemcpyDeviceToHost); break;
+    case LD_STAGE_IBF: e = cudaMemcpy(dst, h->w.dbg_ibf + f * H * W, H * W * 2, cudaMemcpyDeviceToHost); break;
     default: return fail(h, LD_E_ARG, "unknown stage");
     }
     return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "debug copy");
+}
+
+int ld_debug_capture(ld_handle *h, int32_t on)
+{
+    if (!h)
+        return LD_E_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "stream sync");
+    if ((on != 0) == (h->dbg != nullptr))
+        return LD_OK;
+    drop_graphs(h);   // the captured launches hold the workspace pointers
+    h->dbg_valid = false;
+    if (!on) {
+        cudaFree(h->dbg);
+        h->dbg = nullptr;
+        h->w.dbg_mx = nullptr;
+        h->w.dbg_ibf = nullptr;
+        return LD_OK;
+    }
+    const size_t npx = (size_t)h->max_batch * h->max_w * h->max_h;
+    e = cudaMalloc(&h->dbg, align_up(npx * 4) + npx * 2);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->dbg = nullptr;
+        return fail(h, LD_E_NOMEM, std::string("capture buffer: ") + cudaGetErrorString(e));
+    }
+    h->w.dbg_mx = (int32_t *)h->dbg;
+    h->w.dbg_ibf = (int16_t *)((char *)h->dbg + align_up(npx * 4));
+    return LD_OK;
 }
 
 const char *ld_last_error(const ld_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -975,6 +1027,7 @@ void ld_destroy(ld_handle *h)
     drop_graphs(h);
     release_sync_objects(h);
     cudaFree(h->ws);
+    cudaFree(h->dbg);
     delete h;
 }
 
@@ -994,6 +1047,7 @@ int detect_eager(ld_handle *h, const float *disp, const uint8_t *img, int32_t w,
     h->last_h = hh;
     h->last_n = n_frames;
     h->have_last = true;
+    h->dbg_valid = h->dbg != nullptr;
     return enqueue(h, kp, disp, img, out_lanes);
 }
 }  // namespace ld

@@ -6,6 +6,7 @@
 // fixed by the expression alone.  The library is also compiled with --fmad=false as a safety net.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -76,6 +77,8 @@ struct Work {
     int32_t *xsum;       // [n][ceil(H/4)][ceil(W/4)] block sums of |G_x w_g| for the learned proposal, or null
     uint8_t *med;        // [n][H][W] median-filtered image (bilateral = 2), or null
     int64_t *HE;         // [n][n_starts]
+    int32_t *dbg_mx;     // [n][H][W] the Alg. 5 accumulator m_x as the V_px DP kernel forms it, or null (capture off)
+    int16_t *dbg_ibf;    // [n][H][W] bilateral output where the gradient kernel computes it, -1 elsewhere, or null
     const int32_t *wr;   // [kWrEntries] Q15
     const int32_t *wg;   // [kWgEntries] Q12
     int32_t max_w, max_h, pmax;
@@ -124,6 +127,23 @@ inline cudaError_t allow_max_smem(K kernel, int smem_optin)
     if (e != cudaSuccess)
         return e;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)a.sharedSizeBytes);
+}
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount), queried once per
+// device; grids that stop at a whole number of waves are sized from it.
+inline int sm_count()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return 1;
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
 }
 
 // f64 Horner without contraction.

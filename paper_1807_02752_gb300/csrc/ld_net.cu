@@ -173,7 +173,7 @@ int ld_net_create(ld_handle *h, int32_t training, ld_net **out)
     net->max_ns = ld_n_starts(&ld::handle_params(h), mw);
     const size_t cells = (size_t)mb * net->max_mh * net->max_mw, P = ld::kNetParams;
     const size_t ncs = (size_t)(net->max_ns + 3) / 4, ecap = (size_t)ld::kEvalPerTop * ld::kTopKMax;
-    const size_t nparts = 152 * ld::kWgradCtasPerSm;
+    const size_t nparts = (size_t)ld::sm_count() * ld::kWgradCtasPerSm;  // the weight-gradient grid's CTAs
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;

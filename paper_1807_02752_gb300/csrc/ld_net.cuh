@@ -30,7 +30,7 @@ struct NetArgs {
     const float *bias[4];           // b_l, inside the master copy
     const float *bh;                // head bias, inside the master copy
     float *theta, *m, *v;           // master weights and Adam moments [kNetParams]
-    float *part;                    // weight-gradient partials [152 kWgradCtasPerSm][32][289]
+    float *part;                    // weight-gradient partials [SMs x kWgradCtasPerSm][32][289]
     float *part_head;               // loss partials [608][18]
 };
 

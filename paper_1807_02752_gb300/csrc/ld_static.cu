@@ -1,7 +1,7 @@
-// ld_road_path_static: the road-profile DP path (v-disparity histogram + the Eq. 12 DP) for callers that
-// must not allocate device memory.  It is a separate variant of the library's two road kernels, fused
-// into one kernel whose v-disparity scratch lives in a file-scope static device array instead of a
-// handle's workspace.  No other code path uses it.
+// ld_road_path_static: the road-profile DP path (v-disparity histogram and the road DP over it, with the
+// tie rules of the handle-based road kernel) for callers that must not allocate device memory.  It is a
+// separate variant of the library's two road kernels, fused into one kernel whose v-disparity scratch
+// lives in a file-scope static device array instead of a handle's workspace.  No other code path uses it.
 //
 // The array is LD_STATIC_SCRATCH_BYTES bytes of device memory that every GPU which loads the library
 // keeps until the process exits.  Host code cannot use the array's name as a device address (on the host
@@ -159,6 +159,10 @@ extern "C" int ld_road_path_static(const ld_params *p, const float *disp, int32_
     if (p->n_disp < 4 || p->n_disp > LD_MAX_D || p->tau_y < 0 || p->tau_y > 15 || p->lambda_y < 0 ||
         p->lambda_y > 1000 || w < 16 || w > LD_MAX_W || h_px < 16 || h_px > LD_MAX_H || n_frames < 1) {
         ld::set_global_error("ld_road_path_static: parameter or size out of range");
+        return LD_E_ARG;
+    }
+    if (p->dp_literal != 0) {
+        ld::set_global_error("ld_road_path_static: dp_literal = 1 (the DP as printed) is not offered by this entry point");
         return LD_E_ARG;
     }
     const size_t need = (size_t)n_frames * p->n_disp * h_px * sizeof(int32_t);

@@ -346,7 +346,8 @@ int enqueue_stereo(ld_stereo *st, const uint8_t *left, const uint8_t *right, int
         return scuda(st, e, "event");
     const long long total = (long long)n * w * hh;
     const int g = (int)((total + 255) / 256);
-    ld::k_lrc<<<g < 152 * 16 ? g : 152 * 16, 256, 0, s>>>(st->lf, st->rt, w, hh, n, st->sp.tr_lrc, disp);
+    const int gmax = ld::sm_count() * 16;
+    ld::k_lrc<<<g < gmax ? g : gmax, 256, 0, s>>>(st->lf, st->rt, w, hh, n, st->sp.tr_lrc, disp);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return scuda(st, e, "consistency check");
     if (timed && (e = cudaEventRecord(st->ev[2], s)) != cudaSuccess)

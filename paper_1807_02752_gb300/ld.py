@@ -20,6 +20,7 @@ F_NO_ROAD, F_CAP_Y, F_DEGEN_Y, F_CAP_X, F_DEGEN_X, F_NO_LANES, F_FALLBACK = 1, 2
 NET_PARAMS, NET_TOPK_MAX = 18689, 256
 NET_STAGE_XSUM, NET_STAGE_HEATMAP, NET_STAGE_SCORES, NET_STAGE_CFLAG = 1, 2, 3, 4
 STAGE_VDISP, STAGE_PATH_Y, STAGE_INL_Y, STAGE_ROWS, STAGE_EDGES, STAGE_PATH_X, STAGE_INL_X, STAGE_M1, STAGE_HE = range(1, 10)
+STAGE_MX, STAGE_IBF = 10, 11
 
 
 class Params(C.Structure):
@@ -106,6 +107,8 @@ def load():
     L.ld_debug_get.restype = C.c_int
     L.ld_debug_size.argtypes = [p, i32]
     L.ld_debug_size.restype = C.c_size_t
+    L.ld_debug_capture.argtypes = [p, i32]
+    L.ld_debug_capture.restype = C.c_int
     L.ld_tables.argtypes = [P, p, p, p]
     L.ld_tables.restype = C.c_int
     L.ld_launches_per_detect.argtypes = []
@@ -184,7 +187,7 @@ def load():
 
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
-            "ld_debug_get", "ld_debug_size", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
+            "ld_debug_get", "ld_debug_size", "ld_debug_capture", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
             "ld_destroy", "ld_road_path_static", "ld_tune", "ld_detect_groups", "ld_server_create", "ld_server_submit", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_server_set_learned", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
@@ -255,6 +258,7 @@ class Detector:
             raise LDError(rc, self.L.ld_last_error(None).decode())
         self.h = h
         self.max_w, self.max_h, self.max_batch = max_w, max_h, max_batch
+        self.capturing = False
 
     def _check(self, rc):
         if rc != OK:
@@ -351,7 +355,16 @@ class Detector:
             return buf.view(np.int32).reshape(H, W)
         if stage == STAGE_HE:
             return buf.view(np.int64)
+        if stage == STAGE_MX:
+            return buf.view(np.int32).reshape(H, W)
+        if stage == STAGE_IBF:
+            return buf.view(np.int16).reshape(H, W)
         return buf
+
+    def capture(self, on: bool = True):
+        """Record m_x and I^bf on later calls (LD_STAGE_MX / LD_STAGE_IBF); allocates a capture buffer."""
+        self._check(self.L.ld_debug_capture(self.h, 1 if on else 0))
+        self.capturing = bool(on)
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,10 +1,12 @@
 """Frames of several sizes in one call (ld_detect_groups): every group's results must be the ones
 ld_detect gives its frames, byte for byte, on a stream of the handle's own (one captured graph, the groups
-on two forked streams, then replays) and on the legacy default stream (groups one after another)."""
+on two forked streams, then replays) and on the legacy default stream (groups one after another); and
+every frame's lanes, flags and fitted rows must be the oracle's."""
 import numpy as np
 import pytest
 
 from paper_1807_02752_gb300 import ld, scenes
+from gpu_util import compare_frame
 
 pytestmark = pytest.mark.gpu
 
@@ -30,6 +32,15 @@ def _groups(torch, sizes, n_disp, first=300):
         i = torch.from_numpy(np.stack([f[1] for f in fr])).cuda()
         out.append((d, i))
     return out
+
+
+def _check_oracle(groups, outs, p):
+    """Every frame of every group against the oracle (lanes, flags, energies, f and V_px rows)."""
+    for g, ((d, i), o) in enumerate(zip(groups, outs)):
+        res = ld.Detector.lanes(o)
+        dn, im = d.cpu().numpy(), i.cpu().numpy()
+        for k in range(dn.shape[0]):
+            compare_frame(None, res[k], k, dn[k], im[k], p, stages=False)
 
 
 def _alone(torch, groups, p):
@@ -62,6 +73,8 @@ def test_groups_match_ld_detect(torch_cuda, own_stream):
                 torch.cuda.synchronize()
                 got = [ld.Detector.lanes(o).tobytes() for o in outs]
                 assert got == want, f"call {rep}"
+                if rep == 0:
+                    _check_oracle(groups, outs, p)
             # another list (reversed order, so other workspace offsets and stream choices): a new graph
             rev, routs = groups[::-1], outs[::-1]
             for o in routs:
@@ -102,6 +115,7 @@ def test_groups_full_sizes(torch_cuda):
             outs = det.detect_groups(groups, outs)
             torch.cuda.synchronize()
             assert [ld.Detector.lanes(o).tobytes() for o in outs] == want
+        _check_oracle(groups, outs, p)
     finally:
         det.close()
 

@@ -1,7 +1,9 @@
 """GPU parity: the CUDA library against the oracle, element by element, on seeded synthetic frames.
 
-Integer, index and set outputs (histograms, DP paths, inlier sets, edges, Sobel values, votes, M_1,
-energies, lanes) must be identical; fitted road and V_px parameters agree within 1e-4 relative.
+Integer, index and set outputs (histograms, DP paths, inlier sets, edges, Sobel values, votes, m_x, the
+bilateral output, M_1, energies, lanes) must be identical; fitted road and V_px parameters agree within
+1e-4 relative.  Handles that record m_x and I^bf (ld_debug_capture) have them compared too; the 64-frame
+workload runs without that capture, exactly as the benchmark launches it.
 """
 import numpy as np
 import pytest
@@ -22,6 +24,12 @@ def torch_cuda():
     return torch
 
 
+def _captured(W, H, n, p):
+    det = ld.Detector(W, H, n, p)
+    det.capture(True)
+    return det
+
+
 def _run(torch, det, disp, img):
     d = torch.from_numpy(disp).cuda()
     i = torch.from_numpy(img).cuda()
@@ -35,7 +43,7 @@ def test_every_stage_matches_oracle(torch_cuda, name, n):
     cfg, _ = scenes.WORKLOADS[name]
     disp, img, _ = scenes.make_batch(cfg, n)
     p = ld.default_params(n_disp=cfg.n_disp)
-    det = ld.Detector(cfg.width, cfg.height, n, p)
+    det = _captured(cfg.width, cfg.height, n, p)
     res = _run(torch_cuda, det, disp, img)
     for f in range(n):
         compare_frame(det, res[f], f, disp[f], img[f], p)
@@ -60,7 +68,7 @@ def test_hd_frames_match_oracle(torch_cuda):
     cfg, _ = scenes.WORKLOADS["batch16_1920x1080"]
     disp, img, _ = scenes.make_batch(cfg, 2)
     p = ld.default_params(n_disp=cfg.n_disp)
-    det = ld.Detector(cfg.width, cfg.height, 2, p)
+    det = _captured(cfg.width, cfg.height, 2, p)
     res = _run(torch_cuda, det, disp, img)
     for f in range(2):
         compare_frame(det, res[f], f, disp[f], img[f], p)
@@ -75,7 +83,7 @@ def test_ragged_and_tiny_sizes(torch_cuda):
         except RuntimeError:
             continue
         p = ld.default_params(n_disp=D)
-        det = ld.Detector(W + 7, H + 3, 4, p)  # handle larger than the frames
+        det = _captured(W + 7, H + 3, 4, p)  # handle larger than the frames
         res = _run(torch_cuda, det, disp, img)
         for f in range(2):
             compare_frame(det, res[f], f, disp[f], img[f], p)
@@ -97,7 +105,7 @@ def test_degenerate_frames(torch_cuda):
     disp = np.stack([f[0] for f in frames])
     img = np.stack([f[1] for f in frames])
     p = ld.default_params(n_disp=cfg.n_disp)
-    det = ld.Detector(W, H, len(frames), p)
+    det = _captured(W, H, len(frames), p)
     res = _run(torch_cuda, det, disp, img)
     for f in range(len(frames)):
         compare_frame(det, res[f], f, disp[f], img[f], p)
@@ -114,7 +122,7 @@ def test_param_variants(torch_cuda):
                {"dp_literal": 1}, {"dp_literal": 1, "tau_y": 3, "lambda_y": 2}, {"band_literal_bottom": 1},
                {"band_literal_bottom": 1, "chi": 5}, {"band_literal_bottom": 1, "chi": 0}):
         p = ld.default_params(n_disp=cfg.n_disp, **kw)
-        det = ld.Detector(cfg.width, cfg.height, 3, p)
+        det = _captured(cfg.width, cfg.height, 3, p)
         res = _run(torch_cuda, det, disp, img)
         for f in range(3):
             compare_frame(det, res[f], f, disp[f], img[f], p)

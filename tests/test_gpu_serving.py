@@ -1,11 +1,13 @@
 """Serving: frames of two sizes from three camera streams through one server (continuous batching over
-slots).  Every result must be the one the frame gets alone, byte for byte; results carry the caller's tag
-and per-stream sequence numbers; the device-kept stream state is each stream's latest result.
+slots).  Every result must be the one the frame gets alone, byte for byte, and that result the oracle's;
+results carry the caller's tag and per-stream sequence numbers; the device-kept stream state is each
+stream's latest result.
 """
 import numpy as np
 import pytest
 
 from paper_1807_02752_gb300 import ld, scenes
+from gpu_util import compare_frame
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +45,14 @@ def _alone(frames, p):
     for det in dets.values():
         det.close()
     return res
+
+
+def test_alone_results_match_oracle(torch_cuda):
+    """The per-frame results the serving tests compare against are the oracle's (every frame of both sizes)."""
+    p = ld.default_params(n_disp=48)
+    frames = _frames()
+    for tag, ((sid, k, wh, d, i), r) in enumerate(zip(frames, _alone(frames, p))):
+        compare_frame(None, r, tag, d, i, p, stages=False)
 
 
 def _serve(frames, p, **kw):
