@@ -188,7 +188,8 @@ enum ld_stage {
                               values the V_px DP kernel forms in registers (needs ld_debug_capture) */
     LD_STAGE_IBF = 11,     /* int16 [h][w]  bilateral output I^bf (Eq. 15-16; the median or raw image when
                               bilateral is 2 or 0) at the pixels the gradient kernel filters, -1 at the others:
-                              every pixel of the 3x3 neighbourhood of a road pixel (needs ld_debug_capture) */
+                              every pixel of the 3x3 neighbourhood of a road pixel that may be an edge (see
+                              ld_flat_range), so every pixel the Sobel of an edge reads (needs ld_debug_capture) */
 };
 /*
  * Copy stage `stage` of frame `frame` (host buffer host_dst of `bytes` bytes, which must equal the
@@ -218,6 +219,20 @@ int ld_debug_capture(ld_handle *h, int32_t on);
  * floor(sin(dtheta) 2^15).  Any pointer may be NULL.  Errors: LD_E_ARG.
  */
 int ld_tables(const ld_params *p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_q);
+
+/*
+ * Host-only: the exact pruning bound of the gradient kernel.  A road pixel whose neighbourhood (the
+ * windows of its 3x3 neighbours, all inside the frame) spans an image range of at most the returned value
+ * cannot pass the edge test of Sec. 2.3.1, whatever its values: every Q15 weight of those windows lies in
+ * [a, b] (a at the range, b at zero difference), so each bilateral output is within
+ * (b - a) r / (4 a) + 1/2 of its window mean; means of windows two pixels apart differ by at most
+ * 2 r / (2 rho + 1); the Sobel components are then at most 4 (2 r / (2 rho + 1) + 2 e) each, and the
+ * bound is the largest range r for which twice its square stays at most edge_thresh^2.  The kernel leaves
+ * such pixels (and the bilateral outputs only they would read) out; every edge, G and vote is unchanged.
+ * The paper filters the whole image and has no counterpart.  Returns -1 when nothing is pruned
+ * (bilateral != 1, or no range qualifies) or when p is invalid.
+ */
+int32_t ld_flat_range(const ld_params *p);
 
 /* Number of kernel launches one ld_detect call enqueues, and the name of launch k (0-based). */
 int32_t ld_launches_per_detect(void);

@@ -111,6 +111,47 @@ void build_tables(const ld_params &p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_
         }
 }
 
+// The largest image range r for which a road pixel provably fails the edge test, whatever the values
+// inside its neighbourhood (the exact pruning of the gradient kernel); -1 when none or when the pre-filter
+// is not the bilateral.  Let every pixel of the (2 rho + 3)^2 neighbourhood of a pixel s lie in [m, m + r].
+//  1. Every tap weight of Eq. 16 in Q15, w = (ws * wr(|dI|) + 2^14) >> 15, of every window centred in the
+//     3x3 neighbourhood of s lies in [a, b], a = min over classes at |dI| = r (wr is non-increasing),
+//     b = max over classes at |dI| = 0.
+//  2. For a window of n taps with mean mu, sum(w q) / sum(w) - mu = sum((w - (a+b)/2)(q - mu)) / sum(w), and
+//     sum|q - mu| <= n r / 2 for values in an interval of length r, so the weighted mean is within
+//     (b - a) r / (4 a) of mu; the rounded output (2 sum(wq) + sum(w)) / (2 sum(w)) adds at most 1/2: e.
+//  3. Windows two columns (or rows) apart share all but 2 (2 rho + 1) taps, so their means differ by at
+//     most 2 r / (2 rho + 1).
+//  4. Each Sobel component sums weights 1, 2, 1 of such differences: |G_x|, |G_y| <= 4 (2r / (2 rho + 1) + 2e),
+//     and G_x^2 + G_y^2 <= 2 * that^2.  When that is at most thr^2 the pixel is not an edge.
+// The windows must lie inside the frame (n = (2 rho + 1)^2); the kernel never prunes near the border.
+int32_t flat_range(const ld_params &p)
+{
+    if (p.bilateral != 1)
+        return -1;
+    const int rho = p.bf_rho, N = 2 * rho + 1;
+    int32_t ws_q[121], wr_q[256];
+    build_tables(p, ws_q, wr_q, nullptr);
+    int64_t b = 0;
+    for (int i = 0; i < N * N; ++i)
+        b = std::max<int64_t>(b, ((int64_t)ws_q[i] * wr_q[0] + 16384) >> 15);
+    const double thr2 = (double)p.edge_thresh * p.edge_thresh;
+    int32_t best = -1;
+    for (int r = 0; r < 255; ++r) {
+        int64_t a = INT64_MAX;
+        for (int i = 0; i < N * N; ++i)
+            a = std::min<int64_t>(a, ((int64_t)ws_q[i] * wr_q[r] + 16384) >> 15);
+        if (a <= 0)
+            break;
+        const double e = (double)(b - a) * r / (4.0 * a) + 0.5;
+        const double g = 4.0 * (2.0 * r / N + 2.0 * e);
+        if (2.0 * g * g * (1.0 + 1e-9) > thr2)   // margin against the rounding of this evaluation
+            break;
+        best = r;
+    }
+    return best;
+}
+
 const char *check_params(const ld_params *p)
 {
     if (!p)
@@ -225,6 +266,7 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
                 k.cls_ws[c] = (uint16_t)h->ws_q[(dy + rho) * nn + dx + rho];
             }
     }
+    k.flat_range = flat_range(p);
     k.seg_rows = ld::vpx_seg_rows(k, (size_t)h->smem_optin - 1024);
     const bool tuned = W == h->tile_w && H == h->tile_h;
     k.tile_vdisp = tuned ? h->tile[0] : 0;
@@ -542,6 +584,13 @@ int ld_tables(const ld_params *p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_q)
         return LD_E_ARG;
     build_tables(*p, ws_q, wr_q, wg_q);
     return LD_OK;
+}
+
+int32_t ld_flat_range(const ld_params *p)
+{
+    if (check_params(p))
+        return -1;
+    return flat_range(*p);
 }
 
 int32_t ld_launches_per_detect(void) { return kLaunches; }

@@ -48,6 +48,9 @@ struct KParams {
     // time in the same way); cls_ws[c] = the spatial weight of class c.
     int32_t n_cls;
     uint16_t cls_ws[24];
+    // Largest image range (max - min over a group's (4 + 2 rho + 6) x (2 rho + 3) neighbourhood) for which no
+    // pixel of the group can pass the edge test, or -1 (pruning off: bilateral != 1).  See flat_range().
+    int32_t flat_range;
 };
 
 // Per-frame state written by the fit kernels and read downstream.

@@ -111,6 +111,8 @@ def load():
     L.ld_debug_capture.restype = C.c_int
     L.ld_tables.argtypes = [P, p, p, p]
     L.ld_tables.restype = C.c_int
+    L.ld_flat_range.argtypes = [P]
+    L.ld_flat_range.restype = i32
     L.ld_launches_per_detect.argtypes = []
     L.ld_launches_per_detect.restype = i32
     L.ld_launch_name.argtypes = [i32]
@@ -187,7 +189,7 @@ def load():
 
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
-            "ld_debug_get", "ld_debug_size", "ld_debug_capture", "ld_tables", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
+            "ld_debug_get", "ld_debug_size", "ld_debug_capture", "ld_tables", "ld_flat_range", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
             "ld_destroy", "ld_road_path_static", "ld_tune", "ld_detect_groups", "ld_server_create", "ld_server_submit", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_server_set_learned", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
