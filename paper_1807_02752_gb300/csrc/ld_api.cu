@@ -290,6 +290,10 @@ int enqueue_range(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const 
         const size_t npx = (size_t)kp.n_frames * kp.H * kp.W;
         if (k == 3 && w.dbg_ibf && (e = cudaMemsetAsync(w.dbg_ibf, 0xff, npx * 2, s)) != cudaSuccess)
             return cuda_fail(h, e, "capture reset");
+        // the gradient kernel's tiles append their edges and votes to the per-row lists
+        if (k == 3 && ((e = cudaMemsetAsync(w.ecount, 0, (size_t)kp.n_frames * kp.H * 4, s)) != cudaSuccess ||
+                       (e = cudaMemsetAsync(w.vcount, 0, (size_t)kp.n_frames * kp.H * 4, s)) != cudaSuccess))
+            return cuda_fail(h, e, "edge count reset");
         if (k == 4 && w.dbg_mx && (e = cudaMemsetAsync(w.dbg_mx, 0, npx * 4, s)) != cudaSuccess)
             return cuda_fail(h, e, "capture reset");
         switch (k) {
@@ -651,6 +655,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     const size_t o_bt = take(n * H * (size_t)ld::vpx_row_bytes(max_w)), o_m1 = take(n * H * W * 4), o_he = take(n * n_starts * 8);
     const size_t o_pts = take(n * 2 * 3 * pmax * 2), o_np = take(n * 2 * 4);
     const size_t o_tab = take(sizeof(int32_t) * (ld::kWrEntries + ld::kWgEntries));
+    const size_t o_cls = take(sizeof(uint16_t) * ld::kClsTables * 512);
     const size_t o_d = take(n * H * W * 4), o_i = take(n * H * W), o_l = take(n * sizeof(ld_lanes));
     const size_t o_med = take(p->bilateral == 2 ? n * H * W : 0);
     e = cudaMalloc(&h->ws, off);
@@ -682,6 +687,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     h->d_tables = (int32_t *)(b + o_tab);
     w.wr = h->d_tables;
     w.wg = h->d_tables + ld::kWrEntries;
+    w.cls_tab = (const uint16_t *)(b + o_cls);
     w.max_w = max_w;
     w.max_h = max_h;
     h->d_disp = (float *)(b + o_d);
@@ -697,6 +703,15 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     for (int k = 512; k < ld::kWrEntries; ++k)
         tab[k] = 0;
     e = cudaMemcpy(h->d_tables, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice);
+    // the gradient kernel's per-class tables T_c[a] = (ws_c * wr(a) + 2^14) >> 15, a = |dI| < 256, zero above
+    // (the sentinel outside the frame lands there); classes as in make_kparams
+    if (e == cudaSuccess) {
+        std::vector<uint16_t> cls((size_t)ld::kClsTables * 512, 0);
+        for (int c = 0; c < kmax.n_cls; ++c)
+            for (int a = 0; a < 256; ++a)
+                cls[(size_t)c * 512 + a] = (uint16_t)(((uint32_t)kmax.cls_ws[c] * (uint32_t)tab[256 + a] + 16384u) >> 15);
+        e = cudaMemcpy((void *)w.cls_tab, cls.data(), sizeof(uint16_t) * cls.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess)
         e = ld::setup_dp(h->smem_optin);
     if (e == cudaSuccess)
@@ -878,7 +893,7 @@ int ld_tune(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int3
     // candidates per tuned kernel (launch index in the sequence, rows per CTA); the launchers reduce a
     // value that does not fit their shared-memory budget
     static const int kTuned[3] = {0, 3, 6};  // k_vdisp, k_grad, k_m1
-    static const std::vector<int> kCand[3] = {{8, 16, 32}, {12, 16, 20, 24, 28}, {8, 12, 14, 16}};
+    static const std::vector<int> kCand[3] = {{8, 16, 32}, {8, 12, 16, 24, 32}, {8, 12, 14, 16}};
     constexpr int kReps = 3;
     h->tile_w = w;
     h->tile_h = hh;

@@ -18,6 +18,7 @@ constexpr int kMaxHyps = 256;
 constexpr int kWgEntries = 16385;     // Eq. 23 table: sin(dtheta) in [0, 1/2] in steps of 2^-15
 constexpr int kWrEntries = 768;       // Q15 range weight of dI at index 256 + dI (symmetric; entries >= 512 are 0)
 constexpr int kSentinel = 511;        // image value marking taps outside the frame
+constexpr int kClsTables = 24;        // distance classes of the largest bilateral window (rho = 5: 20 used)
 
 // Per-launch constants, passed by value (they live in the kernel-parameter constant bank).
 struct KParams {
@@ -84,6 +85,7 @@ struct Work {
     int16_t *dbg_ibf;    // [n][H][W] bilateral output where the gradient kernel computes it, -1 elsewhere, or null
     const int32_t *wr;   // [kWrEntries] Q15
     const int32_t *wg;   // [kWgEntries] Q12
+    const uint16_t *cls_tab;  // [kClsTables][512] Q15 bilateral weights by distance class and |dI| (zero from 256 on)
     int32_t max_w, max_h, pmax;
 };
 
