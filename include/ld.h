@@ -203,6 +203,20 @@ int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, siz
 size_t ld_debug_size(ld_handle *h, int32_t stage);
 
 /*
+ * Lane drawing (Alg. 7, last step; Sec. 2.4): each selected lane traced by iterating Eq. 25 from its start
+ * (start_u, h-1) up to v_top, with the V_px and V_py rows of the handle's last single-size call, in the
+ * float32 operation order of the energy search (the rounded columns floor(u + 0.5) are the ones whose M_1
+ * the lane's energy summed).  lanes: DEVICE array of that call's results for its first n_frames frames
+ * (out_lanes of ld_detect, or of the learned form); tracks_out: DEVICE float32
+ * [n_frames][LD_MAX_LANES][h]: column u of lane k at row v, NaN above v_top and for k >= n_lanes (and for
+ * frames without a road or V_p fit).  The caller owns both; enqueued on the handle's stream.  The paper
+ * draws these curves on the image; here they are returned, headless.  Errors: LD_E_ARG (null buffer,
+ * n_frames outside [1, frames of the last call]), LD_E_STATE (no single-size call yet, or
+ * ld_detect_groups since), LD_E_CUDA.
+ */
+int ld_lane_tracks(ld_handle *h, const ld_lanes *lanes, int32_t n_frames, float *tracks_out);
+
+/*
  * Stage capture of the two intermediates the kernels keep on chip: m_x (Alg. 5, formed inside the V_px
  * DP kernel) and I^bf (Eq. 15-16, formed inside the gradient kernel).  With on != 0 the handle allocates
  * a capture buffer for max_batch frames (6 bytes per pixel) and every later call also writes both there,

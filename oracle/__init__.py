@@ -105,6 +105,7 @@ def lib():
         L.or_box_sobel.argtypes = [p, i32, i32, i32, i32, p, p]
         L.or_energy.argtypes = [p, i32, i32, i32, p, p, i32, i32, i32, p]
         L.or_select.argtypes = [p, i32, i32, C.POINTER(Params), C.POINTER(Lanes)]
+        L.or_track.argtypes = [p, p, i32, i32, i32, p]
         L.or_detect.argtypes = [p, p, i32, i32, C.POINTER(Params), C.POINTER(Lanes), C.POINTER(Dumps)]
         L.or_detect.restype = i32
         _lib = L
@@ -326,6 +327,15 @@ def select(he: np.ndarray, S0: int, p: Params | None = None):
     out = Lanes()
     lib().or_select(_ptr(h), len(h), S0, C.byref(p), C.byref(out))
     return lanes_dict(out)
+
+
+def track(vpx, vpy, v_top: int, start_u: int) -> np.ndarray:
+    """Alg. 7's drawing step: the Eq. 25 track of a lane started at (start_u, H-1), float32 [H], NaN above v_top."""
+    vx = np.ascontiguousarray(vpx, np.float32)
+    vy = np.ascontiguousarray(vpy, np.float32)
+    out = np.zeros(len(vx), np.float32)
+    lib().or_track(_ptr(vx), _ptr(vy), len(vx), v_top, start_u, _ptr(out))
+    return out
 
 
 def lanes_dict(out: Lanes) -> dict:

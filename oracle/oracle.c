@@ -677,6 +677,27 @@ void or_energy(const int32_t *m1, int32_t W, int32_t H, int32_t v_top, const flo
 }
 
 /* ------------------------------------------------------------------------------------------------ */
+/* Alg. 7, last step: a selected lane is drawn by iterating Eq. 25 from its start (s, H-1) up to v_top.  */
+/* u_out[v] is the track's column at row v in float32 with the operation order of or_energy (the     */
+/* positions whose rounded columns the lane's energy summed); rows above v_top get NaN.               */
+/* ------------------------------------------------------------------------------------------------ */
+void or_track(const float *Vpx, const float *Vpy, int32_t H, int32_t v_top, int32_t start_u, float *u_out)
+{
+    for (int32_t v = 0; v < H; v++)
+        u_out[v] = NAN;
+    float u = (float)start_u;
+    for (int32_t v = H - 1; v >= v_top && v >= 0; v--) {
+        if (v < H - 1) {
+            float vx = Vpx[v + 1], vy = Vpy[v + 1];
+            float num = (vx + (float)v * u) - vy * u;
+            float den = (float)(v + 1) - vy;
+            u = num / den;
+        }
+        u_out[v] = u;
+    }
+}
+
+/* ------------------------------------------------------------------------------------------------ */
 /* Alg. 7 selection: strict interior local minima of H whose energy is below t, then suppression of    */
 /* nearby minima.  Readings: t = ceil(thr * min H) (a fraction of the deepest minimum, since the       */
 /* energy scale depends on image contrast); candidates are taken in increasing (energy, position) and  */

@@ -120,6 +120,7 @@ void or_box_sobel(const int32_t *gw, int32_t W, int32_t H, int32_t nu, int32_t v
 void or_energy(const int32_t *m1, int32_t W, int32_t H, int32_t v_top, const float *Vpx, const float *Vpy,
                int32_t S0, int32_t n_starts, int32_t lambda_g, int64_t *he);
 void or_select(const int64_t *he, int32_t n_starts, int32_t S0, const or_params *p, or_lanes *out);
+void or_track(const float *Vpx, const float *Vpy, int32_t H, int32_t v_top, int32_t start_u, float *u_out);
 
 /* Sec. 2.1 stereo matching (the disparity the path takes as input).  Integral images are (W+1) x (H+1)
    with a zero first row and column; block statistics s (sum) and D = n Q - s^2 per pixel; maps int16. */

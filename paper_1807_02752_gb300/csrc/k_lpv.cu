@@ -380,6 +380,34 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const 
     }
 }
 
+// Alg. 7, last step: each selected lane drawn by iterating Eq. 25 from its start (s, H-1) up to v_top, in
+// the energy kernel's float32 operation order (so its rounded columns are the ones whose M_1 the lane's
+// energy summed).  One thread per lane slot of a frame; rows above v_top and empty slots get NaN.
+__global__ void __launch_bounds__(LD_MAX_LANES) k_tracks(const KParams kp, const Work w, const ld_lanes *lanes, float *out)
+{
+    const int f = blockIdx.x, k = threadIdx.x, H = kp.H;
+    float *o = out + ((size_t)f * LD_MAX_LANES + k) * H;
+    const ld_lanes &L = lanes[f];
+    const int vtop = L.v_top;
+    const bool on = k < L.n_lanes && !(L.flags & (LD_F_NO_ROAD | LD_F_DEGEN_Y | LD_F_DEGEN_X)) && vtop >= 0 && vtop < H;
+    const float *vpy = w.rows + (size_t)f * 3 * H + H, *vpx = vpy + H;
+    const float nanv = __int_as_float(0x7fc00000);
+    float u = on ? (float)L.start_u[k] : 0.0f;
+    for (int v = H - 1; v >= 0; --v) {
+        if (!on || v < vtop) {
+            o[v] = nanv;
+            continue;
+        }
+        if (v < H - 1) {
+            const float fv = (float)v, vx = vpx[v + 1], vy = vpy[v + 1];
+            const float num = __fsub_rn(__fadd_rn(vx, __fmul_rn(fv, u)), __fmul_rn(vy, u));
+            const float den = __fsub_rn(__fadd_rn(fv, 1.0f), vy);
+            u = __fdiv_rn(num, den);
+        }
+        o[v] = u;
+    }
+}
+
 }  // namespace
 
 cudaError_t setup_lpv(int smem_optin)
@@ -426,6 +454,12 @@ static cudaError_t select_mode(const KParams &kp, const Work &w, ld_lanes *out, 
 {
     const size_t smem = sizeof(int) * (size_t)(kp.n_starts + 4);
     k_select<<<kp.n_frames, kSelThreads, smem, s>>>(kp, w, out, cflag, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tracks(const KParams &kp, const Work &w, const ld_lanes *lanes, float *out, cudaStream_t s)
+{
+    k_tracks<<<kp.n_frames, LD_MAX_LANES, 0, s>>>(kp, w, lanes, out);
     return cudaGetLastError();
 }
 

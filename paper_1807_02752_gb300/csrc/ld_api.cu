@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ld_internal.cuh"
 
 static_assert(sizeof(ld_group) == 40, "C-ABI group layout");
@@ -296,6 +298,7 @@ int enqueue_range(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const 
             return cuda_fail(h, e, "edge count reset");
         if (k == 4 && w.dbg_mx && (e = cudaMemsetAsync(w.dbg_mx, 0, npx * 4, s)) != cudaSuccess)
             return cuda_fail(h, e, "capture reset");
+        nvtxRangePushA(kLaunchNames[k]);   // a profiler timeline shows each stage's enqueue by name
         switch (k) {
         case 0: e = ld::launch_vdisp(kp, w, disp, s); break;
         case 1: e = ld::launch_road(kp, w, s); break;
@@ -317,6 +320,7 @@ int enqueue_range(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const 
         case 7: e = ld::launch_energy(kp, w, s); break;
         default: e = ld::launch_select(kp, w, out, s); break;
         }
+        nvtxRangePop();
         if (e != cudaSuccess)
             return cuda_fail(h, e, kLaunchNames[k]);
         if (timed && (e = cudaEventRecord(h->ev[k + 1], s)) != cudaSuccess)
@@ -747,8 +751,27 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     return LD_OK;
 }
 
+}  // extern "C"
+namespace {
+int detect_call(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+                ld_lanes *out_lanes);
+}
+extern "C" {
+
 int ld_detect(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
               ld_lanes *out_lanes)
+{
+    nvtxRangePushA("ld_detect");
+    const int rc = detect_call(h, disp, img, w, hh, n_frames, out_lanes);
+    nvtxRangePop();
+    return rc;
+}
+
+}  // extern "C"
+
+namespace {
+int detect_call(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
+                ld_lanes *out_lanes)
 {
     int rc = check_call(h, disp, img, w, hh, n_frames, out_lanes);
     if (rc != LD_OK)
@@ -805,6 +828,9 @@ int ld_detect(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, in
     e = cudaGraphLaunch(exec, h->stream);
     return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
 }
+}  // namespace
+
+extern "C" {
 
 int ld_detect_groups(ld_handle *h, const ld_group *groups, int32_t n_groups)
 {
@@ -1049,6 +1075,21 @@ int ld_debug_get(ld_handle *h, int32_t frame, int32_t stage, void *host_dst, siz
     default: return fail(h, LD_E_ARG, "unknown stage");
     }
     return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "debug copy");
+}
+
+int ld_lane_tracks(ld_handle *h, const ld_lanes *lanes, int32_t n_frames, float *tracks_out)
+{
+    if (!h)
+        return LD_E_ARG;
+    if (!lanes || !tracks_out)
+        return fail(h, LD_E_ARG, "null buffer");
+    if (!h->have_last)
+        return fail(h, LD_E_STATE, "no single-size detection to trace (none yet, or ld_detect_groups since)");
+    if (n_frames < 1 || n_frames > h->last_n)
+        return fail(h, LD_E_ARG, "n_frames outside [1, frames of the last call]");
+    const ld::KParams kp = make_kparams(h, h->last_w, h->last_h, n_frames);
+    cudaError_t e = ld::launch_tracks(kp, h->w, lanes, tracks_out, h->stream);
+    return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "lane tracks");
 }
 
 int ld_debug_capture(ld_handle *h, int32_t on)

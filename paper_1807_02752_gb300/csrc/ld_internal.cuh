@@ -176,6 +176,7 @@ cudaError_t launch_vpx(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_energy(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_select(const KParams &kp, const Work &w, ld_lanes *out, cudaStream_t s);
+cudaError_t launch_tracks(const KParams &kp, const Work &w, const ld_lanes *lanes, float *out, cudaStream_t s);
 // learned proposal: energies of the listed starts / selection among the candidates (frames without a lane
 // are flagged LD_F_FALLBACK), then the exhaustive energies and selection of the flagged frames only
 cudaError_t launch_energy_list(const KParams &kp, const Work &w, const int32_t *elist, const int32_t *ecnt, int ecap,

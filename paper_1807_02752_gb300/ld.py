@@ -107,6 +107,8 @@ def load():
     L.ld_debug_get.restype = C.c_int
     L.ld_debug_size.argtypes = [p, i32]
     L.ld_debug_size.restype = C.c_size_t
+    L.ld_lane_tracks.argtypes = [p, p, i32, p]
+    L.ld_lane_tracks.restype = C.c_int
     L.ld_debug_capture.argtypes = [p, i32]
     L.ld_debug_capture.restype = C.c_int
     L.ld_tables.argtypes = [P, p, p, p]
@@ -189,7 +191,7 @@ def load():
 
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
-            "ld_debug_get", "ld_debug_size", "ld_debug_capture", "ld_tables", "ld_flat_range", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
+            "ld_debug_get", "ld_debug_size", "ld_debug_capture", "ld_lane_tracks", "ld_tables", "ld_flat_range", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
             "ld_destroy", "ld_road_path_static", "ld_tune", "ld_detect_groups", "ld_server_create", "ld_server_submit", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_server_set_learned", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
@@ -362,6 +364,15 @@ class Detector:
         if stage == STAGE_IBF:
             return buf.view(np.int16).reshape(H, W)
         return buf
+
+    def lane_tracks(self, out, n: int, H: int):
+        """Eq. 25 tracks of the selected lanes of the last call's first n frames (out: that call's device
+        result buffer).  Returns a device float32 tensor [n][LD_MAX_LANES][H], NaN where no lane is."""
+        import torch
+
+        tr = torch.empty((n, MAX_LANES, H), dtype=torch.float32, device="cuda")
+        self._check(self.L.ld_lane_tracks(self.h, out.data_ptr(), n, tr.data_ptr()))
+        return tr
 
     def capture(self, on: bool = True):
         """Record m_x and I^bf on later calls (LD_STAGE_MX / LD_STAGE_IBF); allocates a capture buffer."""

@@ -229,3 +229,33 @@ def test_tuning_keeps_results(torch_cuda):
     assert before[0] == after[0]
     for a, b in zip(before[1], after[1]):
         assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+@pytest.mark.parametrize("name,n", [("single_1242x375", 2), ("batch64_1242x375", 64), ("batch16_1920x1080", 2)])
+def test_lane_tracks_match_oracle(torch_cuda, name, n):
+    """Alg. 7's drawing step (ld_lane_tracks): every selected lane's Eq. 25 track, bit-exact against the
+    oracle's track on the oracle's V_p rows, NaN above v_top and in empty lane slots."""
+    import oracle
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS[name]
+    disp, img, _ = scenes.make_batch(cfg, n)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    det = ld.Detector(cfg.width, cfg.height, n, p)
+    d = torch.from_numpy(disp).cuda()
+    i = torch.from_numpy(img).cuda()
+    out = det.detect(d, i)
+    tr = det.lane_tracks(out, n, cfg.height)
+    torch.cuda.synchronize()
+    tr = tr.cpu().numpy()
+    for f in ((0, 1) if n <= 2 else (0, 9, 40, 63)):
+        ref = oracle.detect(disp[f], img[f], oracle_params(p))
+        for k in range(ld.MAX_LANES):
+            if k < ref["n_lanes"]:
+                want = oracle.track(ref["Vpx"], ref["Vpy"], ref["v_top"], ref["start_u"][k])
+                assert np.array_equal(tr[f, k], want, equal_nan=True), f"frame {f} lane {k}"
+            else:
+                assert np.isnan(tr[f, k]).all()
+    with pytest.raises(ld.LDError) as e:
+        det.lane_tracks(out, n + 1, cfg.height)
+    assert e.value.code == ld.E_ARG
+    det.close()

@@ -361,3 +361,56 @@ def test_selection_properties_on_random_histograms(oracle_mod):
         if acc:
             best = min(cand, key=lambda i: (he[i], i))
             assert best in acc
+
+
+# ---------------------------------------------------------------------------------------------- Alg. 7 drawing
+def test_track_is_exact_on_straight_lanes(oracle_mod):
+    """Flat road, constant V_p: every Eq. 25 step lands on the straight line through (s, H-1) and V_p."""
+    H, vh, vp = 120, 40.0, 150.0
+    vpx = np.full(H, vp, np.float32)
+    vpy = np.full(H, vh, np.float32)
+    for s in (-30, 12, 150, 290, 400):
+        u = oracle_mod.track(vpx, vpy, 41, s)
+        v = np.arange(H, dtype=np.float64)
+        line = vp + (s - vp) * (v - vh) / (H - 1 - vh)
+        assert np.isnan(u[:41]).all()
+        assert np.allclose(u[41:], line[41:], atol=1e-3 * max(1, abs(s - vp)) + 1e-3)
+
+
+def test_track_follows_planted_lanes(oracle_mod):
+    """The planted lanes are field lines of the planted V_p (Eq. 14, Eq. 25): the track from a planted start,
+    stepped on the planted V_p rows, stays within half a pixel of the lane curve on every road row."""
+    cfg = scenes.SINGLE_1242x375
+    H = cfg.height
+    for fr in range(4):
+        _, _, t = scenes.make_frame(cfg, fr)
+        vt = int(np.ceil(t.v_horizon)) + 1
+        vpx = np.where(np.isnan(t.vpx), 0, t.vpx).astype(np.float32)
+        vpy = np.where(np.isnan(t.vpy), 0, t.vpy).astype(np.float32)
+        fm = np.polyval(t.beta[::-1], H - 1)
+        v = np.arange(vt, H)
+        f = np.polyval(t.beta[::-1], v)
+        for s in t.lane_starts:
+            si = (s - t.alpha[0] - t.alpha[2] * fm * fm) / fm - t.alpha[1]
+            lane = t.alpha[0] + (t.alpha[1] + si) * f + t.alpha[2] * f * f
+            u = oracle_mod.track(vpx, vpy, vt, int(round(s)))
+            # the start is rounded to a column: the offset scales with f along the field line
+            assert np.abs(u[vt:] - (lane + (round(s) - s) * f / fm)).max() < 0.5
+
+
+def test_track_energy_is_the_histogram_entry(oracle_mod):
+    """Summing M_1 at the rounded track columns gives the start's entry of the energy histogram."""
+    cfg = scenes.SINGLE_1242x375
+    disp, img, _ = scenes.make_frame(cfg, 2)
+    p = oracle_mod.default_params(n_disp=cfg.n_disp)
+    r = oracle_mod.detect(disp, img, p)
+    W, H = cfg.width, cfg.height
+    S0 = (oracle_mod.n_starts(W, p) - W) // 2
+    for s in list(r["start_u"]) + [-100, 7, 600, 1500]:
+        u = oracle_mod.track(r["Vpx"], r["Vpy"], r["v_top"], int(s))
+        e = 0
+        for v in range(r["v_top"], H):
+            c = np.floor(np.float32(u[v]) + np.float32(0.5))
+            if 0 <= c < W:
+                e += int(r["M1"][v, int(c)])
+        assert e == int(r["HE"][int(s) + S0])
