@@ -166,6 +166,24 @@ typedef struct ld_group {
 int ld_detect_groups(ld_handle *h, const ld_group *groups, int32_t n_groups);
 
 /*
+ * Frames of several sizes in one launch per stage and half.  The same group list, workspace views and
+ * results as ld_detect_groups, but the groups are split into two halves (by pixel count, largest first,
+ * each to the half with fewer pixels so far; a single group by alternate frames) that run on two streams
+ * forked from the handle's, and each of the nine stages is one kernel launch over every frame of a half,
+ * whatever the sizes of its groups: a CTA
+ * reads its frame's descriptor (the frame's size, start range and polynomial basis, its workspace view
+ * and its buffers; built on the host and kept on the device with the captured graph) and returns when its
+ * tile lies outside that frame, the grids and shared memory being sized for the list's largest frame.  The
+ * tile shapes are the built-in ones (ld_tune tunes one size).  On a stream of the handle's own the call is
+ * captured as one CUDA graph per group list (the descriptors are uploaded, with a wait for the stream,
+ * when a list is first seen) and replayed when the list comes back; on the legacy default stream, or
+ * inside the caller's capture, the groups are enqueued one after another as ld_detect_groups does, with
+ * the same results.  ld_debug_get reports on no frame of it.  The paper processes one frame at a time and
+ * has no counterpart.  Errors as ld_detect_groups.
+ */
+int ld_detect_mixed(ld_handle *h, const ld_group *groups, int32_t n_groups);
+
+/*
  * Same as ld_detect with HOST buffers: copies the inputs to device staging owned by the handle, runs the
  * path, copies the results to out_lanes (host, n_frames entries) and waits for the stream.  Page-locked
  * (pinned) inputs give the fastest copies.  Errors as ld_detect.

@@ -119,10 +119,10 @@ __device__ __forceinline__ void atoms_add(uint32_t a, int v) { asm volatile("red
 // k_road_dp
 // ---------------------------------------------------------------------------------------------------
 template <int TMAX>
-__global__ void __launch_bounds__(1024) k_road_dp(const KParams kp, const Work w)
+__device__ __forceinline__ void road_dp_body(const KParams &kp, const Work &w, const int f)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int f = blockIdx.x, H = kp.H, D = kp.D, Hp = (H + 1) >> 1;  // Hp: pairs of rows
+    const int H = kp.H, D = kp.D, Hp = (H + 1) >> 1;  // Hp: pairs of rows
     const int tid = threadIdx.x, nt = blockDim.x;
     const int32_t *my = w.myT + (size_t)f * D * H;
 
@@ -241,6 +241,17 @@ __global__ void __launch_bounds__(1024) k_road_dp(const KParams kp, const Work w
         w.npts[f * 2] = k;
 }
 
+template <int TMAX>
+__global__ void __launch_bounds__(1024) k_road_dp(const KParams kp, const Work w) { road_dp_body<TMAX>(kp, w, blockIdx.x); }
+template <int TMAX>
+__global__ void __launch_bounds__(1024) k_road_dp_fd(const FrameDesc *__restrict__ fd)
+{
+    const FrameDesc &d = fd[blockIdx.x];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    road_dp_body<TMAX>(kp, w, 0);
+}
+
 // ---------------------------------------------------------------------------------------------------
 // k_road_dp_lit: Eq. 12 as printed (dp_literal), for A/B against the reading above:
 //   E_d(v) = -m_y(d, v) + min_{tau in [0, tau_y], v - tau >= 0} [E_{d+1}(v - tau) - lambda_y tau],
@@ -248,10 +259,10 @@ __global__ void __launch_bounds__(1024) k_road_dp(const KParams kp, const Work w
 // per-row loops (a thread per pair of rows, 4-bit backtrack entries of the pair in one byte); the same
 // shared-memory layout and outputs as k_road_dp.
 // ---------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_road_dp_lit(const KParams kp, const Work w)
+__device__ __forceinline__ void road_dp_lit_body(const KParams &kp, const Work &w, const int f)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int f = blockIdx.x, H = kp.H, D = kp.D, Hp = (H + 1) >> 1;
+    const int H = kp.H, D = kp.D, Hp = (H + 1) >> 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int32_t *my = w.myT + (size_t)f * D * H;
     unsigned char *p = smem;
@@ -322,6 +333,15 @@ __global__ void __launch_bounds__(1024) k_road_dp_lit(const KParams kp, const Wo
     }
     if (tid == 0)
         w.npts[f * 2] = k;
+}
+
+__global__ void __launch_bounds__(1024) k_road_dp_lit(const KParams kp, const Work w) { road_dp_lit_body(kp, w, blockIdx.x); }
+__global__ void __launch_bounds__(1024) k_road_dp_lit_fd(const FrameDesc *__restrict__ fd)
+{
+    const FrameDesc &d = fd[blockIdx.x];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    road_dp_lit_body(kp, w, 0);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -657,10 +677,10 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
 }
 
 template <int TAU, int NP>
-__global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
+__device__ __forceinline__ void vpx_dp_kernel_body(const KParams &kp, const Work &w, const int f)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int f = blockIdx.x, W = kp.W, H = kp.H, NPr = vpx_pairs(W);
+    const int W = kp.W, H = kp.H, NPr = vpx_pairs(W);
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const FrameState fs0 = w.fs[f];
     if (fs0.flags & LD_F_NO_LANES)
@@ -791,6 +811,17 @@ __global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w)
         w.npts[f * 2 + 1] = k;
 }
 
+template <int TAU, int NP>
+__global__ void __launch_bounds__(1024) k_vpx_dp(const KParams kp, const Work w) { vpx_dp_kernel_body<TAU, NP>(kp, w, blockIdx.x); }
+template <int TAU, int NP>
+__global__ void __launch_bounds__(1024) k_vpx_dp_fd(const FrameDesc *__restrict__ fd)
+{
+    const FrameDesc &d = fd[blockIdx.x];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    vpx_dp_kernel_body<TAU, NP>(kp, w, 0);
+}
+
 // Threads: one per cell pair up to 1024 (two pairs per thread past 2048 columns).
 int vpx_np(int W) { return vpx_pairs(W) > 1024 ? 2 : 1; }
 int vpx_threads(int W)
@@ -842,6 +873,23 @@ VpxKernel vpx_kernel_np(int tau)
 }
 VpxKernel vpx_kernel(int tau, int W) { return vpx_np(W) == 2 ? vpx_kernel_np<2>(tau) : vpx_kernel_np<1>(tau); }
 
+using VpxKernelFd = void (*)(const FrameDesc *);
+template <int NP>
+VpxKernelFd vpx_kernel_fd_np(int tau)
+{
+    switch (tau) {
+    case 0: return k_vpx_dp_fd<0, NP>;
+    case 1: return k_vpx_dp_fd<1, NP>;
+    case 2: return k_vpx_dp_fd<2, NP>;
+    case 3: return k_vpx_dp_fd<3, NP>;
+    case 4: return k_vpx_dp_fd<4, NP>;
+    case 5: return k_vpx_dp_fd<5, NP>;
+    case 6: return k_vpx_dp_fd<6, NP>;
+    default: return k_vpx_dp_fd<7, NP>;
+    }
+}
+VpxKernelFd vpx_kernel_fd(int tau, int W) { return vpx_np(W) == 2 ? vpx_kernel_fd_np<2>(tau) : vpx_kernel_fd_np<1>(tau); }
+
 using RoadKernel = void (*)(KParams, Work);
 RoadKernel road_kernel(int tau) { return tau <= 6 ? k_road_dp<6> : k_road_dp<15>; }
 
@@ -890,7 +938,17 @@ cudaError_t setup_dp(int smem_optin)
         e = allow_max_smem(vpx_kernel_np<1>(t), smem_optin);
         if (e == cudaSuccess)
             e = allow_max_smem(vpx_kernel_np<2>(t), smem_optin);
+        if (e == cudaSuccess)
+            e = allow_max_smem(vpx_kernel_fd_np<1>(t), smem_optin);
+        if (e == cudaSuccess)
+            e = allow_max_smem(vpx_kernel_fd_np<2>(t), smem_optin);
     }
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_road_dp_fd<6>, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_road_dp_fd<15>, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_road_dp_lit_fd, smem_optin);
     return e;
 }
 
@@ -900,6 +958,23 @@ cudaError_t launch_road(const KParams &kp, const Work &w, cudaStream_t s)
         k_road_dp_lit<<<kp.n_frames, road_threads(kp.H), road_smem_bytes(kp), s>>>(kp, w);
     else
         road_kernel(kp.tau_y)<<<kp.n_frames, road_threads(kp.H), road_smem_bytes(kp), s>>>(kp, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_road_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
+{
+    if (kmax.dp_literal)
+        k_road_dp_lit_fd<<<n, road_threads(kmax.H), road_smem_bytes(kmax), s>>>(fd);
+    else if (kmax.tau_y <= 6)
+        k_road_dp_fd<6><<<n, road_threads(kmax.H), road_smem_bytes(kmax), s>>>(fd);
+    else
+        k_road_dp_fd<15><<<n, road_threads(kmax.H), road_smem_bytes(kmax), s>>>(fd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vpx_fd(const KParams &kmax, const FrameDesc *fd, int n, size_t smem, cudaStream_t s)
+{
+    vpx_kernel_fd(kmax.tau_x, kmax.W)<<<n, vpx_threads(kmax.W), smem, s>>>(fd);
     return cudaGetLastError();
 }
 

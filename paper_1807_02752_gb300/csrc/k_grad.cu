@@ -168,14 +168,16 @@ __host__ __device__ inline GradTile grad_tile(int nr, int nj, int n_cls)
 }
 
 template <int RHO>
-__global__ void __launch_bounds__(kThreads, 4) k_grad(const KParams kp, const Work w, const float *__restrict__ disp,
-                                                   const uint8_t *__restrict__ img, int R)
+// filter: apply Eq. 15-16 (0: the image is used as it is, the median pre-filter's output or bilateral = 0)
+__device__ __forceinline__ void grad_body(const KParams &kp, const Work &w, const float *__restrict__ disp,
+                                          const uint8_t *__restrict__ img, int R, const int f, const int bx, const int by,
+                                          const bool filter)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NW = kThreads / 32;
     const int W = kp.W, H = kp.H, NG = (W + 3) >> 2;
-    const int f = blockIdx.z, r0 = blockIdx.y * R, nr = min(R, H - r0);
-    const int j0 = blockIdx.x * kGroups, nj = min(kGroups, NG - j0);
+    const int r0 = by * R, nr = min(R, H - r0);
+    const int j0 = bx * kGroups, nj = min(kGroups, NG - j0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const FrameState &fs = w.fs[f];
     const int vtop = fs.v_top;
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_grad(const KParams kp, const Wo
         const int nv = min(4, W - u0);
         uint32_t out;
         // the group's windows start at tile row b (frame row v - RHO) and tile column 4 g (frame column u0 - RHO)
-        if (kp.bilateral) {
+        if (filter) {
             out = bilateral4<RHO>(kp, tile, T.TWP, b, 4 * g, nv, tab);
         } else {
             const uint16_t *c = tile + (b + RHO) * T.TWP + 4 * g + RHO;
@@ -396,6 +398,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_grad(const KParams kp, const Wo
         }
 }
 
+template <int RHO>
+__global__ void __launch_bounds__(kThreads, 4) k_grad(const KParams kp, const Work w, const float *__restrict__ disp,
+                                                   const uint8_t *__restrict__ img, int R)
+{
+    grad_body<RHO>(kp, w, disp, img, R, blockIdx.z, blockIdx.x, blockIdx.y, kp.bilateral != 0);
+}
+
+// median_input: the frame's image is its median-filtered copy in the workspace (bilateral = 2)
+template <int RHO>
+__global__ void __launch_bounds__(kThreads, 4) k_grad_fd(const FrameDesc *__restrict__ fd, int R, int median_input)
+{
+    const FrameDesc &d = fd[blockIdx.z];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    if ((int)blockIdx.y * R >= kp.H || (int)blockIdx.x * kGroups >= (kp.W + 3) / 4)
+        return;
+    grad_body<RHO>(kp, w, d.disp, median_input ? w.med : d.img, R, 0, blockIdx.x, blockIdx.y,
+                   !median_input && kp.bilateral != 0);
+}
+
 // Rows per CTA: the tuned value when set, else 16.
 template <int RHO>
 int grad_rows(int tuned)
@@ -414,7 +436,29 @@ cudaError_t launch_grad_t(const KParams &kp, const Work &w, const float *disp, c
     return cudaGetLastError();
 }
 
+template <int RHO>
+cudaError_t launch_grad_fd_t(const KParams &kmax, const FrameDesc *fd, int n, bool median_input, cudaStream_t s)
+{
+    const int R = grad_rows<RHO>(0);
+    const int NG = (kmax.W + 3) / 4, nj = NG < kGroups ? NG : kGroups;
+    const size_t smem = grad_tile<RHO>(R, nj, kmax.n_cls).bytes;
+    dim3 grid((NG + kGroups - 1) / kGroups, (kmax.H + R - 1) / R, n);
+    k_grad_fd<RHO><<<grid, kThreads, smem, s>>>(fd, R, median_input ? 1 : 0);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_grad_fd(const KParams &kmax, const FrameDesc *fd, int n, bool median_input, cudaStream_t s)
+{
+    switch (kmax.rho) {
+    case 1: return launch_grad_fd_t<1>(kmax, fd, n, median_input, s);
+    case 2: return launch_grad_fd_t<2>(kmax, fd, n, median_input, s);
+    case 3: return launch_grad_fd_t<3>(kmax, fd, n, median_input, s);
+    case 4: return launch_grad_fd_t<4>(kmax, fd, n, median_input, s);
+    default: return launch_grad_fd_t<5>(kmax, fd, n, median_input, s);
+    }
+}
 
 cudaError_t setup_grad(int smem_optin)
 {
@@ -429,6 +473,16 @@ cudaError_t setup_grad(int smem_optin)
         e = allow_max_smem(k_grad<4>, smem_optin);
     if (e == cudaSuccess)
         e = allow_max_smem(k_grad<5>, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_grad_fd<1>, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_grad_fd<2>, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_grad_fd<3>, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_grad_fd<4>, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_grad_fd<5>, smem_optin);
     return e;
 }
 

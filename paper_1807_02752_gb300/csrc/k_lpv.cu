@@ -60,13 +60,12 @@ inline M1Layout m1_layout(int W, int vs, int tuned)
     return L;
 }
 
-__global__ void __launch_bounds__(kM1Threads, 2) k_m1(const KParams kp, const Work w, int R, int Wc)
+__device__ __forceinline__ void m1_body(const KParams &kp, const Work &w, int R, int Wc, const int f, int tile)
 {
     extern __shared__ __align__(16) int32_t dd[];   // [nr + 2 + 2 varsigma][Wc]: rows r0-1-varsigma ..
     __shared__ int32_t eoff[kM1MaxEdgeRows + 1];
     const int W = kp.W, H = kp.H;
-    const int f = blockIdx.y;
-    const int r0 = blockIdx.x * R;
+    const int r0 = tile * R;
     const int nr = min(R, H - r0);
     const FrameState &fs = w.fs[f];
     const int vtop = fs.v_top, vmax = H - 1;
@@ -182,25 +181,37 @@ __global__ void __launch_bounds__(kM1Threads, 2) k_m1(const KParams kp, const Wo
     }
 }
 
+__global__ void __launch_bounds__(kM1Threads, 2) k_m1(const KParams kp, const Work w, int R, int Wc)
+{
+    m1_body(kp, w, R, Wc, blockIdx.y, blockIdx.x);
+}
+__global__ void __launch_bounds__(kM1Threads, 2) k_m1_fd(const FrameDesc *__restrict__ fd, int R, int Wc)
+{
+    const FrameDesc &d = fd[blockIdx.y];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    if ((int)blockIdx.x * R >= kp.H)
+        return;
+    m1_body(kp, w, R, Wc, 0, blockIdx.x);
+}
+
 // MODE 0: every start of every frame; 1: the starts listed per frame (learned proposal); 2: every start of
 // the frames flagged LD_F_FALLBACK (the proposal selected no lane there).
 // A short list (MODE 1) is latency-bound: each start is a serial chain of divisions and gathers, so the
 // list form issues the M_1 loads of 32 rows at a time instead of 8 (fewer dependent round trips).
 template <int MODE>
-__global__ void __launch_bounds__(kEnThreads, MODE == 1 ? 2 : 8) k_energy(const KParams kp, const Work w,
-                                                                         const int32_t *elist, const int32_t *ecnt,
-                                                                         int ecap)
+__device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, const int32_t *elist, const int32_t *ecnt,
+                                            int ecap, const int f, const int tile)
 {
     constexpr int kEnBatch = MODE == 1 ? 32 : kEnBatchDefault;
     extern __shared__ float vrow[];   // [2][H]: V_px, V_py
     const int W = kp.W, H = kp.H;
-    const int f = blockIdx.y;
     const FrameState &fs = w.fs[f];
     if (fs.flags & LD_F_NO_LANES)
         return;
     if (MODE == 2 && !(fs.flags & LD_F_FALLBACK))
         return;
-    if (MODE == 1 && blockIdx.x * kEnThreads >= ecnt[f])
+    if (MODE == 1 && tile * kEnThreads >= ecnt[f])
         return;
     const int vtop = fs.v_top, vmax = H - 1;
     const float *rows = w.rows + (size_t)f * 3 * H;
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(kEnThreads, MODE == 1 ? 2 : 8) k_energy(const 
         vrow[H + v] = rows[H + v];
     }
     __syncthreads();
-    int i = blockIdx.x * kEnThreads + threadIdx.x;
+    int i = tile * kEnThreads + threadIdx.x;
     if (MODE == 1) {
         if (i >= ecnt[f])
             return;
@@ -262,17 +273,34 @@ __global__ void __launch_bounds__(kEnThreads, MODE == 1 ? 2 : 8) k_energy(const 
     w.HE[(size_t)f * kp.n_starts + i] = (int64_t)E;
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(kEnThreads, MODE == 1 ? 2 : 8) k_energy(const KParams kp, const Work w,
+                                                                         const int32_t *elist, const int32_t *ecnt,
+                                                                         int ecap)
+{
+    energy_body<MODE>(kp, w, elist, ecnt, ecap, blockIdx.y, blockIdx.x);
+}
+__global__ void __launch_bounds__(kEnThreads, 8) k_energy_fd(const FrameDesc *__restrict__ fd)
+{
+    const FrameDesc &d = fd[blockIdx.y];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    if ((int)blockIdx.x * kEnThreads >= kp.n_starts)
+        return;
+    energy_body<0>(kp, w, nullptr, nullptr, 0, 0, blockIdx.x);
+}
+
 // mode 0: every start; 1: minima only at candidate starts (cflag bit 0), minimum over the evaluated ones
 // (bit 1), and a frame without a lane is flagged LD_F_FALLBACK; 2: the flagged frames only, every start.
-__global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const Work w, ld_lanes *out,
-                                                        const uint8_t *cflag, int mode)
+__device__ __forceinline__ void select_body(const KParams &kp, const Work &w, ld_lanes *out, const uint8_t *cflag,
+                                            int mode, const int f)
 {
     extern __shared__ int cand[];     // [n_starts / 2 + 2] candidate positions, then their sorted order
     __shared__ long long red[kSelThreads / 32];
     __shared__ int ncand;
     __shared__ int acc[LD_MAX_LANES];
     __shared__ int nacc;
-    const int f = blockIdx.x, ns = kp.n_starts;
+    const int ns = kp.n_starts;
     const int tid = threadIdx.x;
     const FrameState fs = w.fs[f];
     if (mode == 2 && !(fs.flags & LD_F_FALLBACK))
@@ -380,6 +408,19 @@ __global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const 
     }
 }
 
+__global__ void __launch_bounds__(kSelThreads) k_select(const KParams kp, const Work w, ld_lanes *out,
+                                                        const uint8_t *cflag, int mode)
+{
+    select_body(kp, w, out, cflag, mode, blockIdx.x);
+}
+__global__ void __launch_bounds__(kSelThreads) k_select_fd(const FrameDesc *__restrict__ fd)
+{
+    const FrameDesc &d = fd[blockIdx.x];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    select_body(kp, w, d.out, nullptr, 0, 0);
+}
+
 // Alg. 7, last step: each selected lane drawn by iterating Eq. 25 from its start (s, H-1) up to v_top, in
 // the energy kernel's float32 operation order (so its rounded columns are the ones whose M_1 the lane's
 // energy summed).  One thread per lane slot of a frame; rows above v_top and empty slots get NaN.
@@ -415,6 +456,12 @@ cudaError_t setup_lpv(int smem_optin)
     cudaError_t e = allow_max_smem(k_m1, smem_optin);
     if (e == cudaSuccess)
         e = allow_max_smem(k_select, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_m1_fd, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_select_fd, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_energy_fd, smem_optin);
     return e;
 }
 
@@ -424,6 +471,28 @@ cudaError_t launch_m1(const KParams &kp, const Work &w, cudaStream_t s)
     const size_t smem = sizeof(int32_t) * (size_t)(L.R + 2 + 2 * kp.box_vs) * L.Wc;
     dim3 grid((kp.H + L.R - 1) / L.R, kp.n_frames);
     k_m1<<<grid, kM1Threads, smem, s>>>(kp, w, L.R, L.Wc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m1_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
+{
+    const M1Layout L = m1_layout(kmax.W, kmax.box_vs, 0);
+    const size_t smem = sizeof(int32_t) * (size_t)(L.R + 2 + 2 * kmax.box_vs) * L.Wc;
+    dim3 grid((kmax.H + L.R - 1) / L.R, n);
+    k_m1_fd<<<grid, kM1Threads, smem, s>>>(fd, L.R, L.Wc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
+{
+    dim3 grid((kmax.n_starts + kEnThreads - 1) / kEnThreads, n);
+    k_energy_fd<<<grid, kEnThreads, sizeof(float) * 2 * kmax.H, s>>>(fd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
+{
+    k_select_fd<<<n, kSelThreads, sizeof(int) * (size_t)(kmax.n_starts + 4), s>>>(fd);
     return cudaGetLastError();
 }
 

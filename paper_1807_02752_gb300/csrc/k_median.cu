@@ -15,11 +15,12 @@ namespace {
 
 constexpr int kMedRows = 8, kMedCols = 32, kMedMaxRho = 5;
 
-__global__ void __launch_bounds__(kMedRows * kMedCols) k_median(const KParams kp, const Work w, const uint8_t *img)
+__device__ __forceinline__ void median_body(const KParams &kp, const Work &w, const uint8_t *img, const int f,
+                                            const int bx, const int by)
 {
     __shared__ uint8_t tile[(kMedRows + 2 * kMedMaxRho) * (kMedCols + 2 * kMedMaxRho)];
-    const int W = kp.W, H = kp.H, rho = kp.rho, f = blockIdx.z;
-    const int x0 = blockIdx.x * kMedCols, y0 = blockIdx.y * kMedRows;
+    const int W = kp.W, H = kp.H, rho = kp.rho;
+    const int x0 = bx * kMedCols, y0 = by * kMedRows;
     const int u = x0 + (threadIdx.x & (kMedCols - 1)), v = y0 + threadIdx.x / kMedCols;
     const uint8_t *in = img + (size_t)f * H * W;
     uint8_t *out = w.med + (size_t)f * H * W;
@@ -61,7 +62,28 @@ __global__ void __launch_bounds__(kMedRows * kMedCols) k_median(const KParams kp
     out[(size_t)v * W + u] = (uint8_t)m;
 }
 
+__global__ void __launch_bounds__(kMedRows * kMedCols) k_median(const KParams kp, const Work w, const uint8_t *img)
+{
+    median_body(kp, w, img, blockIdx.z, blockIdx.x, blockIdx.y);
+}
+__global__ void __launch_bounds__(kMedRows * kMedCols) k_median_fd(const FrameDesc *__restrict__ fd)
+{
+    const FrameDesc &d = fd[blockIdx.z];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    if ((int)blockIdx.x * kMedCols >= kp.W || (int)blockIdx.y * kMedRows >= kp.H)
+        return;
+    median_body(kp, w, d.img, 0, blockIdx.x, blockIdx.y);
+}
+
 }  // namespace
+
+cudaError_t launch_median_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
+{
+    dim3 grid((kmax.W + kMedCols - 1) / kMedCols, (kmax.H + kMedRows - 1) / kMedRows, n);
+    k_median_fd<<<grid, kMedRows * kMedCols, 0, s>>>(fd);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_median(const KParams &kp, const Work &w, const uint8_t *img, cudaStream_t s)
 {

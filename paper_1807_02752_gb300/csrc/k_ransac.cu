@@ -211,13 +211,13 @@ __device__ __forceinline__ bool newton_inlier(const float *c, const float *nodes
 }
 
 template <int M>
-__global__ void __launch_bounds__(kFitThreads) k_fit(const KParams kp, const Work w)
+__device__ __forceinline__ void fit_body(const KParams &kp, const Work &w, const int f)
 {
     constexpr int stage = M == 3 ? 0 : 1;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double coef_s[M];
     __shared__ int sh[4];
-    const int f = blockIdx.x, H = kp.H, P = w.pmax;
+    const int H = kp.H, P = w.pmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const FrameState fs0 = w.fs[f];
     if (stage == 1 && (fs0.flags & LD_F_NO_LANES))
@@ -509,6 +509,17 @@ __global__ void __launch_bounds__(kFitThreads) k_fit(const KParams kp, const Wor
 }
 
 template <int M>
+__global__ void __launch_bounds__(kFitThreads) k_fit(const KParams kp, const Work w) { fit_body<M>(kp, w, blockIdx.x); }
+template <int M>
+__global__ void __launch_bounds__(kFitThreads) k_fit_fd(const FrameDesc *__restrict__ fd)
+{
+    const FrameDesc &d = fd[blockIdx.x];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    fit_body<M>(kp, w, 0);
+}
+
+template <int M>
 size_t fit_smem(int P)
 {
     size_t s = 0;
@@ -533,6 +544,10 @@ cudaError_t setup_ransac(int smem_optin)
 {
     cudaError_t e = allow_max_smem(k_fit<3>, smem_optin);
     if (e == cudaSuccess)
+        e = allow_max_smem(k_fit_fd<3>, smem_optin);
+    if (e == cudaSuccess)
+        e = allow_max_smem(k_fit_fd<5>, smem_optin);
+    if (e == cudaSuccess)
         e = allow_max_smem(k_fit<5>, smem_optin);
     return e;
 }
@@ -540,6 +555,18 @@ cudaError_t setup_ransac(int smem_optin)
 cudaError_t launch_fit_y(const KParams &kp, const Work &w, cudaStream_t s)
 {
     k_fit<3><<<kp.n_frames, kFitThreads, fit_smem<3>(w.pmax), s>>>(kp, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_y_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
+{
+    k_fit_fd<3><<<n, kFitThreads, fit_smem<3>(kmax.pmax_hint), s>>>(fd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_x_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
+{
+    k_fit_fd<5><<<n, kFitThreads, fit_smem<5>(kmax.pmax_hint), s>>>(fd);
     return cudaGetLastError();
 }
 

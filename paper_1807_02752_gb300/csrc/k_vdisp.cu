@@ -34,13 +34,13 @@ __device__ __forceinline__ void red_add_if(bool p, uint32_t a, int v)
                  "r"((int)p));
 }
 
-__global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *__restrict__ myT,
-                                                    const float *__restrict__ disp, int kRows)
+// Rows [tile * kRows, ..) of frame f.
+__device__ __forceinline__ void vdisp_body(const KParams &kp, int32_t *__restrict__ myT, const float *__restrict__ disp,
+                                           int kRows, int f, int tile)
 {
     extern __shared__ int32_t hist[];  // [kRows][D + 1]
     const int W = kp.W, H = kp.H, D = kp.D, Dp = D + 1;
-    const int f = blockIdx.y;
-    const int r0 = blockIdx.x * kRows;
+    const int r0 = tile * kRows;
     const int nr = min(kRows, H - r0);
     const int tid = threadIdx.x;
     for (int i = tid; i < kRows * Dp; i += kThreads)
@@ -113,6 +113,22 @@ __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *_
         for (int d = tid / nr; d < D; d += step)
             dst[(size_t)d * H + r0 + r] = hist[r * Dp + d];
 }
+
+__global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *__restrict__ myT,
+                                                    const float *__restrict__ disp, int kRows)
+{
+    vdisp_body(kp, myT, disp, kRows, blockIdx.y, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kThreads) k_vdisp_fd(const FrameDesc *__restrict__ fd, int kRows)
+{
+    const FrameDesc &d = fd[blockIdx.y];
+    const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
+    const Work w = d.w;
+    if ((int)blockIdx.x * kRows >= kp.H)
+        return;
+    vdisp_body(kp, w.myT, d.disp, kRows, 0, blockIdx.x);
+}
 }  // namespace
 
 // Rows per CTA: the tuned value when set, at most one per thread (the write-out gives each row at least
@@ -131,6 +147,14 @@ cudaError_t launch_vdisp(const KParams &kp, const Work &w, const float *disp, cu
     dim3 grid((kp.H + kRows - 1) / kRows, kp.n_frames);
     const size_t smem = sizeof(int32_t) * kRows * (kp.D + 1);
     k_vdisp<<<grid, kThreads, smem, s>>>(kp, w.myT, disp, kRows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vdisp_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
+{
+    const int kRows = vdisp_rows(kmax);
+    dim3 grid((kmax.H + kRows - 1) / kRows, n);
+    k_vdisp_fd<<<grid, kThreads, sizeof(int32_t) * kRows * (kmax.D + 1), s>>>(fd, kRows);
     return cudaGetLastError();
 }
 

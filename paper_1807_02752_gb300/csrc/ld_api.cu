@@ -40,6 +40,12 @@ struct GroupGraph {
     cudaGraphExec_t exec = nullptr;
 };
 
+// A captured ld_detect_mixed call: its group list and the device descriptors its launches read.
+struct MixedGraph {
+    std::vector<ld_group> groups;
+    cudaGraphExec_t exec = nullptr;
+};
+
 }  // namespace
 
 struct ld_handle {
@@ -62,6 +68,10 @@ struct ld_handle {
     int next_slot = 0;
     GroupGraph group_graphs[kGraphSlots];
     int next_group_slot = 0;
+    MixedGraph mixed_graphs[kGraphSlots];
+    int next_mixed_slot = 0;
+    ld::FrameDesc *d_fdesc = nullptr;   // [kGraphSlots][max_batch] descriptors of the captured mixed calls
+    ld::FrameDesc *h_fdesc = nullptr;   // pinned host staging of one list
     cudaEvent_t ev[kLaunches + 1] = {};
     // two half-batches forked onto their own streams inside a captured call (joined before it ends)
     cudaStream_t sub[2] = {};
@@ -269,6 +279,7 @@ ld::KParams make_kparams(const ld_handle *h, int W, int H, int n)
             }
     }
     k.flat_range = flat_range(p);
+    k.pmax_hint = h->w.pmax;
     k.seg_rows = ld::vpx_seg_rows(k, (size_t)h->smem_optin - 1024);
     const bool tuned = W == h->tile_w && H == h->tile_h;
     k.tile_vdisp = tuned ? h->tile[0] : 0;
@@ -443,6 +454,143 @@ int enqueue_groups(ld_handle *h, const ld_group *g, int ng, bool fork)
     return LD_OK;
 }
 
+// The frames of a group list as descriptors (h->h_fdesc): each frame's own parameters and the workspace
+// seen from its slot (frames counted in the largest size, as enqueue_groups views them).  Returns the
+// launch parameters of the list's largest frame (grid and shared-memory shapes) and the V_px kernel's
+// shared memory (the largest over the frames).
+struct MixedHalf {
+    ld::KParams kl;      // launch shapes: the half's largest frame
+    int first, n;        // descriptors [first, first + n)
+    size_t vpx_smem;
+};
+
+// The list is split into two halves that run concurrently: the groups by pixel count, largest first, each
+// to the half with fewer pixels so far (a group of one size whose frames outweigh the rest gets a half of
+// its own, and its long serial stages overlap the other half's frames; a half holding several groups
+// mixes their sizes in each launch); one group alone is split by frames.  Each half's descriptors are
+// contiguous.
+int fill_descriptors(ld_handle *h, const ld_group *g, int ng, MixedHalf half[2])
+{
+    const ld::KParams kmax = make_kparams(h, h->max_w, h->max_h, h->max_batch);
+    struct Fr { int grp, k, F; size_t px; };
+    std::vector<Fr> fr;
+    for (int i = 0, F = 0; i < ng; F += g[i].n_frames, ++i)
+        for (int k = 0; k < g[i].n_frames; ++k)
+            fr.push_back({i, k, F + k, (size_t)g[i].w * g[i].h});
+    const int n = (int)fr.size();
+    std::vector<int> gside(ng, 0), order(ng);
+    for (int i = 0; i < ng; ++i)
+        order[i] = i;
+    auto gpx = [&](int i) { return (size_t)g[i].w * g[i].h * g[i].n_frames; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gpx(a) > gpx(b); });
+    size_t load[2] = {0, 0};
+    for (int i : order) {
+        const int s = load[0] <= load[1] ? 0 : 1;
+        gside[i] = s;
+        load[s] += gpx(i);
+    }
+    std::vector<int> side(n);
+    int cnt[2] = {0, 0};
+    for (int j = 0; j < n; ++j) {
+        // one group alone: its frames alternate between the halves
+        const int s = ng == 1 ? (fr[j].k & 1) : gside[fr[j].grp];
+        side[j] = s;
+        ++cnt[s];
+    }
+    int pos[2] = {0, cnt[0]};
+    int Wm[2] = {16, 16}, Hm[2] = {16, 16};
+    size_t vs[2] = {0, 0};
+    for (int j = 0; j < n; ++j) {
+        const ld_group &gg = g[fr[j].grp];
+        ld::KParams kp = make_kparams(h, gg.w, gg.h, 1);
+        kp.tile_vdisp = kp.tile_grad = kp.tile_m1 = 0;   // one launch shape for all sizes: the built-in rules
+        const int s = side[j];
+        Wm[s] = std::max(Wm[s], (int)gg.w);
+        Hm[s] = std::max(Hm[s], (int)gg.h);
+        vs[s] = std::max(vs[s], ld::vpx_smem_bytes(kp));
+        const size_t px = (size_t)gg.w * gg.h;
+        ld::FrameDesc &d = h->h_fdesc[pos[s]++];
+        d.kp = kp;
+        d.w = work_from(h->w, kmax, fr[j].F);
+        d.disp = gg.disp + fr[j].k * px;
+        d.img = gg.img + fr[j].k * px;
+        d.out = gg.out_lanes + fr[j].k;
+    }
+    for (int s = 0; s < 2; ++s) {
+        half[s].kl = make_kparams(h, Wm[s], Hm[s], cnt[s]);
+        half[s].kl.tile_vdisp = half[s].kl.tile_grad = half[s].kl.tile_m1 = 0;
+        half[s].first = s ? cnt[0] : 0;
+        half[s].n = cnt[s];
+        half[s].vpx_smem = vs[s];
+    }
+    return n;
+}
+
+// The nine stages of a mixed call, one launch each over all frames (descriptors at fd, already on the
+// device), on the handle's stream.
+int enqueue_mixed_half(ld_handle *h, const ld::KParams &kl, const ld::FrameDesc *fd, int n, size_t vpx_smem,
+                       cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kLaunches; ++k) {
+        nvtxRangePushA(kLaunchNames[k]);
+        switch (k) {
+        case 0: e = ld::launch_vdisp_fd(kl, fd, n, s); break;
+        case 1: e = ld::launch_road_fd(kl, fd, n, s); break;
+        case 2: e = ld::launch_fit_y_fd(kl, fd, n, s); break;
+        case 3:
+            if (kl.bilateral == 2) {
+                e = ld::launch_median_fd(kl, fd, n, s);
+                if (e == cudaSuccess)
+                    e = ld::launch_grad_fd(kl, fd, n, true, s);
+            } else {
+                e = ld::launch_grad_fd(kl, fd, n, false, s);
+            }
+            break;
+        case 4: e = ld::launch_vpx_fd(kl, fd, n, vpx_smem, s); break;
+        case 5: e = ld::launch_fit_x_fd(kl, fd, n, s); break;
+        case 6: e = ld::launch_m1_fd(kl, fd, n, s); break;
+        case 7: e = ld::launch_energy_fd(kl, fd, n, s); break;
+        default: e = ld::launch_select_fd(kl, fd, n, s); break;
+        }
+        nvtxRangePop();
+        if (e != cudaSuccess)
+            return cuda_fail(h, e, kLaunchNames[k]);
+    }
+    return LD_OK;
+}
+
+// The two halves of a mixed call on the handle's sub-streams, forked from and joined back to its stream;
+// the per-row edge counts (and the stage capture) of every frame slot are reset first.
+int enqueue_mixed(ld_handle *h, const MixedHalf half[2], const ld::FrameDesc *fd, int n)
+{
+    cudaStream_t s = h->stream;
+    const size_t rows = (size_t)n * h->max_h, px = rows * h->max_w;   // the frames' slots, largest-size strides
+    cudaError_t e = cudaSuccess;
+    if (h->w.dbg_ibf && (e = cudaMemsetAsync(h->w.dbg_ibf, 0xff, px * 2, s)) != cudaSuccess)
+        return cuda_fail(h, e, "capture reset");
+    if (h->w.dbg_mx && (e = cudaMemsetAsync(h->w.dbg_mx, 0, px * 4, s)) != cudaSuccess)
+        return cuda_fail(h, e, "capture reset");
+    if ((e = cudaMemsetAsync(h->w.ecount, 0, rows * 4, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->w.vcount, 0, rows * 4, s)) != cudaSuccess)
+        return cuda_fail(h, e, "edge count reset");
+    if ((e = cudaEventRecord(h->fork, s)) != cudaSuccess)
+        return cuda_fail(h, e, "fork");
+    for (int k = 0; k < 2; ++k) {
+        if (half[k].n == 0)
+            continue;
+        if ((e = cudaStreamWaitEvent(h->sub[k], h->fork, 0)) != cudaSuccess)
+            return cuda_fail(h, e, "fork wait");
+        const int rc = enqueue_mixed_half(h, half[k].kl, fd + half[k].first, half[k].n, half[k].vpx_smem, h->sub[k]);
+        if (rc != LD_OK)
+            return rc;
+        if ((e = cudaEventRecord(h->join[k], h->sub[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, h->join[k], 0)) != cudaSuccess)
+            return cuda_fail(h, e, "join");
+    }
+    return LD_OK;
+}
+
 bool same_groups(const std::vector<ld_group> &a, const ld_group *b, int n)
 {
     if ((int)a.size() != n)
@@ -465,6 +613,11 @@ void drop_graphs(ld_handle *h)
         if (g.exec) {
             cudaGraphExecDestroy(g.exec);
             g = GroupGraph();
+        }
+    for (MixedGraph &g : h->mixed_graphs)
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g = MixedGraph();
         }
 }
 
@@ -662,6 +815,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     const size_t o_cls = take(sizeof(uint16_t) * ld::kClsTables * 512);
     const size_t o_d = take(n * H * W * 4), o_i = take(n * H * W), o_l = take(n * sizeof(ld_lanes));
     const size_t o_med = take(p->bilateral == 2 ? n * H * W : 0);
+    const size_t o_fd = take(sizeof(ld::FrameDesc) * kGraphSlots * n);
     e = cudaMalloc(&h->ws, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -692,6 +846,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
     w.wr = h->d_tables;
     w.wg = h->d_tables + ld::kWrEntries;
     w.cls_tab = (const uint16_t *)(b + o_cls);
+    h->d_fdesc = (ld::FrameDesc *)(b + o_fd);
     w.max_w = max_w;
     w.max_h = max_h;
     h->d_disp = (float *)(b + o_d);
@@ -740,6 +895,8 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(&h->join[k], cudaEventDisableTiming);
     }
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&h->h_fdesc, sizeof(ld::FrameDesc) * (size_t)max_batch);
     if (e != cudaSuccess) {
         cuda_fail(nullptr, e, "stream and event creation");
         release_sync_objects(h);
@@ -881,6 +1038,72 @@ int ld_detect_groups(ld_handle *h, const ld_group *groups, int32_t n_groups)
     h->next_group_slot = (h->next_group_slot + 1) % kGraphSlots;
     if (g.exec)
         cudaGraphExecDestroy(g.exec);
+    g.exec = exec;
+    g.groups.assign(groups, groups + n_groups);
+    e = cudaGraphLaunch(exec, h->stream);
+    return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
+}
+
+int ld_detect_mixed(ld_handle *h, const ld_group *groups, int32_t n_groups)
+{
+    if (!h)
+        return LD_E_ARG;
+    if (!groups || n_groups < 1 || n_groups > LD_MAX_GROUPS)
+        return fail(h, LD_E_ARG, "groups is NULL or n_groups outside [1, LD_MAX_GROUPS]");
+    int64_t total = 0;
+    for (int i = 0; i < n_groups; ++i) {
+        const ld_group &g = groups[i];
+        const int rc = check_call(h, g.disp, g.img, g.w, g.h, g.n_frames, g.out_lanes);
+        if (rc != LD_OK)
+            return rc;
+        total += g.n_frames;
+    }
+    if (total > h->max_batch)
+        return fail(h, LD_E_ARG, "the groups hold more than max_batch frames");
+    h->have_last = false;   // the workspace now holds frames of several sizes
+    for (MixedGraph &g : h->mixed_graphs)
+        if (g.exec && same_groups(g.groups, groups, n_groups)) {
+            cudaError_t e = cudaGraphLaunch(g.exec, h->stream);
+            return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
+        }
+    cudaStreamCaptureStatus st;
+    cudaError_t e = cudaStreamIsCapturing(h->stream, &st);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "stream query");
+    if (st != cudaStreamCaptureStatusNone || h->stream == nullptr)  // caller captures, or legacy stream
+        return enqueue_groups(h, groups, n_groups, false);          // the same results, one group at a time
+    // descriptors of this list into the next slot's device region (uploaded before the capture: the
+    // graph's launches read them there on every replay)
+    const int slot = h->next_mixed_slot;
+    MixedHalf half[2];
+    const int n = fill_descriptors(h, groups, n_groups, half);
+    ld::FrameDesc *fd = h->d_fdesc + (size_t)slot * h->max_batch;
+    MixedGraph &g = h->mixed_graphs[slot];
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g = MixedGraph();
+    }
+    if ((e = cudaMemcpyAsync(fd, h->h_fdesc, sizeof(ld::FrameDesc) * n, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "descriptor upload");
+    if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(h, e, "begin capture");
+    const int rc = enqueue_mixed(h, half, fd, n);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->stream, &graph);
+    if (rc != LD_OK) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "end capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "graph instantiate");
+    h->next_mixed_slot = (slot + 1) % kGraphSlots;
     g.exec = exec;
     g.groups.assign(groups, groups + n_groups);
     e = cudaGraphLaunch(exec, h->stream);
@@ -1133,6 +1356,7 @@ void ld_destroy(ld_handle *h)
     release_sync_objects(h);
     cudaFree(h->ws);
     cudaFree(h->dbg);
+    cudaFreeHost(h->h_fdesc);
     delete h;
 }
 

@@ -52,6 +52,7 @@ struct KParams {
     // Largest image range (max - min over a group's (4 + 2 rho + 6) x (2 rho + 3) neighbourhood) for which no
     // pixel of the group can pass the edge test, or -1 (pruning off: bilateral != 1).  See flat_range().
     int32_t flat_range;
+    int32_t pmax_hint;                 // the workspace's path-point capacity (Work::pmax), for launch shapes
 };
 
 // Per-frame state written by the fit kernels and read downstream.
@@ -87,6 +88,18 @@ struct Work {
     const int32_t *wg;   // [kWgEntries] Q12
     const uint16_t *cls_tab;  // [kClsTables][512] Q15 bilateral weights by distance class and |dI| (zero from 256 on)
     int32_t max_w, max_h, pmax;
+};
+
+// One frame of a call over frames of several sizes (ld_detect_mixed): its own parameters (W, H, start
+// range, polynomial basis), the workspace seen from its slot (frame index 0 inside the view) and its
+// buffers.  The per-frame launches below run one CTA grid over all frames, sized for the largest; each
+// CTA reads its frame's descriptor and returns when its tile lies outside that frame.
+struct FrameDesc {
+    KParams kp;
+    Work w;
+    const float *disp;   // [H][W]
+    const uint8_t *img;  // [H][W]
+    ld_lanes *out;       // [1]
 };
 
 // ---------------------------------------------------------------------------------------------------
@@ -184,6 +197,18 @@ cudaError_t launch_energy_list(const KParams &kp, const Work &w, const int32_t *
 cudaError_t launch_select_set(const KParams &kp, const Work &w, const uint8_t *cflag, ld_lanes *out, cudaStream_t s);
 cudaError_t launch_energy_fallback(const KParams &kp, const Work &w, cudaStream_t s);
 cudaError_t launch_select_fallback(const KParams &kp, const Work &w, ld_lanes *out, cudaStream_t s);
+// the same stages over a descriptor array (kmax: parameters of the call's largest frame, which size the
+// grids and shared memory; n: frames)
+cudaError_t launch_vdisp_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s);
+cudaError_t launch_road_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s);
+cudaError_t launch_fit_y_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s);
+cudaError_t launch_fit_x_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s);
+cudaError_t launch_grad_fd(const KParams &kmax, const FrameDesc *fd, int n, bool median_input, cudaStream_t s);
+cudaError_t launch_median_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s);
+cudaError_t launch_vpx_fd(const KParams &kmax, const FrameDesc *fd, int n, size_t smem, cudaStream_t s);
+cudaError_t launch_m1_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s);
+cudaError_t launch_energy_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s);
+cudaError_t launch_select_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s);
 size_t road_smem_bytes(const KParams &kp);
 size_t vpx_smem_bytes(const KParams &kp);
 int vpx_seg_rows(const KParams &kp, size_t budget);

@@ -129,6 +129,8 @@ def load():
     L.ld_road_path_static.restype = C.c_int
     L.ld_detect_groups.argtypes = [p, p, i32]
     L.ld_detect_groups.restype = C.c_int
+    L.ld_detect_mixed.argtypes = [p, p, i32]
+    L.ld_detect_mixed.restype = C.c_int
     L.ld_tune.argtypes = [p, p, p, i32, i32, i32, p, p]
     L.ld_tune.restype = C.c_int
     L.ld_server_create.argtypes = [P, C.POINTER(ServerConfig), C.POINTER(p)]
@@ -192,7 +194,7 @@ def load():
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
             "ld_debug_get", "ld_debug_size", "ld_debug_capture", "ld_lane_tracks", "ld_tables", "ld_flat_range", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
-            "ld_destroy", "ld_road_path_static", "ld_tune", "ld_detect_groups", "ld_server_create", "ld_server_submit", "ld_server_poll",
+            "ld_destroy", "ld_road_path_static", "ld_tune", "ld_detect_groups", "ld_detect_mixed", "ld_server_create", "ld_server_submit", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_server_set_learned", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
             "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
@@ -293,9 +295,10 @@ class Detector:
     def lanes(out) -> np.ndarray:
         return np.frombuffer(out.cpu().numpy().tobytes(), dtype=LANES_DTYPE)
 
-    def detect_groups(self, groups, outs=None):
+    def detect_groups(self, groups, outs=None, mixed=False):
         """Frames of several sizes in one call: groups is a list of (disp, img) device tensors [n,H,W], one
-        size per group.  Returns the device result buffers, one per group (see lanes())."""
+        size per group.  Returns the device result buffers, one per group (see lanes()).  mixed=True runs
+        ld_detect_mixed (one launch per stage over all frames) instead of ld_detect_groups."""
         arr = (Group * max(1, len(groups)))()
         outs = [self.alloc_lanes(d.shape[0]) for d, _ in groups] if outs is None else outs
         for k, ((d, i), o) in enumerate(zip(groups, outs)):
@@ -303,7 +306,7 @@ class Detector:
             assert d.is_contiguous() and i.is_contiguous() and d.shape == i.shape
             n, H, W = d.shape
             arr[k] = Group(d.data_ptr(), i.data_ptr(), o.data_ptr(), W, H, n, 0)
-        self._check(self.L.ld_detect_groups(self.h, arr, len(groups)))
+        self._check((self.L.ld_detect_mixed if mixed else self.L.ld_detect_groups)(self.h, arr, len(groups)))
         return outs
 
     def detect_host(self, disp: np.ndarray, img: np.ndarray) -> np.ndarray:

@@ -12,8 +12,8 @@ the learned form instead (the network with the package's trained weights ranks t
 energies for the top_k coarse starts), timed as a whole.  With `stereo` each call is the stereo stage on
 the workload's stereo pairs (search range propagation for both maps, then the consistency check).
 `mixed` times frames of three camera sizes (16 x 1242x375, 8 x 1280x720, 8 x 1920x1080, D = 256) as one
-ld_detect_groups call and as three ld_detect calls in a row on the same stream (captured graphs,
-replayed; CUDA events; median of the calls).
+ld_detect_groups call, as one ld_detect_mixed call (one launch per stage) and as three ld_detect calls in
+a row on the same stream (captured graphs, replayed; CUDA events; median of the calls).
 """
 from __future__ import annotations
 
@@ -54,9 +54,11 @@ def mixed(calls: int):
         return float(np.median(ms))
 
     one = timed(lambda: det.detect_groups(groups, outs))
+    mixed_ms = timed(lambda: det.detect_groups(groups, outs, mixed=True))
     three = timed(lambda: [det.detect(d, i, o) for (d, i), o in zip(groups, outs)])
     n = sum(n for _, n in spec)
     print({"frames": n, "groups_ms": round(one, 4), "groups_fps": round(n / one * 1e3, 1),
+           "mixed_ms": round(mixed_ms, 4), "mixed_fps": round(n / mixed_ms * 1e3, 1),
            "three_calls_ms": round(three, 4), "three_calls_fps": round(n / three * 1e3, 1)})
     det.close()
 

@@ -1,7 +1,8 @@
-"""Frames of several sizes in one call (ld_detect_groups): every group's results must be the ones
-ld_detect gives its frames, byte for byte, on a stream of the handle's own (one captured graph, the groups
-on two forked streams, then replays) and on the legacy default stream (groups one after another); and
-every frame's lanes, flags and fitted rows must be the oracle's."""
+"""Frames of several sizes in one call: ld_detect_groups (one launch sequence per group, the groups on two
+forked streams) and ld_detect_mixed (one launch per stage over every frame, each CTA on its frame's
+descriptor).  Every group's results must be the ones ld_detect gives its frames, byte for byte, on a
+stream of the handle's own (one captured graph, then replays) and on the legacy default stream (groups one
+after another); and every frame's lanes, flags and fitted rows must be the oracle's."""
 import numpy as np
 import pytest
 
@@ -55,8 +56,9 @@ def _alone(torch, groups, p):
     return res
 
 
+@pytest.mark.parametrize("mixed", [False, True])
 @pytest.mark.parametrize("own_stream", [True, False])
-def test_groups_match_ld_detect(torch_cuda, own_stream):
+def test_groups_match_ld_detect(torch_cuda, own_stream, mixed):
     torch = torch_cuda
     p = ld.default_params(n_disp=48)
     groups = _groups(torch, SIZES, 48)
@@ -69,7 +71,7 @@ def test_groups_match_ld_detect(torch_cuda, own_stream):
             for rep in range(3):            # capture, then replays of the same list
                 for o in outs:
                     o.zero_()
-                det.detect_groups(groups, outs)
+                det.detect_groups(groups, outs, mixed=mixed)
                 torch.cuda.synchronize()
                 got = [ld.Detector.lanes(o).tobytes() for o in outs]
                 assert got == want, f"call {rep}"
@@ -79,7 +81,7 @@ def test_groups_match_ld_detect(torch_cuda, own_stream):
             rev, routs = groups[::-1], outs[::-1]
             for o in routs:
                 o.zero_()
-            det.detect_groups(rev, routs)
+            det.detect_groups(rev, routs, mixed=mixed)
             torch.cuda.synchronize()
             assert [ld.Detector.lanes(o).tobytes() for o in outs] == want
             # the workspace held several sizes: ld_debug_get refuses until the next single-size call
@@ -95,7 +97,8 @@ def test_groups_match_ld_detect(torch_cuda, own_stream):
         det.close()
 
 
-def test_groups_full_sizes(torch_cuda):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_groups_full_sizes(torch_cuda, mixed):
     """Three camera sizes at D = 256 (1242x375, 1280x720, 1920x1080) in one captured call."""
     torch = torch_cuda
     p = ld.default_params(n_disp=256)
@@ -111,8 +114,8 @@ def test_groups_full_sizes(torch_cuda):
     det = ld.Detector(1920, 1080, 8, p, stream=stream)
     try:
         with torch.cuda.stream(stream):
-            outs = det.detect_groups(groups)
-            outs = det.detect_groups(groups, outs)
+            outs = det.detect_groups(groups, mixed=mixed)
+            outs = det.detect_groups(groups, outs, mixed=mixed)
             torch.cuda.synchronize()
             assert [ld.Detector.lanes(o).tobytes() for o in outs] == want
         _check_oracle(groups, outs, p)
@@ -140,5 +143,24 @@ def test_group_argument_errors(torch_cuda):
         outs = det.detect_groups([(d[:2], i[:2]), (d2, i2)])   # exactly max_batch: accepted
         torch.cuda.synchronize()
         assert len(outs) == 2
+    finally:
+        det.close()
+
+
+@pytest.mark.parametrize("kw", [{"bilateral": 2}, {"dp_literal": 1}, {"tau_y": 15}, {"bilateral": 0, "chi": 5}])
+def test_mixed_param_variants(torch_cuda, kw):
+    """ld_detect_mixed with the median pre-filter, the literal Eq. 12, the wide road step and the raw image:
+    every group's results are the ones ld_detect gives it."""
+    torch = torch_cuda
+    p = ld.default_params(n_disp=48, **kw)
+    groups = _groups(torch, SIZES, 48, first=500)
+    want = _alone(torch, groups, p)
+    stream = torch.cuda.Stream()
+    det = ld.Detector(400, 150, sum(n for _, n in SIZES), p, stream=stream)
+    try:
+        with torch.cuda.stream(stream):
+            outs = det.detect_groups(groups, mixed=True)
+            torch.cuda.synchronize()
+            assert [ld.Detector.lanes(o).tobytes() for o in outs] == want
     finally:
         det.close()
