@@ -332,6 +332,12 @@ typedef struct ld_server_config {
     int32_t max_batch;                        /* frames per batch, >= 1 */
     int32_t max_wait_us;                      /* a partial batch launches once its oldest frame waited this */
     int32_t n_streams;                        /* camera streams: ids 0 .. n_streams-1 */
+    int32_t reserved;                         /* 0 */
+    int64_t hbm_budget_bytes;                 /* 0: the slots_per_size slots of each class only.  > 0: when
+                                               * every slot of a class is full or in flight, a submit adds
+                                               * one more slot while the slots' device bytes stay within
+                                               * this budget and the device keeps 256 MiB free; slots are
+                                               * kept until ld_server_destroy */
 } ld_server_config;
 
 typedef struct ld_result {
@@ -346,17 +352,36 @@ typedef struct ld_server_stats {
     int64_t submitted, completed, rejected, batches;
     double mean_batch;                        /* frames per launched batch */
     double p50_ms, p99_ms;                    /* latency percentiles of the completed frames */
+    int64_t slots;                            /* slots allocated (initial and added under the budget) */
+    int64_t device_bytes;                     /* device bytes of the slots' buffers and handle workspaces */
 } ld_server_stats;
 
 /* Create a server (all memory allocated here).  Errors: LD_E_ARG (bad config or params), LD_E_NOMEM,
  * LD_E_CUDA; *out is NULL on error and ld_server_last_error(NULL) describes it. */
 int ld_server_create(const ld_params *p, const ld_server_config *cfg, ld_server **out);
 
-/* Submit one frame (HOST pointers, [h][w]; copied before the call returns, so the caller may reuse them).
+/* Submit one frame (HOST pointers, [h][w]; copied into the slot's page-locked staging before the call
+ * returns, so the caller may reuse them; the copy to the device is enqueued at once on the slot's stream).
  * Errors: LD_E_ARG (unknown size or stream id, null pointer), LD_E_BUSY (every slot of the class is full
- * or in flight: poll and retry), LD_E_CUDA. */
+ * or in flight and the HBM budget admits no further slot: poll and retry), LD_E_CUDA. */
 int ld_server_submit(ld_server *s, int32_t stream_id, const float *disp, const uint8_t *img, int32_t w, int32_t h,
                      uint64_t tag);
+
+/* As ld_server_submit, for frames in PAGE-LOCKED host memory (cudaMallocHost, cudaHostRegister, a pinned
+ * torch tensor): the device reads them directly (no host copy), so the caller must leave both buffers
+ * unchanged until the frame's result has come out of ld_server_poll.  Pageable pointers still work, at the
+ * cost of a copy the driver stages.  Errors as ld_server_submit. */
+int ld_server_submit_pinned(ld_server *s, int32_t stream_id, const float *disp, const uint8_t *img, int32_t w,
+                            int32_t h, uint64_t tag);
+
+/* Submit n_frames frames of one size at once: disp [n_frames][h][w] and img [n_frames][h][w] contiguous
+ * HOST arrays, stream_ids and tags [n_frames]; pinned != 0 as ld_server_submit_pinned, else as
+ * ld_server_submit.  Frames are placed in order, a run per slot with one device copy per buffer and run.
+ * Several threads may submit at once: the copies are made outside the server's lock.  Returns the number
+ * of frames accepted (the first ones; fewer than n_frames when the slots filled up: poll and resubmit the
+ * rest) or, when none was, LD_E_BUSY; LD_E_ARG, LD_E_CUDA as ld_server_submit. */
+int ld_server_submit_batch(ld_server *s, int32_t n_frames, const int32_t *stream_ids, const float *disp,
+                           const uint8_t *img, int32_t w, int32_t h, const uint64_t *tags, int32_t pinned);
 
 /* Switch the server's batches to the learned form (ld_detect_learned below, with the network run and the
  * given top_k) or, with top_k = 0, back to the plain form.  params: DEVICE pointer to LD_NET_PARAMS floats,

@@ -54,6 +54,7 @@ struct ld_handle {
     cudaStream_t stream = nullptr;
     int smem_optin = 0;
     void *ws = nullptr;          // device workspace
+    size_t ws_bytes = 0;
     ld::Work w{};
     int32_t *d_tables = nullptr; // wr, wg
     int32_t ws_q[121]{};
@@ -822,6 +823,7 @@ int ld_create(const ld_params *p, int32_t max_w, int32_t max_h, int32_t max_batc
         delete h;
         return fail(nullptr, LD_E_NOMEM, std::string("workspace allocation: ") + cudaGetErrorString(e));
     }
+    h->ws_bytes = off;
     char *b = (char *)h->ws;
     ld::Work &w = h->w;
     w.myT = (int32_t *)(b + o_my);
@@ -1363,6 +1365,8 @@ void ld_destroy(ld_handle *h)
 }  // extern "C"
 
 namespace ld {
+size_t handle_device_bytes(const ld_handle *h) { return h ? h->ws_bytes : 0; }
+
 // ld_detect without the graph cache: the nine launches are enqueued directly on the handle's stream (the
 // serving path, whose batch sizes vary from call to call).
 int detect_eager(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,

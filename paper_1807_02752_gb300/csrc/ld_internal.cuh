@@ -220,4 +220,6 @@ int detect_eager(ld_handle *h, const float *disp, const uint8_t *img, int32_t w,
                  ld_lanes *out_lanes);
 int detect_learned_eager(ld_net *net, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
                          int32_t top_k, ld_lanes *out_lanes);
+// device bytes of a handle's workspace (its buffers for max_batch frames of the largest size)
+size_t handle_device_bytes(const ld_handle *h);
 }  // namespace ld

@@ -61,7 +61,8 @@ class StereoParams(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("n_sizes", C.c_int32), ("sizes", (C.c_int32 * 2) * MAX_SIZE_CLASSES), ("slots_per_size", C.c_int32),
-                ("max_batch", C.c_int32), ("max_wait_us", C.c_int32), ("n_streams", C.c_int32)]
+                ("max_batch", C.c_int32), ("max_wait_us", C.c_int32), ("n_streams", C.c_int32),
+                ("reserved", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
 
 
 class Group(C.Structure):
@@ -74,7 +75,8 @@ assert C.sizeof(Group) == 40
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rejected", C.c_int64), ("batches", C.c_int64),
-                ("mean_batch", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
+                ("mean_batch", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("slots", C.c_int64),
+                ("device_bytes", C.c_int64)]
 
 
 RESULT_DTYPE = np.dtype([("tag", "<u8"), ("stream_id", "<i4"), ("w", "<i4"), ("h", "<i4"), ("pad", "<i4"),
@@ -137,6 +139,10 @@ def load():
     L.ld_server_create.restype = C.c_int
     L.ld_server_submit.argtypes = [p, i32, p, p, i32, i32, C.c_uint64]
     L.ld_server_submit.restype = C.c_int
+    L.ld_server_submit_pinned.argtypes = [p, i32, p, p, i32, i32, C.c_uint64]
+    L.ld_server_submit_pinned.restype = C.c_int
+    L.ld_server_submit_batch.argtypes = [p, i32, p, p, p, i32, i32, p, i32]
+    L.ld_server_submit_batch.restype = C.c_int
     L.ld_server_poll.argtypes = [p, p, i32, i32]
     L.ld_server_poll.restype = C.c_int
     L.ld_server_drain.argtypes = [p]
@@ -194,7 +200,8 @@ def load():
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
             "ld_debug_get", "ld_debug_size", "ld_debug_capture", "ld_lane_tracks", "ld_tables", "ld_flat_range", "ld_launches_per_detect", "ld_launch_name", "ld_last_error",
-            "ld_destroy", "ld_road_path_static", "ld_tune", "ld_detect_groups", "ld_detect_mixed", "ld_server_create", "ld_server_submit", "ld_server_poll",
+            "ld_destroy", "ld_road_path_static", "ld_tune", "ld_detect_groups", "ld_detect_mixed", "ld_server_create", "ld_server_submit",
+            "ld_server_submit_pinned", "ld_server_submit_batch", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_server_set_learned", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
             "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
@@ -398,7 +405,7 @@ class Server:
     """Continuous batching of frames of several sizes from several camera streams (ld_server_* of ld.h)."""
 
     def __init__(self, sizes, params: Params | None = None, slots_per_size: int = 2, max_batch: int = 16,
-                 max_wait_us: int = 500, n_streams: int = 8):
+                 max_wait_us: int = 500, n_streams: int = 8, hbm_budget_bytes: int = 0):
         self.L = load()
         self.params = params or default_params()
         cfg = ServerConfig()
@@ -407,6 +414,7 @@ class Server:
             cfg.sizes[k][0] = w
             cfg.sizes[k][1] = h
         cfg.slots_per_size, cfg.max_batch, cfg.max_wait_us, cfg.n_streams = slots_per_size, max_batch, max_wait_us, n_streams
+        cfg.hbm_budget_bytes = hbm_budget_bytes
         self.cfg = cfg
         s = C.c_void_p()
         rc = self.L.ld_server_create(C.byref(self.params), C.byref(cfg), C.byref(s))
@@ -425,6 +433,41 @@ class Server:
         if rc != 0:
             raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
         return True
+
+    def submit_pinned(self, stream_id: int, disp, img, tag: int = 0) -> bool:
+        """Submit one frame held in page-locked host memory (pinned torch tensors [h][w]): read by the device
+        directly, so both must stay unchanged until the frame's result has been polled."""
+        H, W = disp.shape
+        assert disp.is_contiguous() and img.is_contiguous() and disp.dtype.itemsize == 4 and img.dtype.itemsize == 1
+        rc = self.L.ld_server_submit_pinned(self.s, stream_id, disp.data_ptr(), img.data_ptr(), W, H, tag)
+        if rc == E_BUSY:
+            return False
+        if rc != 0:
+            raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
+        return True
+
+    def submit_batch(self, stream_ids, disp, img, tags, pinned: bool = False) -> int:
+        """Submit frames [n][h][w] of one size (numpy arrays, or pinned torch tensors with pinned=True: then
+        they must stay unchanged until their results have been polled).  Returns how many were accepted (the
+        first ones)."""
+        sid = np.ascontiguousarray(stream_ids, np.int32)
+        tg = np.ascontiguousarray(tags, np.uint64)
+        if pinned:
+            assert disp.is_contiguous() and img.is_contiguous() and disp.dtype.itemsize == 4 and img.dtype.itemsize == 1
+            n, H, W = disp.shape
+            dp, ip = disp.data_ptr(), img.data_ptr()
+        else:
+            disp = np.ascontiguousarray(disp, np.float32)
+            img = np.ascontiguousarray(img, np.uint8)
+            n, H, W = disp.shape
+            dp, ip = disp.ctypes.data, img.ctypes.data
+        assert sid.shape == (n,) and tg.shape == (n,)
+        rc = self.L.ld_server_submit_batch(self.s, n, sid.ctypes.data, dp, ip, W, H, tg.ctypes.data, 1 if pinned else 0)
+        if rc == E_BUSY:
+            return 0
+        if rc < 0:
+            raise LDError(rc, self.L.ld_server_last_error(self.s).decode())
+        return rc
 
     def set_learned(self, theta=None, top_k: int = 0):
         """Run the batches in the learned form (theta: float32 device tensor of NET_PARAMS values, copied in)
