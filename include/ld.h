@@ -266,6 +266,30 @@ int ld_tables(const ld_params *p, int32_t *ws_q, int32_t *wr_q, int32_t *wg_q);
  */
 int32_t ld_flat_range(const ld_params *p);
 
+/*
+ * Bounds-checked build.  lib/libld_checked.so is this library compiled with LD_CHECKED (build.py
+ * --checked).  Before each access its kernels test, against the buffer's extent, every index they
+ * compute from data: histogram bins, vote and edge columns, decoded backtrack steps, path cells,
+ * point-list and sample indices, track columns and list decodes.  They also test every append to a
+ * fixed-capacity list and each tile against its frame.  A failing access is skipped (loads read 0) and
+ * counted; the first failure's site, index and bound are kept.  Nothing traps.  In the regular library
+ * the tests compile away and the calls below report a clean state.
+ *   ld_checked_build   1 in the checked library, 0 otherwise.
+ *   ld_check_status    waits for the device, then out[0] = failures since the last reset,
+ *                      out[1..3] = site, index and bound of the first one (0 when none).  LD_E_CUDA on
+ *                      a device error.
+ *   ld_check_reset     clears the counts (waits for the device first).
+ *   ld_check_site_name the name of a site ("?" for an unknown one).
+ *   ld_check_selftest  checked library only: one thread evaluates a test with index = bound (no access
+ *                      follows), so the status then shows one failure at site "selftest".  LD_E_STATE
+ *                      in the regular library.
+ */
+int32_t ld_checked_build(void);
+int ld_check_status(int64_t out[4]);
+int ld_check_reset(void);
+const char *ld_check_site_name(int32_t site);
+int ld_check_selftest(void);
+
 /* Number of kernel launches one ld_detect call enqueues, and the name of launch k (0-based). */
 int32_t ld_launches_per_detect(void);
 const char *ld_launch_name(int32_t k);

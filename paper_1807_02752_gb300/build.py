@@ -2,6 +2,9 @@
 
 Every translation unit under csrc/ is compiled in parallel, then linked into lib/libld.so, which the
 Python binding in ld.py loads.  No CPU fallback exists: without this library the binding raises.
+build(checked=True) (or --checked) builds the bounds-checked variant lib/libld_checked.so from the same
+sources with LD_CHECKED defined: its kernels test every data-derived index before the access and record
+failures instead of trapping (ld_check_status in include/ld.h).
 """
 from __future__ import annotations
 
@@ -16,7 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libld.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "libld_checked.so")
 OBJ_DIR = os.path.join(ROOT, "_build", "ld")
+OBJ_DIR_CHECKED = os.path.join(ROOT, "_build", "ld_checked")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-prec-div=true", "-prec-sqrt=true",
@@ -41,13 +46,16 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    obj_dir, lib = (OBJ_DIR_CHECKED, LIB_CHECKED) if checked else (OBJ_DIR, LIB)
+    if checked:
+        extra = (*extra, "-DLD_CHECKED")
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    os.makedirs(obj_dir, exist_ok=True)
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "ld.h")]
     objs, procs = [], []
     for src in sources():
-        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src, *headers]):
             cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
@@ -64,13 +72,35 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-lpthread", "-ldl"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> tuple:
+    """Both variants, their translation units compiled concurrently: (libld.so, libld_checked.so)."""
+    import threading
+
+    out, errs = {}, []
+
+    def one(checked):
+        try:
+            out[checked] = build(force=force, checked=checked)
+        except Exception as e:  # re-raised below
+            errs.append(e)
+
+    ths = [threading.Thread(target=one, args=(c,)) for c in (False, True)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    if errs:
+        raise errs[0]
+    return out[False], out[True]
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [])
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose=True, extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [],
+                checked="--checked" in sys.argv))

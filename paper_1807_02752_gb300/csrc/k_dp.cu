@@ -220,23 +220,25 @@ __device__ __forceinline__ void road_dp_body(const KParams &kp, const Work &w, c
         path[1] = (int16_t)v;
         const uint8_t *row = bt + Hp;
         for (int d = 1; d <= D - 2; ++d, row += Hp) {
-            v += (row[v >> 1] >> (4 * (v & 1))) & 15;
+            if (LD_IN(v, H, CK_ROAD_PATH))
+                v += (row[v >> 1] >> (4 * (v & 1))) & 15;
             path[d + 1] = (int16_t)v;
         }
     }
     __syncthreads();
     for (int d = tid; d < D; d += nt) {
-        flag[d] = d >= 1 && my[(size_t)d * H + path[d]] > 0;
+        flag[d] = d >= 1 && LD_IN(path[d], H, CK_ROAD_PATH) && my[(size_t)d * H + path[d]] > 0;
         w.path_y[(size_t)f * D + d] = path[d];
     }
     __syncthreads();
     const int k = block_compact(flag, D, pid, sh);
     int16_t *gp = w.pts + (size_t)f * 2 * 3 * w.pmax;
-    for (int j = tid; j < k; j += nt) {
-        gp[j] = path[pid[j]];
-        gp[w.pmax + j] = pid[j];
-        gp[2 * w.pmax + j] = pid[j];
-    }
+    for (int j = tid; j < k; j += nt)
+        if (LD_IN(j, w.pmax, CK_ROAD_PTS) && LD_IN(pid[j], D, CK_ROAD_PTS)) {
+            gp[j] = path[pid[j]];
+            gp[w.pmax + j] = pid[j];
+            gp[2 * w.pmax + j] = pid[j];
+        }
     if (tid == 0)
         w.npts[f * 2] = k;
 }
@@ -314,23 +316,25 @@ __device__ __forceinline__ void road_dp_lit_body(const KParams &kp, const Work &
         int v = vstar;
         path[1] = (int16_t)v;
         for (int d = 1; d <= D - 2; ++d) {
-            v -= (bt[(size_t)d * Hp + (v >> 1)] >> (4 * (v & 1))) & 15;
+            if (LD_IN(v, H, CK_ROAD_PATH))
+                v -= (bt[(size_t)d * Hp + (v >> 1)] >> (4 * (v & 1))) & 15;
             path[d + 1] = (int16_t)v;
         }
     }
     __syncthreads();
     for (int d = tid; d < D; d += nt) {
-        flag[d] = d >= 1 && my[(size_t)d * H + path[d]] > 0;
+        flag[d] = d >= 1 && LD_IN(path[d], H, CK_ROAD_PATH) && my[(size_t)d * H + path[d]] > 0;
         w.path_y[(size_t)f * D + d] = path[d];
     }
     __syncthreads();
     const int k = block_compact(flag, D, pid, sh);
     int16_t *gp = w.pts + (size_t)f * 2 * 3 * w.pmax;
-    for (int j = tid; j < k; j += nt) {
-        gp[j] = path[pid[j]];
-        gp[w.pmax + j] = pid[j];
-        gp[2 * w.pmax + j] = pid[j];
-    }
+    for (int j = tid; j < k; j += nt)
+        if (LD_IN(j, w.pmax, CK_ROAD_PTS) && LD_IN(pid[j], D, CK_ROAD_PTS)) {
+            gp[j] = path[pid[j]];
+            gp[w.pmax + j] = pid[j];
+            gp[2 * w.pmax + j] = pid[j];
+        }
     if (tid == 0)
         w.npts[f * 2] = k;
 }
@@ -408,24 +412,28 @@ __device__ __forceinline__ void scatter_delta(const KParams &kp, const Work &w, 
         for (int r = max(r_lo, vtop); r <= v; ++r) {
             const VoteRow vr = vote_row(kp, w, S, f, r, staged);
             for (int q = t0; q < vr.n; q += stride)
-                atoms_add(delta + 4u * (uint32_t)vr.p[q], 1);
+                if (LD_IN(vr.p[q], kp.W, CK_VPX_VOTE))
+                    atoms_add(delta + 4u * (uint32_t)vr.p[q], 1);
         }
         if (v == vmax - chi - 1) {
             const VoteRow vr = vote_row(kp, w, S, f, vmax, staged);
             for (int q = t0; q < vr.n; q += stride)
-                atoms_add(delta + 4u * (uint32_t)vr.p[q], -1);
+                if (LD_IN(vr.p[q], kp.W, CK_VPX_VOTE))
+                    atoms_add(delta + 4u * (uint32_t)vr.p[q], -1);
         }
         return;
     }
     if (v - chi >= vtop) {
         const VoteRow vr = vote_row(kp, w, S, f, v - chi, staged);
         for (int q = t0; q < vr.n; q += stride)
-            atoms_add(delta + 4u * (uint32_t)vr.p[q], 1);
+            if (LD_IN(vr.p[q], kp.W, CK_VPX_VOTE))
+                atoms_add(delta + 4u * (uint32_t)vr.p[q], 1);
     }
     if (v + chi + 1 <= vmax) {
         const VoteRow vr = vote_row(kp, w, S, f, v + chi + 1, staged);
         for (int q = t0; q < vr.n; q += stride)
-            atoms_add(delta + 4u * (uint32_t)vr.p[q], -1);
+            if (LD_IN(vr.p[q], kp.W, CK_VPX_VOTE))
+                atoms_add(delta + 4u * (uint32_t)vr.p[q], -1);
     }
 }
 
@@ -579,12 +587,14 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
         const int r0 = kp.band_literal ? vmax : max(vtop, vmax - chi);   // the literal bottom band of row vmax is [vmax, vmax]
         if (staged) {
             for (int q = S.voff[r0] + tid; q < S.voff[vmax + 1]; q += nt)
-                atoms_add(d0 + 4u * (uint32_t)S.vb[q], 1);
+                if (LD_IN(S.vb[q], W, CK_VPX_VOTE))
+                    atoms_add(d0 + 4u * (uint32_t)S.vb[q], 1);
         } else {
             for (int r = r0; r <= vmax; ++r) {
                 const VoteRow vr = vote_row(kp, w, S, f, r, staged);
                 for (int q = tid; q < vr.n; q += nt)
-                    atoms_add(d0 + 4u * (uint32_t)vr.p[q], 1);
+                    if (LD_IN(vr.p[q], W, CK_VPX_VOTE))
+                        atoms_add(d0 + 4u * (uint32_t)vr.p[q], 1);
             }
         }
     }
@@ -668,7 +678,8 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
                 S.path[vtop] = (int16_t)u;
             uint32_t rowa = bt;
             for (int v = lo; v <= hi; ++v, rowa += (uint32_t)RB) {
-                u += bt_step(rowa, u, PACKED);
+                if (LD_IN(u, W, CK_VPX_PATH))
+                    u += bt_step(rowa, u, PACKED);
                 S.path[v + 1] = (int16_t)u;
             }
         }
@@ -686,6 +697,8 @@ __device__ __forceinline__ void vpx_dp_kernel_body(const KParams &kp, const Work
     if (fs0.flags & LD_F_NO_LANES)
         return;
     const int vtop = fs0.v_top, vmax = H - 1, chi = kp.chi;
+    if (!LD_IN(vtop, H, CK_VPX_TILE))
+        return;
 
     VpxMem S;
     unsigned char *p = smem;
@@ -702,8 +715,10 @@ __device__ __forceinline__ void vpx_dp_kernel_body(const KParams &kp, const Work
     S.dyn = carve<unsigned char>(p, 0);
 
     // ---- vote rows [vtop, vmax]: offsets by a block scan, staged in shared memory when they fit ----
-    for (int v = tid; v < H; v += nt)
-        S.voff[v] = v >= vtop ? w.vcount[(size_t)f * H + v] : 0;
+    for (int v = tid; v < H; v += nt) {
+        const int c = v >= vtop ? w.vcount[(size_t)f * H + v] : 0;
+        S.voff[v] = LD_IN(c, W + 1, CK_VPX_VOFF) ? c : 0;   // a row holds at most W votes
+    }
     for (int u = tid; u < 2 * NPr; u += nt) {
         S.D0[u] = 0;
         S.D1[u] = 0;
@@ -736,7 +751,8 @@ __device__ __forceinline__ void vpx_dp_kernel_body(const KParams &kp, const Work
                         else
                             hi = mid;
                     }
-                    val[k] = __ldg(w.vbins + ((size_t)f * H + lo) * W + (q - S.voff[lo]));
+                    if (LD_IN(q - S.voff[lo], W, CK_VPX_STAGE) && LD_IN(q, kp.vote_cap, CK_VPX_STAGE))
+                        val[k] = __ldg(w.vbins + ((size_t)f * H + lo) * W + (q - S.voff[lo]));
                 }
             }
 #pragma unroll
@@ -774,11 +790,16 @@ __device__ __forceinline__ void vpx_dp_kernel_body(const KParams &kp, const Work
             if (r <= rhi) {
                 const VoteRow vr = vote_row(kp, w, S, f, r, staged);
                 for (int q = lane & 7; q < vr.n; q += 8)
-                    atoms_or(sa(cb + (size_t)vr.p[q] * HB + ((r - rb) >> 5)), 1u << ((r - rb) & 31));
+                    if (LD_IN(vr.p[q], W, CK_VPX_VOTE))
+                        atoms_or(sa(cb + (size_t)vr.p[q] * HB + ((r - rb) >> 5)), 1u << ((r - rb) & 31));
             }
         }
         __syncthreads();
         for (int v = R0 + tid; v < R1; v += nt) {
+            if (!LD_IN(S.path[v], W, CK_VPX_PATH)) {
+                S.sup[v] = 0;
+                continue;
+            }
             const uint32_t *col = cb + (size_t)S.path[v] * HB;
             const int lo = (kp.band_literal && v > vmax - chi - 1 ? v : max(vtop, v - chi)) - rb, hi = min(vmax, v + chi) - rb;
             uint8_t sp = 0;
@@ -800,11 +821,12 @@ __device__ __forceinline__ void vpx_dp_kernel_body(const KParams &kp, const Work
     const int t = vmax - vtop + 1;
     const int k = block_compact(S.sup + vtop, t, S.pid, S.sh);
     int16_t *gp = w.pts + ((size_t)f * 2 + 1) * 3 * w.pmax;
-    for (int j = tid; j < k; j += nt) {
-        gp[j] = (int16_t)(vtop + S.pid[j]);
-        gp[w.pmax + j] = S.path[vtop + S.pid[j]];
-        gp[2 * w.pmax + j] = (int16_t)(vtop + S.pid[j]);
-    }
+    for (int j = tid; j < k; j += nt)
+        if (LD_IN(j, w.pmax, CK_VPX_PTS) && LD_IN(S.pid[j], t, CK_VPX_PTS)) {
+            gp[j] = (int16_t)(vtop + S.pid[j]);
+            gp[w.pmax + j] = S.path[vtop + S.pid[j]];
+            gp[2 * w.pmax + j] = (int16_t)(vtop + S.pid[j]);
+        }
     for (int v = tid; v < H; v += nt)
         w.path_x[(size_t)f * H + v] = v >= vtop ? S.path[v] : (int16_t)0;
     if (tid == 0)

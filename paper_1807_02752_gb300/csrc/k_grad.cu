@@ -183,6 +183,8 @@ __device__ __forceinline__ void grad_body(const KParams &kp, const Work &w, cons
     const int vtop = fs.v_top;
     if ((fs.flags & LD_F_NO_LANES) || r0 + nr - 1 < vtop)
         return;   // no road pixel of the tile (the per-row counts were zeroed before the launch)
+    if (!LD_IN(kp.n_cls, kClsTables + 1, CK_GRAD_TILE))   // the class tables the tile copies
+        return;
     const GradTile T = grad_tile<RHO>(nr, nj, kp.n_cls);
     const int cbase = 4 * j0 - RHO - 4, rbase = r0 - RHO - 1;   // frame column / row of tile column / row 0
     uint16_t *tabs = reinterpret_cast<uint16_t *>(smem + T.o_tab);    // [n_cls][512]
@@ -303,14 +305,20 @@ __device__ __forceinline__ void grad_body(const KParams &kp, const Work &w, cons
             if (lane == 0 && m)
                 base = atomicAdd(cnt, __popc(m));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (need)
-                glist[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((b << 8) | g);
+            const int at = base + __popc(m & ((1u << lane) - 1u));
+            if (need && LD_IN(at, (nr + 2) * T.NGB, CK_GRAD_GLIST))
+                glist[at] = (uint16_t)((b << 8) | g);
         }
     __syncthreads();
-    const int ng = *cnt;
+    const int ng = LD_IN(*cnt, (nr + 2) * T.NGB + 1, CK_GRAD_GLIST) ? *cnt : 0;
     const uint32_t tab = smem_addr(tabs);
+    constexpr int NLW = (4 + 2 * RHO + 3) / 4;   // 8-byte loads per window row of a group
     for (int k = tid; k < ng; k += kThreads) {
         const int e = glist[k], b = e >> 8, g = e & 255;
+        // the group's cell, then its windows (tile rows b .. b + 2 RHO, tile columns 4 g .. 4 g + 4 NLW - 1)
+        if (!LD_IN(b, nr + 2, CK_GRAD_GROUP) || !LD_IN(g, T.NGB, CK_GRAD_GROUP) ||
+            !LD_IN(b + 2 * RHO, T.TR, CK_GRAD_TAP) || !LD_IN(4 * g + 4 * NLW - 1, T.TWP, CK_GRAD_TAP))
+            continue;
         const int u0 = 4 * (j0 - 1 + g), v = r0 - 1 + b;   // frame column of the group, frame row
         const int nv = min(4, W - u0);
         uint32_t out;
@@ -388,12 +396,14 @@ __device__ __forceinline__ void grad_body(const KParams &kp, const Work &w, cons
             if (ne) {
                 const int pe = atomicAdd(ecnt + v, ne);
                 for (int k = 0; k < ne; ++k)
-                    *reinterpret_cast<short4 *>(edges + ((size_t)v * W + pe + k) * 4) = ent[k];
+                    if (LD_IN(pe + k, W, CK_GRAD_EDGE))   // a row holds at most W edge entries
+                        *reinterpret_cast<short4 *>(edges + ((size_t)v * W + pe + k) * 4) = ent[k];
             }
             if (nb) {
                 const int pv = atomicAdd(vcnt + v, nb);
                 for (int k = 0; k < nb; ++k)
-                    vbins[(size_t)v * W + pv + k] = (int16_t)bins[k];
+                    if (LD_IN(pv + k, W, CK_GRAD_VOTE) && LD_IN(bins[k], W, CK_GRAD_VOTE))
+                        vbins[(size_t)v * W + pv + k] = (int16_t)bins[k];
             }
         }
 }

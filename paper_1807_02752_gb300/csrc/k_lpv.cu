@@ -78,10 +78,14 @@ __device__ __forceinline__ void m1_body(const KParams &kp, const Work &w, int R,
     // edge rows that reach the M_0 rows r0-1 .. r0+nr, and the prefix of their edge counts
     const int elo = max(vtop, d0), ehi = min(vmax, r0 + nr + vs);
     const int ner = max(0, ehi - elo + 1);           // <= kM1MaxEdgeRows (R <= 16, varsigma <= 8)
+    if (!LD_IN(ner, kM1MaxEdgeRows + 1, CK_M1_CHUNK))
+        return;
     if (tid < 32) {
         const int32_t *ec = w.ecount + (size_t)f * H + elo;
-        const int a = 2 * lane < ner ? ec[2 * lane] : 0;
-        const int b = 2 * lane + 1 < ner ? ec[2 * lane + 1] : 0;
+        int a = 2 * lane < ner ? ec[2 * lane] : 0;
+        int b = 2 * lane + 1 < ner ? ec[2 * lane + 1] : 0;
+        a = LD_IN(a, W + 1, CK_M1_EDGE) ? a : 0;    // a row holds at most W edge entries
+        b = LD_IN(b, W + 1, CK_M1_EDGE) ? b : 0;
         int s = a + b;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -122,6 +126,8 @@ __device__ __forceinline__ void m1_body(const KParams &kp, const Work &w, int R,
             const int v = elo + lo;
             const short4 e = reinterpret_cast<const short4 *>(w.edges + ((size_t)f * H + v) * W * 4)[q - eoff[lo]];
             const int u = e.x, gx = e.z, gy = e.w;
+            if (!LD_IN(u, W, CK_M1_EDGE) || !LD_IN(v - d0, ndr, CK_M1_CHUNK))
+                continue;
             if (u + nu + 1 < c0 || u - nu - 1 >= c1)
                 if (!(c0 == 0 && abs(u - 1) <= nu) && !(c1 == W && abs(u - (W - 2)) <= nu))
                     continue;
@@ -135,8 +141,9 @@ __device__ __forceinline__ void m1_body(const KParams &kp, const Work &w, int R,
             int wg = 0;
             if (den > 0.0f) {
                 const float s = __fdiv_rn(num, den);
-                if (s <= 0.25f)
-                    wg = __ldg(w.wg + (int)__fmul_rn(__fsqrt_rn(s), 32768.0f));
+                const int ti = (int)__fmul_rn(__fsqrt_rn(s), 32768.0f);
+                if (s <= 0.25f && LD_IN(ti, kWgEntries, CK_M1_COL))
+                    wg = __ldg(w.wg + ti);
             }
             const int g = gx * wg;
             if (g == 0)
@@ -222,11 +229,11 @@ __device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, co
     __syncthreads();
     int i = tile * kEnThreads + threadIdx.x;
     if (MODE == 1) {
-        if (i >= ecnt[f])
+        if (i >= ecnt[f] || !LD_IN(i, ecap, CK_EN_START))
             return;
         i = elist[(size_t)f * ecap + i];
     }
-    if (i >= kp.n_starts)
+    if (i >= kp.n_starts || !LD_IN(i, kp.n_starts, CK_EN_START))
         return;
     const int32_t *M1 = w.M1 + (size_t)f * H * W;
     const float fW = (float)W;
@@ -259,7 +266,8 @@ __device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, co
         int32_t m[kEnBatch];
 #pragma unroll
         for (int b = 0; b < kEnBatch; ++b)
-            m[b] = col[b] >= 0 ? __ldg(M1 + (size_t)(v0 - b) * W + col[b]) : 0;
+            m[b] = col[b] >= 0 && LD_IN(col[b], W, CK_EN_COL) && LD_IN(v0 - b, H, CK_EN_ROW)
+                       ? __ldg(M1 + (size_t)(v0 - b) * W + col[b]) : 0;
 #pragma unroll
         for (int b = 0; b < kEnBatch; ++b)
             if (decltype(full)::value || b < nb)
@@ -337,11 +345,14 @@ __device__ __forceinline__ void select_body(const KParams &kp, const Work &w, ld
                 if (cf && !(cf[i] & 1))
                     continue;
                 const long long h = he[i];
-                if (h < he[i - 1] && h < he[i + 1] && h < t)
-                    pos[atomicAdd(&ncand, 1)] = i;
+                if (h < he[i - 1] && h < he[i + 1] && h < t) {
+                    const int at = atomicAdd(&ncand, 1);   // strict minima: at most (ns - 1) / 2
+                    if (LD_IN(at, ns / 2 + 2, CK_SEL_START))
+                        pos[at] = i;
+                }
             }
             __syncthreads();
-            const int nc = ncand;
+            const int nc = LD_IN(ncand, ns / 2 + 3, CK_SEL_START) ? ncand : 0;
             // order by (energy, position): rank of each candidate
             int *ord = cand + nc;
             for (int a = tid; a < nc; a += kSelThreads) {
@@ -353,12 +364,13 @@ __device__ __forceinline__ void select_body(const KParams &kp, const Work &w, ld
                     const long long eb = he[ib];
                     rank += (eb < ea) || (eb == ea && ib < ia);
                 }
-                ord[rank] = ia;
+                if (LD_IN(nc + rank, ns + 4, CK_SEL_START))
+                    ord[rank] = ia;
             }
             __syncthreads();
             if (tid == 0) {
                 int na = 0;
-                for (int a = 0; a < nc && na < kp.max_lanes; ++a) {
+                for (int a = 0; a < nc && na < kp.max_lanes && LD_IN(na, LD_MAX_LANES, CK_SEL_LANES); ++a) {
                     const int c = ord[a];
                     bool ok = true;
                     for (int b = 0; b < na; ++b)

@@ -20,6 +20,8 @@ __device__ __forceinline__ void median_body(const KParams &kp, const Work &w, co
 {
     __shared__ uint8_t tile[(kMedRows + 2 * kMedMaxRho) * (kMedCols + 2 * kMedMaxRho)];
     const int W = kp.W, H = kp.H, rho = kp.rho;
+    if (!LD_IN(rho, kMedMaxRho + 1, CK_MED_TILE))   // the halo the shared tile holds
+        return;
     const int x0 = bx * kMedCols, y0 = by * kMedRows;
     const int u = x0 + (threadIdx.x & (kMedCols - 1)), v = y0 + threadIdx.x / kMedCols;
     const uint8_t *in = img + (size_t)f * H * W;

@@ -173,7 +173,10 @@ __device__ bool hypothesis(const KParams &kp, const int16_t *xs, const int16_t *
             blk = philox4x32_10(make_uint4(((uint32_t)stage << 24) | (uint32_t)round, (uint32_t)h, (uint32_t)(j >> 2), 0u),
                                 kp.key0, kp.key1);
         const uint32_t wv = (j & 3) == 0 ? blk.x : (j & 3) == 1 ? blk.y : (j & 3) == 2 ? blk.z : blk.w;
-        const int pt = list[(int)(((unsigned long long)wv * (unsigned long long)ns) >> 32)];
+        const int idx = (int)(((unsigned long long)wv * (unsigned long long)ns) >> 32);
+        if (!LD_IN(idx, ns, CK_FIT_SAMPLE))
+            continue;
+        const int pt = list[idx];
         bool dup = false;
         for (int q = 0; q < got; ++q)
             dup |= (pick[q] == pt) | (xs[pick[q]] == xs[pt]);
@@ -222,7 +225,8 @@ __device__ __forceinline__ void fit_body(const KParams &kp, const Work &w, const
     const FrameState fs0 = w.fs[f];
     if (stage == 1 && (fs0.flags & LD_F_NO_LANES))
         return;
-    const int n = w.npts[f * 2 + stage];
+    const int n0 = w.npts[f * 2 + stage];
+    const int n = LD_IN(n0, P + 1, CK_FIT_NPTS) ? n0 : 0;   // a point list holds at most P points
     const int16_t *gp = w.pts + ((size_t)f * 2 + stage) * 3 * P;
 
     unsigned char *p = smem;
@@ -413,7 +417,8 @@ __device__ __forceinline__ void fit_body(const KParams &kp, const Work &w, const
             inl[d] = 0;
         __syncthreads();
         for (int j = tid; j < n; j += kFitThreads)
-            inl[pid[j]] = member[j];
+            if (LD_IN(pid[j], kp.D, CK_FIT_ROW))
+                inl[pid[j]] = member[j];
         int flags = 0;
         if (fl & 1)
             flags |= LD_F_CAP_Y;
@@ -484,7 +489,8 @@ __device__ __forceinline__ void fit_body(const KParams &kp, const Work &w, const
             inl[v] = 0;
         __syncthreads();
         for (int j = tid; j < n; j += kFitThreads)
-            inl[pid[j]] = member[j];
+            if (LD_IN(pid[j], H, CK_FIT_ROW))
+                inl[pid[j]] = member[j];
         int flags = fs0.flags;
         if (fl & 1)
             flags |= LD_F_CAP_X;

@@ -59,8 +59,8 @@ __device__ __forceinline__ void vdisp_body(const KParams &kp, int32_t *__restric
     const int nb = (n - head) >> 2, tail0 = head + 4 * nb;
     if (tid < head + n - tail0) {
         const int off = tid < head ? tid : tail0 + (tid - head);
-        const int b = bin_of(__ldg(src + off));
-        if (b >= 0)
+        const int b = LD_IN(off, n, CK_VDISP_LOAD) ? bin_of(__ldg(src + off)) : -1;
+        if (b >= 0 && LD_IN((off / W) * Dp + b, nr * Dp, CK_VDISP_BIN))
             atomicAdd(&hist[(off / W) * Dp + b], 1);
     }
     // each warp takes one contiguous span of the 16-byte chunks (about one row), so a lane's successive
@@ -81,7 +81,8 @@ __device__ __forceinline__ void vdisp_body(const KParams &kp, int32_t *__restric
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             const int i = base + 32 * k + lane;
-            x[k] = i < w1 ? __ldg(body + i) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // 0 does not count
+            x[k] = i < w1 && LD_IN(head + 4 * i + 3, n, CK_VDISP_LOAD) ? __ldg(body + i)
+                                                                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // 0 does not count
         }
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
@@ -93,7 +94,7 @@ __device__ __forceinline__ void vdisp_body(const KParams &kp, int32_t *__restric
                 const bool ok = l[e] > 0.0f && b < (uint32_t)D;
                 const int key = ok ? (e < rw ? rb : rb + Dp) + (int)b : run_key;
                 const bool nk = key != run_key;
-                red_add_if(nk, hbase + 4u * (uint32_t)run_key, run_cnt);
+                red_add_if(nk && LD_IN(run_key, nr * Dp, CK_VDISP_RUN), hbase + 4u * (uint32_t)run_key, run_cnt);
                 run_cnt = (nk ? 0 : run_cnt) + (int)ok;
                 run_key = key;
             }
@@ -104,14 +105,15 @@ __device__ __forceinline__ void vdisp_body(const KParams &kp, int32_t *__restric
             }
         }
     }
-    red_add_if(run_cnt != 0, hbase + 4u * (uint32_t)run_key, run_cnt);
+    red_add_if(run_cnt != 0 && LD_IN(run_key, nr * Dp, CK_VDISP_RUN), hbase + 4u * (uint32_t)run_key, run_cnt);
     __syncthreads();
     // thread t writes row r = t mod nr of bins d = t / nr, t / nr + step, ... (one division per thread)
     int32_t *dst = myT + (size_t)f * D * H;
     const int step = kThreads / nr, r = tid % nr;
     if (tid < step * nr)
         for (int d = tid / nr; d < D; d += step)
-            dst[(size_t)d * H + r0 + r] = hist[r * Dp + d];
+            if (LD_IN(r0 + r, H, CK_VDISP_OUT))
+                dst[(size_t)d * H + r0 + r] = hist[r * Dp + d];
 }
 
 __global__ void __launch_bounds__(kThreads) k_vdisp(const KParams kp, int32_t *__restrict__ myT,

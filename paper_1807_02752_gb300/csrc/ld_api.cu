@@ -48,6 +48,27 @@ struct MixedGraph {
 
 }  // namespace
 
+#ifdef LD_CHECKED
+namespace {
+std::vector<std::pair<ld::CkRead, ld::CkReset>> &ck_registry()
+{
+    static std::vector<std::pair<ld::CkRead, ld::CkReset>> r;   // filled during static initialisation
+    return r;
+}
+// index == bound: the test fails and is recorded; nothing is accessed
+__global__ void k_ck_selftest(int n)
+{
+    if (!LD_IN(n, n, CK_SELFTEST))
+        return;
+}
+}  // namespace
+int ld::ck_register(ld::CkRead read, ld::CkReset reset)
+{
+    ck_registry().emplace_back(read, reset);
+    return (int)ck_registry().size();
+}
+#endif
+
 struct ld_handle {
     ld_params p{};
     int max_w = 0, max_h = 0, max_batch = 0;
@@ -1348,6 +1369,82 @@ int ld_debug_capture(ld_handle *h, int32_t on)
 }
 
 const char *ld_last_error(const ld_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int32_t ld_checked_build(void)
+{
+#ifdef LD_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int ld_check_status(int64_t out[4])
+{
+    if (!out)
+        return LD_E_ARG;
+    out[0] = out[1] = out[2] = out[3] = 0;
+#ifdef LD_CHECKED
+    cudaError_t e = cudaDeviceSynchronize();
+    for (const auto &fns : ck_registry()) {
+        unsigned long long w[4] = {0, 0, 0, 0};
+        if (e == cudaSuccess)
+            e = fns.first(w);
+        if (e != cudaSuccess)
+            break;
+        if (w[0] && !out[0]) {
+            out[1] = (int64_t)w[1];
+            out[2] = (int64_t)w[2];
+            out[3] = (int64_t)w[3];
+        }
+        out[0] += (int64_t)w[0];
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(nullptr, e, "check status");
+#endif
+    return LD_OK;
+}
+
+int ld_check_reset(void)
+{
+#ifdef LD_CHECKED
+    cudaError_t e = cudaDeviceSynchronize();
+    for (const auto &fns : ck_registry())
+        if (e == cudaSuccess)
+            e = fns.second();
+    if (e != cudaSuccess)
+        return cuda_fail(nullptr, e, "check reset");
+#endif
+    return LD_OK;
+}
+
+const char *ld_check_site_name(int32_t site)
+{
+    static const char *const names[ld::CK_N_SITES] = {
+        "none", "selftest",
+        "vdisp_bin", "vdisp_run", "vdisp_load", "vdisp_out",
+        "road_path", "road_pts",
+        "fit_npts", "fit_sample", "fit_row",
+        "grad_tile", "grad_glist", "grad_group", "grad_tap", "grad_edge", "grad_vote",
+        "vpx_tile", "vpx_vote", "vpx_voff", "vpx_stage", "vpx_path", "vpx_pts",
+        "m1_edge", "m1_col", "m1_chunk",
+        "energy_start", "energy_col", "energy_row",
+        "select_start", "select_lanes", "track_col",
+        "median_tile",
+    };
+    return site >= 0 && site < ld::CK_N_SITES ? names[site] : "?";
+}
+
+int ld_check_selftest(void)
+{
+#ifdef LD_CHECKED
+    k_ck_selftest<<<1, 1>>>(7);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LD_OK : cuda_fail(nullptr, e, "check self-test");
+#else
+    return fail(nullptr, LD_E_STATE, "not the bounds-checked library (LD_CHECKED)");
+#endif
+}
 
 void ld_destroy(ld_handle *h)
 {

@@ -20,6 +20,65 @@ constexpr int kWrEntries = 768;       // Q15 range weight of dI at index 256 + d
 constexpr int kSentinel = 511;        // image value marking taps outside the frame
 constexpr int kClsTables = 24;        // distance classes of the largest bilateral window (rho = 5: 20 used)
 
+// Bounds-checked build (-DLD_CHECKED, lib/libld_checked.so).  LD_IN(i, n, site) holds when 0 <= i < n.
+// Otherwise it counts a failure in this translation unit's error word, records the first one (site,
+// index, bound) and is false, so the guarded access is skipped: a checked kernel never reads or writes
+// outside its buffers and never traps.  In the regular build LD_IN is the constant true and the guards
+// compile away.  Checked: every index computed from data (histogram bins, vote and edge columns, decoded
+// backtrack steps, path cells, point-list and sample indices, track columns, list decodes), every append
+// to a fixed-capacity list, and each kernel's tile against its frame and buffers.
+enum CkSite : int {
+    CK_NONE = 0,
+    CK_SELFTEST,
+    CK_VDISP_BIN, CK_VDISP_RUN, CK_VDISP_LOAD, CK_VDISP_OUT,
+    CK_ROAD_PATH, CK_ROAD_PTS,
+    CK_FIT_NPTS, CK_FIT_SAMPLE, CK_FIT_ROW,
+    CK_GRAD_TILE, CK_GRAD_GLIST, CK_GRAD_GROUP, CK_GRAD_TAP, CK_GRAD_EDGE, CK_GRAD_VOTE,
+    CK_VPX_TILE, CK_VPX_VOTE, CK_VPX_VOFF, CK_VPX_STAGE, CK_VPX_PATH, CK_VPX_PTS,
+    CK_M1_EDGE, CK_M1_COL, CK_M1_CHUNK,
+    CK_EN_START, CK_EN_COL, CK_EN_ROW,
+    CK_SEL_START, CK_SEL_LANES, CK_TRACK_COL,
+    CK_MED_TILE,
+    CK_N_SITES
+};
+}  // namespace ld
+
+#ifdef LD_CHECKED
+namespace ld {
+using CkRead = cudaError_t (*)(unsigned long long *out4);
+using CkReset = cudaError_t (*)();
+int ck_register(CkRead read, CkReset reset);   // ld_api.cu: collects every translation unit's error word
+}  // namespace ld
+namespace {
+__device__ unsigned long long g_ld_ck[4];      // failures, first site, first index, first bound
+__device__ __noinline__ bool ld_ck_fail(long long i, long long n, int site)
+{
+    if (atomicAdd(&g_ld_ck[0], 1ull) == 0ull) {
+        g_ld_ck[1] = (unsigned long long)site;
+        g_ld_ck[2] = (unsigned long long)i;
+        g_ld_ck[3] = (unsigned long long)n;
+    }
+    return false;
+}
+__device__ __forceinline__ bool ld_ck_in(long long i, long long n, int site)
+{
+    return (i >= 0 && i < n) ? true : ld_ck_fail(i, n, site);
+}
+cudaError_t ld_ck_read(unsigned long long *out4) { return cudaMemcpyFromSymbol(out4, g_ld_ck, sizeof(g_ld_ck)); }
+cudaError_t ld_ck_reset()
+{
+    static const unsigned long long zero[4] = {0, 0, 0, 0};
+    return cudaMemcpyToSymbol(g_ld_ck, zero, sizeof(zero));
+}
+[[maybe_unused]] const int ld_ck_registered = ld::ck_register(ld_ck_read, ld_ck_reset);
+}  // namespace
+#define LD_IN(i, n, site) ld_ck_in((long long)(i), (long long)(n), (int)(::ld::site))
+#else
+#define LD_IN(i, n, site) true
+#endif
+
+namespace ld {
+
 // Per-launch constants, passed by value (they live in the kernel-parameter constant bank).
 struct KParams {
     int32_t W, H, D, n_frames;

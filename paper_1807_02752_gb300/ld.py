@@ -12,6 +12,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libld.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "lib", "libld_checked.so")   # build.build(checked=True)
 
 MAX_LANES = 8
 LD_STATIC_SCRATCH_BYTES = 8 << 20
@@ -83,17 +84,18 @@ RESULT_DTYPE = np.dtype([("tag", "<u8"), ("stream_id", "<i4"), ("w", "<i4"), ("h
                          ("seq", "<i8"), ("latency_ms", "<f8"), ("lanes", LANES_DTYPE)])
 assert RESULT_DTYPE.itemsize == 232
 
-_lib = None
+_libs = {}
 
 
-def load():
-    """Load lib/libld.so (built by build.py / __graft_entry__.build())."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing (run paper_1807_02752_gb300/build.py)")
-    L = C.CDLL(LIB_PATH)
+def load(checked: bool = False):
+    """Load lib/libld.so (built by build.py / __graft_entry__.build()), or with checked=True the
+    bounds-checked build lib/libld_checked.so (build.build(checked=True))."""
+    path = LIB_CHECKED_PATH if checked else LIB_PATH
+    if path in _libs:
+        return _libs[path]
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run paper_1807_02752_gb300/build.py)")
+    L = C.CDLL(path)
     p, i32, P = C.c_void_p, C.c_int32, C.POINTER(Params)
     L.ld_params_default.argtypes = [P]
     L.ld_params_default.restype = None
@@ -194,8 +196,29 @@ def load():
                  "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs", "ld_detect_learned",
                  "ld_net_debug_get"):
         getattr(L, name).restype = C.c_int
-    _lib = L
+    L.ld_checked_build.argtypes = []
+    L.ld_checked_build.restype = i32
+    L.ld_check_status.argtypes = [p]
+    L.ld_check_status.restype = C.c_int
+    L.ld_check_reset.argtypes = []
+    L.ld_check_reset.restype = C.c_int
+    L.ld_check_site_name.argtypes = [i32]
+    L.ld_check_site_name.restype = C.c_char_p
+    L.ld_check_selftest.argtypes = []
+    L.ld_check_selftest.restype = C.c_int
+    _libs[path] = L
     return L
+
+
+def check_status(L) -> dict:
+    """Bounds-check failures recorded by the kernels of library L (ld_check_status): the count and the
+    first failure's site, index and bound."""
+    out = (C.c_int64 * 4)()
+    rc = L.ld_check_status(out)
+    if rc != OK:
+        raise LDError(rc, L.ld_last_error(None).decode())
+    return {"failures": int(out[0]), "site": L.ld_check_site_name(int(out[1])).decode(), "index": int(out[2]),
+            "bound": int(out[3])}
 
 
 EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_detect_host", "ld_detect_timed",
@@ -207,7 +230,8 @@ EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_de
             "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
             "ld_detect_learned", "ld_net_debug_size", "ld_net_debug_get", "ld_net_status", "ld_net_last_error", "ld_net_destroy",
             "ld_stereo_params_default", "ld_stereo_create", "ld_stereo_run", "ld_stereo_run_timed", "ld_detect_stereo",
-            "ld_stereo_maps", "ld_stereo_last_error", "ld_stereo_destroy"]
+            "ld_stereo_maps", "ld_stereo_last_error", "ld_stereo_destroy", "ld_checked_build", "ld_check_status",
+            "ld_check_reset", "ld_check_site_name", "ld_check_selftest"]
 
 
 def launch_names():
@@ -257,10 +281,11 @@ def lanes_to_dicts(arr: np.ndarray):
 class Detector:
     """A library handle: workspace for frames up to max_w x max_h and batches up to max_batch."""
 
-    def __init__(self, max_w: int, max_h: int, max_batch: int, params: Params | None = None, stream=None):
+    def __init__(self, max_w: int, max_h: int, max_batch: int, params: Params | None = None, stream=None,
+                 lib=None):
         import torch
 
-        self.L = load()
+        self.L = lib if lib is not None else load()
         self.params = params if params is not None else default_params()
         if stream is None:
             stream = torch.cuda.current_stream()

@@ -296,3 +296,31 @@ def make_batch(cfg: SceneConfig, n_frames: int, seed: int = BASE_SEED, first_fra
 
 def with_size(cfg: SceneConfig, **kw) -> SceneConfig:
     return dataclasses.replace(cfg, **kw)
+
+
+def make_tiny_frame(w: int, h: int, n_disp: int, seed: int):
+    """A small adversarial frame (seeded) for the smallest shapes the library accepts (16 x 16 and up), where
+    the road scenes above do not fit: a disparity ramp from a random horizon row down to about n_disp - 1.5
+    at the bottom row, with noise; one box of constant disparity; about 3 % NaN, 2 % +inf, 3 % zero, 2 %
+    negative and 2 % at or above n_disp.  The image is grey noise with one to three bright stripes of random
+    slope below the horizon.  Returns (disparity float32 [h][w], image uint8 [h][w])."""
+    rng = np.random.default_rng(seed)
+    v = np.arange(h, dtype=np.float64)[:, None] * np.ones((1, w))
+    vh = int(rng.integers(h // 4, h // 2 + 1))
+    disp = np.clip((v - vh) * (n_disp - 1.5) / max(1, h - 1 - vh), 0, None) + rng.normal(0, 0.3, (h, w))
+    bw, bh = max(2, w // 5), max(2, h // 5)
+    bx, by = int(rng.integers(0, w - bw)), int(rng.integers(0, h - bh))
+    disp[by:by + bh, bx:bx + bw] = rng.uniform(1, n_disp - 1)
+    r = rng.random((h, w))
+    disp[r < 0.03] = np.nan
+    disp[(r >= 0.03) & (r < 0.05)] = np.inf
+    disp[(r >= 0.05) & (r < 0.08)] = 0.0
+    disp[(r >= 0.08) & (r < 0.10)] = -rng.uniform(0, 5)
+    disp[(r >= 0.10) & (r < 0.12)] = n_disp + rng.uniform(0, 40)
+    img = 70 + rng.normal(0, 6, (h, w))
+    for _ in range(int(rng.integers(1, 4))):
+        c0, slope = rng.uniform(0, w), rng.uniform(-1.5, 1.5)
+        for vv in range(vh, h):
+            c = int(round(c0 + slope * (vv - vh)))
+            img[vv, max(0, c - 1):max(0, c + 2)] = 200 + rng.normal(0, 10)
+    return disp.astype(np.float32), np.clip(img, 0, 255).astype(np.uint8)

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def ldmod():
     from paper_1807_02752_gb300 import build, ld
     build.build()
-    ld._lib = None
+    ld._libs.clear()
     return ld
 
 
@@ -81,3 +81,15 @@ def test_object_entry_points_reject_null_handles_without_device(ldmod):
     assert L.ld_server_set_learned(None, None, 0) == ldmod.E_ARG
     assert L.ld_detect_groups(None, None, 1) == ldmod.E_ARG
     assert ctypes.sizeof(ldmod.Group) == 40
+
+
+def test_checked_build_loads_and_exports(ldmod):
+    """The bounds-checked variant builds from the same sources and exports the same entry points."""
+    from paper_1807_02752_gb300 import build
+    build.build(checked=True)
+    L = ldmod.load(checked=True)
+    assert L.ld_checked_build() == 1
+    assert ldmod.load().ld_checked_build() == 0
+    for name in ldmod.EXPORTED:
+        assert hasattr(L, name), f"{name} missing from the checked library"
+    assert L.ld_check_site_name(1) == b"selftest" and L.ld_check_site_name(10 ** 6) == b"?"

@@ -1,0 +1,114 @@
+"""The bounds-checked build (LD_CHECKED, lib/libld_checked.so).
+
+Its kernels test every data-derived index, every append to a fixed-capacity list and each tile against its
+frame before the access, and count a failure instead of trapping (include/ld.h, ld_check_status).  These
+tests run the whole path through that library on the smallest shapes it accepts, with adversarial
+disparities (NaN, +inf, zero, negative, beyond D), and on the camera sizes.  They require a clean status
+and, for every frame, every stage dump equal to the oracle's.  The recorder itself is checked with
+ld_check_selftest, which evaluates one failing test and accesses nothing.
+"""
+import numpy as np
+import pytest
+
+from paper_1807_02752_gb300 import ld, scenes
+from gpu_util import compare_frame
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def checked():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1807_02752_gb300 import build
+    build.build(checked=True)
+    L = ld.load(checked=True)
+    assert L.ld_checked_build() == 1
+    return torch, L
+
+
+def _clean(L):
+    st = ld.check_status(L)
+    assert st["failures"] == 0, f"bounds-check failures: {st}"
+
+
+def test_selftest_records_and_resets(checked):
+    torch, L = checked
+    assert L.ld_check_reset() == ld.OK
+    _clean(L)
+    assert L.ld_check_selftest() == ld.OK
+    assert ld.check_status(L) == {"failures": 1, "site": "selftest", "index": 7, "bound": 7}
+    assert L.ld_check_reset() == ld.OK
+    _clean(L)
+    R = ld.load()                      # the regular library: no checks, a clean status, no self-test
+    assert R.ld_checked_build() == 0
+    assert ld.check_status(R)["failures"] == 0
+    assert R.ld_check_selftest() == ld.E_STATE
+
+
+def _run(torch, L, frames, p, capture=True):
+    disp = np.stack([f[0] for f in frames])
+    img = np.stack([f[1] for f in frames])
+    n, H, W = disp.shape
+    det = ld.Detector(W, H, n, p, lib=L)
+    try:
+        if capture:
+            det.capture(True)
+        assert L.ld_check_reset() == ld.OK
+        out = det.detect(torch.from_numpy(disp).cuda(), torch.from_numpy(img).cuda())
+        torch.cuda.synchronize()
+        _clean(L)
+        rows = ld.Detector.lanes(out)
+        for k in range(n):
+            compare_frame(det, rows[k], k, disp[k], img[k], p)
+    finally:
+        det.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 4), (17, 16, 4), (24, 18, 8), (70, 33, 16), (130, 50, 24),
+                                   (257, 67, 32)])
+def test_tiny_shapes(checked, shape):
+    torch, L = checked
+    w, h, D = shape
+    frames = [scenes.make_tiny_frame(w, h, D, 900 + k) for k in range(4)]
+    _run(torch, L, frames, ld.default_params(n_disp=D))
+
+
+@pytest.mark.parametrize("kw", [{"bilateral": 0}, {"bilateral": 2}, {"dp_literal": 1}, {"tau_y": 15},
+                                {"tau_x": 7, "chi": 5}, {"lambda_g": 0}])
+def test_tiny_shapes_param_variants(checked, kw):
+    torch, L = checked
+    frames = [scenes.make_tiny_frame(70, 33, 16, 950 + k) for k in range(3)]
+    _run(torch, L, frames, ld.default_params(n_disp=16, **kw))
+
+
+def test_camera_size_and_groups(checked):
+    """Four 1242x375 frames at D = 256 through the checked library, then a mixed-size call (one launch per
+    stage over three tiny sizes): a clean status, and every frame the oracle's."""
+    torch, L = checked
+    cfg = scenes.with_size(scenes.BATCH64_1242x375, n_disp=256)
+    frames = [scenes.make_frame(cfg, 1200 + k)[:2] for k in range(4)]
+    _run(torch, L, frames, ld.default_params(n_disp=256), capture=False)
+    p = ld.default_params(n_disp=16)
+    groups = []
+    for g, (w, h) in enumerate(((70, 33), (40, 20), (130, 50))):
+        fr = [scenes.make_tiny_frame(w, h, 16, 1300 + 10 * g + k) for k in range(2)]
+        groups.append((torch.from_numpy(np.stack([f[0] for f in fr])).cuda(),
+                       torch.from_numpy(np.stack([f[1] for f in fr])).cuda()))
+    stream = torch.cuda.Stream()
+    det = ld.Detector(130, 50, 6, p, stream=stream, lib=L)
+    try:
+        assert L.ld_check_reset() == ld.OK
+        with torch.cuda.stream(stream):
+            for mixed in (False, True):
+                outs = det.detect_groups(groups, mixed=mixed)
+                torch.cuda.synchronize()
+                _clean(L)
+                for (d, i), o in zip(groups, outs):
+                    res = ld.Detector.lanes(o)
+                    dn, im = d.cpu().numpy(), i.cpu().numpy()
+                    for k in range(dn.shape[0]):
+                        compare_frame(None, res[k], k, dn[k], im[k], p, stages=False)
+    finally:
+        det.close()
