@@ -298,7 +298,9 @@ const char *ld_launch_name(int32_t k);
  * Profiling form of ld_detect (DEVICE buffers as ld_detect): enqueues the same kernels without graph
  * capture, with a CUDA event recorded on the handle's stream before the first kernel and after each one,
  * waits for the stream, and writes the duration of launch k in milliseconds to ms_out[k]
- * (ld_launches_per_detect() entries).  Errors as ld_detect.
+ * (ld_launches_per_detect() entries).  The stream is held at a host function (at most one second) until
+ * every launch is enqueued, so the kernels run back to back and no interval holds host enqueue time; the
+ * buffer resets of the later stages are made before the first event.  Errors as ld_detect.
  */
 int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t h_px,
                     int32_t n_frames, ld_lanes *out_lanes, float *ms_out);

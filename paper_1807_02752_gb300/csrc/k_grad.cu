@@ -193,9 +193,8 @@ __device__ __forceinline__ void grad_body(const KParams &kp, const Work &w, cons
     uint8_t *live = smem + T.o_live;                                  // [nr][IWO] owned road pixels left after pruning
     uint8_t *ibf = smem + T.o_ibf;                                    // [nr + 2][IWB] bilateral output, row b = v - r0 + 1
     uint16_t *glist = reinterpret_cast<uint16_t *>(smem + T.o_gl);    // groups (b << 8 | g) that need the filter
-    float *rowF = reinterpret_cast<float *>(smem + T.o_row);
-    float *rowVy = rowF + nr;
-    int *cnt = reinterpret_cast<int *>(rowVy + nr);                   // [1] groups that need the filter
+    float *rowVy = reinterpret_cast<float *>(smem + T.o_row);
+    int *cnt = reinterpret_cast<int *>(rowVy + 2 * nr);               // [1] groups that need the filter
 
     // per-class weight tables T_c[a] = (ws_c * wr(a) + 2^14) >> 15 for a = |I(i,j) - I(u,v)|, built once per
     // handle (zero from a = 256 on), copied in 16-byte pieces with every load issued before the first store
@@ -213,39 +212,63 @@ __device__ __forceinline__ void grad_body(const KParams &kp, const Work &w, cons
                 reinterpret_cast<uint4 *>(tabs)[tid + k * kThreads] = tv[k];
     }
     const float *rows = w.rows + (size_t)f * 3 * H;
-    if (tid < nr) {
-        // rows that hold no interior road pixel get f(v) = NaN, which fails the on-road test below
-        const int v = r0 + tid;
-        rowF[tid] = (v >= vtop && v >= 1 && v <= H - 2) ? __ldg(rows + v) : __int_as_float(0x7fc00000);
-        rowVy[tid] = __ldg(rows + H + v);
-    }
+    if (tid < nr)
+        rowVy[tid] = __ldg(rows + H + r0 + tid);   // V_py(v) of the owned rows, for the votes
     if (tid == 0)
         *cnt = 0;
-    // image region, coalesced byte loads: consecutive lanes read consecutive bytes of a row
-    const uint8_t *im = img + (size_t)f * H * W;
-    for (int tr = warp; tr < T.TR; tr += NW) {
-        const int v = rbase + tr;
-        const bool vin = v >= 0 && v < H;
-        const uint8_t *src = im + (size_t)(vin ? v : 0) * W;
-        for (int tc = lane; tc < T.TWP; tc += 32) {
-            const int c = cbase + tc;
-            tile[tr * T.TWP + tc] = (uint16_t)(vin && c >= 0 && c < W ? 2u * __ldg(src + c) : 2u * kSentinel);
-        }
-    }
-    __syncthreads();  // rowF
-    // road mask of the owned pixels: l > 0 with |l - f(v)| <= varpi (an infinite or NaN l fails the second
-    // test because f(v) is finite), v >= v_top, 1 <= u <= W-2
+    // road mask of the owned pixels first: l > 0 with |l - f(v)| <= varpi (an infinite or NaN l fails the
+    // second test because f(v) is finite), v >= v_top, 1 <= u <= W-2.  A warp takes two rows at a time with
+    // all of their loads in flight, f(v) read directly (rows off the road get NaN, which fails the test).
     const float *dsrc = disp + ((size_t)f * H + r0) * W;
-    for (int r = warp; r < nr; r += NW)
-        for (int x = lane; x < T.IWO; x += 32) {
-            const int u = 4 * j0 + x;
-            bool m = false;
-            if (u >= 1 && u <= W - 2) {
-                const float l = __ldg(dsrc + (size_t)r * W + u);
-                m = l > 0.0f && fabsf(__fsub_rn(l, rowF[r])) <= kp.varpi;
+    constexpr int KX = 4 * kGroups / 32;   // 32-pixel chunks of an owned row
+    for (int rr = 2 * warp; rr < nr; rr += 2 * NW) {
+        float lv[2][KX], fv[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = rr + q, v = r0 + r;
+            fv[q] = r < nr && v >= vtop && v >= 1 && v <= H - 2 ? __ldg(rows + v) : __int_as_float(0x7fc00000);
+#pragma unroll
+            for (int k = 0; k < KX; ++k) {
+                const int u = 4 * j0 + lane + 32 * k;
+                lv[q][k] = r < nr && lane + 32 * k < T.IWO && u >= 1 && u <= W - 2 ? __ldg(dsrc + (size_t)r * W + u)
+                                                                                    : 0.0f;
             }
-            live[r * T.IWO + x] = (uint8_t)m;
         }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int k = 0; k < KX; ++k) {
+                const int r = rr + q, x = lane + 32 * k;
+                if (r < nr && x < T.IWO)
+                    live[r * T.IWO + x] = (uint8_t)(lv[q][k] > 0.0f && fabsf(__fsub_rn(lv[q][k], fv[q])) <= kp.varpi);
+            }
+    }
+    // image region, coalesced byte loads: consecutive lanes read consecutive bytes of a row.  A warp takes
+    // two tile rows at a time and issues all of their loads before its first store.
+    const uint8_t *im = img + (size_t)f * H * W;
+    constexpr int KC = (4 * kGroups + 2 * RHO + 11 + 31) / 32;   // 32-column chunks of a tile row (>= TWP / 32)
+    for (int tr0 = 2 * warp; tr0 < T.TR; tr0 += 2 * NW) {
+        uint32_t px[2][KC];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int v = rbase + tr0 + q;
+            const bool vin = tr0 + q < T.TR && v >= 0 && v < H;
+            const uint8_t *src = im + (size_t)(vin ? v : 0) * W;
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const int c = cbase + lane + 32 * k;
+                px[q][k] = vin && c >= 0 && c < W ? 2u * __ldg(src + c) : 2u * kSentinel;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const int tc = lane + 32 * k;
+                if (tr0 + q < T.TR && tc < T.TWP)
+                    tile[(tr0 + q) * T.TWP + tc] = (uint16_t)px[q][k];
+            }
+    }
     __syncthreads();
     // Exact pruning (see the comment at the top): a group is flat when the image range over columns
     // 4g - RHO - 4 .. 4g + RHO + 5 (a superset of its 3x3 neighbours' windows: tile columns 4 (g - j0) ..)

@@ -4,7 +4,10 @@
 // overlap the other half's dense kernels), calls over groups of frames of several sizes, the host-buffer
 // path and the debug getters.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -318,19 +321,30 @@ int enqueue_range(ld_handle *h, const ld::KParams &kp, const ld::Work &w, const 
                   ld_lanes *out, cudaStream_t s, bool timed, int first, int last)
 {
     cudaError_t e = cudaSuccess;
-    if (timed && (e = cudaEventRecord(h->ev[first], s)) != cudaSuccess)
-        return cuda_fail(h, e, "event record");
-    for (int k = first; k < last; ++k) {
-        // stage capture: I^bf starts at -1 (not computed), m_x at 0 (rows above v_top)
-        const size_t npx = (size_t)kp.n_frames * kp.H * kp.W;
+    const size_t npx = (size_t)kp.n_frames * kp.H * kp.W;
+    // buffer resets before stage k: stage capture (I^bf starts at -1, not computed; m_x at 0, rows above
+    // v_top) and the per-row lists the gradient kernel's tiles append their edges and votes to.  No earlier
+    // stage touches these buffers, so the timed form makes them before its first event, which keeps them
+    // out of the per-kernel times.
+    auto resets = [&](int k) -> int {
         if (k == 3 && w.dbg_ibf && (e = cudaMemsetAsync(w.dbg_ibf, 0xff, npx * 2, s)) != cudaSuccess)
             return cuda_fail(h, e, "capture reset");
-        // the gradient kernel's tiles append their edges and votes to the per-row lists
         if (k == 3 && ((e = cudaMemsetAsync(w.ecount, 0, (size_t)kp.n_frames * kp.H * 4, s)) != cudaSuccess ||
                        (e = cudaMemsetAsync(w.vcount, 0, (size_t)kp.n_frames * kp.H * 4, s)) != cudaSuccess))
             return cuda_fail(h, e, "edge count reset");
         if (k == 4 && w.dbg_mx && (e = cudaMemsetAsync(w.dbg_mx, 0, npx * 4, s)) != cudaSuccess)
             return cuda_fail(h, e, "capture reset");
+        return LD_OK;
+    };
+    if (timed)
+        for (int k = first; k < last; ++k)
+            if (resets(k) != LD_OK)
+                return LD_E_CUDA;
+    if (timed && (e = cudaEventRecord(h->ev[first], s)) != cudaSuccess)
+        return cuda_fail(h, e, "event record");
+    for (int k = first; k < last; ++k) {
+        if (!timed && resets(k) != LD_OK)
+            return LD_E_CUDA;
         nvtxRangePushA(kLaunchNames[k]);   // a profiler timeline shows each stage's enqueue by name
         switch (k) {
         case 0: e = ld::launch_vdisp(kp, w, disp, s); break;
@@ -1133,6 +1147,33 @@ int ld_detect_mixed(ld_handle *h, const ld_group *groups, int32_t n_groups)
     return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "graph launch");
 }
 
+}  // extern "C"
+
+namespace {
+// Holds a stream at a host function until the enqueueing thread opens it (at most one second).
+struct StartGate {
+    std::mutex m;
+    std::condition_variable cv;
+    bool is_open = false;
+    void open()
+    {
+        {
+            std::lock_guard<std::mutex> g(m);
+            is_open = true;
+        }
+        cv.notify_all();
+    }
+};
+void CUDART_CB start_gate_wait(void *arg)
+{
+    StartGate *g = static_cast<StartGate *>(arg);
+    std::unique_lock<std::mutex> lk(g->m);
+    g->cv.wait_for(lk, std::chrono::seconds(1), [&] { return g->is_open; });
+}
+}  // namespace
+
+extern "C" {
+
 int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t w, int32_t hh, int32_t n_frames,
                     ld_lanes *out_lanes, float *ms_out)
 {
@@ -1147,10 +1188,19 @@ int ld_detect_timed(ld_handle *h, const float *disp, const uint8_t *img, int32_t
     h->last_n = n_frames;
     h->have_last = true;
     h->dbg_valid = h->dbg != nullptr;
+    // the stream waits at a host gate until every launch is enqueued, so the kernels run back to back as
+    // in a captured call and no interval holds host enqueue time
+    StartGate gate;
+    cudaError_t e = cudaLaunchHostFunc(h->stream, start_gate_wait, &gate);
+    if (e != cudaSuccess)
+        return cuda_fail(h, e, "start gate");
     rc = enqueue(h, kp, disp, img, out_lanes, true);
-    if (rc != LD_OK)
+    gate.open();
+    if (rc != LD_OK) {
+        cudaStreamSynchronize(h->stream);   // the gate's host function has returned before it goes
         return rc;
-    cudaError_t e = cudaEventSynchronize(h->ev[kLaunches]);
+    }
+    e = cudaEventSynchronize(h->ev[kLaunches]);
     for (int k = 0; k < kLaunches && e == cudaSuccess; ++k)
         e = cudaEventElapsedTime(&ms_out[k], h->ev[k], h->ev[k + 1]);
     return e == cudaSuccess ? LD_OK : cuda_fail(h, e, "event timing");
