@@ -31,7 +31,7 @@ namespace ld {
 
 namespace {
 
-constexpr int kFitThreads = 512;
+constexpr int kFitThreads = 256;
 constexpr int kNW = kFitThreads / 32;
 
 __device__ __forceinline__ double p2d(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
