@@ -333,9 +333,10 @@ def test_trained_network_gains_over_untrained_and_raw_map(torch_cuda):
     2,000,000 on, disjoint from the training frames): the learned form's lanes agree with the exhaustive
     search's far more often with the package's trained weights than with the untrained initial weights,
     and at a small budget (top_k 16, about 3 % of the starts evaluated) more often than when the starts are
-    ranked by the raw input map itself; at top_k 96 the trained form agrees on at least 98 % (on 2,000
-    held-out frames: 0.954 against 0.869 at top_k 16, 0.970 against 0.760 untrained at top_k 32, 0.995 at
-    top_k 96)."""
+    ranked by the raw input map itself.  At the bench's operating point (top_k 96, about 16 % of the starts)
+    the trained form agrees on at least 99 % and is within 0.01 of ranking by the raw map, which is as good
+    there: the network gains nothing at that budget (on 2,000 held-out frames: 0.954 against 0.869 at
+    top_k 16, 0.970 against 0.760 untrained at top_k 32, 0.995 against 0.997 at top_k 96)."""
     import os
 
     from paper_1807_02752_gb300 import train_proposal as T
@@ -365,11 +366,12 @@ def test_trained_network_gains_over_untrained_and_raw_map(torch_cuda):
     try:
         a16 = {"trained": mean_agreement(trained, None, 16), "raw map": mean_agreement(None, raw_map, 16)}
         a32 = {"trained": mean_agreement(trained, None, 32), "untrained": mean_agreement(untrained, None, 32)}
-        a96 = mean_agreement(trained, None, 96)
+        a96 = {"trained": mean_agreement(trained, None, 96), "raw map": mean_agreement(None, raw_map, 96)}
         print("agreement, top_k 16:", a16, "top_k 32:", a32, "top_k 96:", a96)
         assert a32["trained"] >= a32["untrained"] + 0.1
         assert a16["trained"] >= a16["raw map"] + 0.03
-        assert a96 >= 0.98
+        assert a96["trained"] >= 0.99
+        assert a96["trained"] >= a96["raw map"] - 0.01
     finally:
         net.close()
         det.close()
