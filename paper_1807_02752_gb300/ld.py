@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libld.so")
 LIB_CHECKED_PATH = os.path.join(HERE, "lib", "libld_checked.so")   # build.build(checked=True)
 
 MAX_LANES = 8
+MAX_W, MAX_H, MAX_D = 4096, 1088, 256   # LD_MAX_W, LD_MAX_H, LD_MAX_D: the largest frame a handle takes
 LD_STATIC_SCRATCH_BYTES = 8 << 20
 OK, E_ARG, E_CUDA, E_NOMEM, E_STATE = 0, -1, -2, -3, -4
 F_NO_ROAD, F_CAP_Y, F_DEGEN_Y, F_CAP_X, F_DEGEN_X, F_NO_LANES, F_FALLBACK = 1, 2, 4, 8, 16, 32, 64

@@ -93,3 +93,10 @@ def test_checked_build_loads_and_exports(ldmod):
     for name in ldmod.EXPORTED:
         assert hasattr(L, name), f"{name} missing from the checked library"
     assert L.ld_check_site_name(1) == b"selftest" and L.ld_check_site_name(10 ** 6) == b"?"
+
+
+def test_size_limits_match_header(ldmod):
+    hdr = open(os.path.join(ROOT, "include", "ld.h")).read()
+    for name, val in (("LD_MAX_W", ldmod.MAX_W), ("LD_MAX_H", ldmod.MAX_H), ("LD_MAX_D", ldmod.MAX_D),
+                      ("LD_MAX_LANES", ldmod.MAX_LANES)):
+        assert int(re.search(r"#define %s (\d+)" % name, hdr).group(1)) == val, name

@@ -112,3 +112,12 @@ def test_camera_size_and_groups(checked):
                         compare_frame(None, res[k], k, dn[k], im[k], p, stages=False)
     finally:
         det.close()
+
+
+def test_maximum_frame_size_checked(checked):
+    """One 4096 x 1088 frame at D = 256 (the handle limits) through the checked library: a clean status and
+    every stage the oracle's."""
+    torch, L = checked
+    cfg = scenes.with_size(scenes.HD_1920x1080, width=ld.MAX_W, height=ld.MAX_H, n_disp=ld.MAX_D)
+    frames = [scenes.make_frame(cfg, 1400)[:2]]
+    _run(torch, L, frames, ld.default_params(n_disp=cfg.n_disp))

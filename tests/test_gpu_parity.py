@@ -152,6 +152,18 @@ def test_wide_frames_chunked_m1(torch_cuda):
             compare_frame(det, res[f], f, disp[f], img[f], p)
 
 
+def test_maximum_frame_size(torch_cuda):
+    """The largest frame a handle accepts (LD_MAX_W x LD_MAX_H = 4096 x 1088) at the most disparity bins
+    (LD_MAX_D = 256): every stage, m_x and I^bf against the oracle."""
+    cfg = scenes.with_size(scenes.HD_1920x1080, width=ld.MAX_W, height=ld.MAX_H, n_disp=ld.MAX_D)
+    disp, img, _ = scenes.make_batch(cfg, 1, first_frame=11)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    det = _captured(cfg.width, cfg.height, 1, p)
+    res = _run(torch_cuda, det, disp, img)
+    compare_frame(det, res[0], 0, disp[0], img[0], p)
+    det.close()
+
+
 def test_graph_replay_and_host_path_agree(torch_cuda):
     torch = torch_cuda
     cfg = scenes.SINGLE_1242x375
