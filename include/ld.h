@@ -482,6 +482,12 @@ int ld_net_create(ld_handle *h, int32_t training, ld_net **out);
 /* Copy LD_NET_PARAMS floats in as the master weights; resets the Adam moments and step count. */
 int ld_net_set_params(ld_net *net, const float *params);
 int ld_net_get_params(ld_net *net, float *params);
+/* Form of the inference forward (ld_net_forward, ld_detect_learned): on != 0 runs all four layers and the
+ * head in one kernel per 32 x 16-cell tile with the activations kept on chip; 0 (the default, the faster
+ * form on GB300) runs one kernel per layer through device memory.  The logits and heatmap values are identical on every cell the road
+ * rows need (the two forms issue the same MMAs); the per-layer form also computes rows above them.  Waits
+ * for the handle's stream; drops the captured learned calls.  Training always runs per layer. */
+int ld_net_set_fused(ld_net *net, int32_t on);
 /* logits[n][mh][mw] of the block sums xsum[n][mh][mw] of frames of w x h pixels. */
 int ld_net_forward(ld_net *net, const int32_t *xsum, int32_t w, int32_t h_px, int32_t n_frames, float *logits);
 /* Gradient of the mean loss over n frames (grad: LD_NET_PARAMS floats) and the loss (1 float); labels are

@@ -197,19 +197,16 @@ __device__ __forceinline__ void grad_body(const KParams &kp, const Work &w, cons
     int *cnt = reinterpret_cast<int *>(rowVy + 2 * nr);               // [1] groups that need the filter
 
     // per-class weight tables T_c[a] = (ws_c * wr(a) + 2^14) >> 15 for a = |I(i,j) - I(u,v)|, built once per
-    // handle (zero from a = 256 on), copied in 16-byte pieces with every load issued before the first store
+    // handle (zero from a = 256 on), copied asynchronously in 16-byte pieces (cp.async): the filter is the
+    // first reader, so the copy overlaps the staging, flatness and compaction phases
     {
-        constexpr int kTabLoads = (kClsTables * kTabBytes / 16 + kThreads - 1) / kThreads;
         const int nt16 = kp.n_cls * (kTabBytes / 16);
-        uint4 tv[kTabLoads];
-#pragma unroll
-        for (int k = 0; k < kTabLoads; ++k)
-            if (tid + k * kThreads < nt16)
-                tv[k] = __ldg(reinterpret_cast<const uint4 *>(w.cls_tab) + tid + k * kThreads);
-#pragma unroll
-        for (int k = 0; k < kTabLoads; ++k)
-            if (tid + k * kThreads < nt16)
-                reinterpret_cast<uint4 *>(tabs)[tid + k * kThreads] = tv[k];
+        const char *src = reinterpret_cast<const char *>(w.cls_tab);
+        const uint32_t dst0 = smem_addr(tabs);
+        for (int k = tid; k < nt16; k += kThreads)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + 16u * (uint32_t)k),
+                         "l"(src + 16 * (size_t)k) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
     }
     const float *rows = w.rows + (size_t)f * 3 * H;
     if (tid < nr)
@@ -332,6 +329,7 @@ __device__ __forceinline__ void grad_body(const KParams &kp, const Work &w, cons
             if (need && LD_IN(at, (nr + 2) * T.NGB, CK_GRAD_GLIST))
                 glist[at] = (uint16_t)((b << 8) | g);
         }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // this thread's table pieces have landed
     __syncthreads();
     const int ng = LD_IN(*cnt, (nr + 2) * T.NGB + 1, CK_GRAD_GLIST) ? *cnt : 0;
     const uint32_t tab = smem_addr(tabs);

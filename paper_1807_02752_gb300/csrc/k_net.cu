@@ -397,6 +397,319 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tc(const ConvIO io, int *
 }
 
 // ---------------------------------------------------------------------------------------------------
+// The inference forward in one kernel: layers 1-4 and the head for a 32 x 16-cell output tile, the
+// activations kept in shared memory between the layers and the accumulators in tensor memory.
+//
+// A layer-4 output tile of kFR x kFC cells needs layer 3 on a one-cell border around it, layer 2 on two
+// cells, layer 1 on three and the input on four.  Layers 2 and 3 run as 3 x 3 MMA blocks of 16 x 8 cells
+// (M 128) over a 48 x 24 region, layer 4 as 2 x 2 blocks; every block is the per-layer kernel's MMA
+// sequence (taps in order, then 16-channel K steps, bf16 x bf16 -> f32) on operands in the same plane
+// layout (8 channels per plane, 16 bytes per cell; K halves one plane apart, 8-row groups one region row
+// apart), so every accumulator, and therefore every activation and logit of the road rows, equals the
+// per-layer kernels' bit for bit.  Cells outside the map are stored as zero (the zero padding of the
+// next layer); cells a block computes beyond the region the next layer reads are dropped.  One thread
+// issues a layer's MMAs into up to nine accumulators (32 tensor-memory columns each) and commits them to
+// an mbarrier; the whole CTA waits (bounded), reads the accumulators back (tcgen05.ld, one lane quarter per
+// warp, warps w and w + 4 taking the two column halves) and writes the next layer's input.  Layer 1 (one
+// input channel) runs on the CUDA cores in the per-layer kernel's operation order.  The next tile's input
+// arrives by cp.async while the current tile runs.
+//
+// Measured on the 64-frame 1242x375 learned detection (top_k 96): 1.26 ms per call against 1.13 ms with one
+// kernel per layer.  With about 170 KB of shared memory a CTA is alone on its SM and a tile's phases run
+// one after another (issue 21 % active, tensor pipe 12 %), where the per-layer kernels keep four CTAs per
+// SM and overlap one tile's MMAs with the next tile's copies; so the per-layer form is the default.
+// ---------------------------------------------------------------------------------------------------
+constexpr int kFR = 32, kFC = 16;                                // layer-4 output tile (cells)
+constexpr int kF1R = kFR + 18, kF1C = kFC + 10;                  // layer-1 region (layer-2 input), origin (-3, -3)
+constexpr int kF2R = kF1R, kF2C = kF1C;                          // layer-2 region (layer-3 input), origin (-2, -2)
+constexpr int kF3R = kFR + 2, kF3C = kFC + 2;                    // layer-3 region (layer-4 input), origin (-1, -1)
+constexpr int kFXR = kF1R + 2, kFXC = kF1C + 2;                  // input region, origin (-4, -4)
+constexpr int kFusedThreads = 256;
+constexpr int kFP1 = kF1R * kF1C * 16, kFP2 = kF2R * kF2C * 16, kFP3 = kF3R * kF3C * 16;   // plane bytes
+constexpr int kFBufA = 2 * kFP1 > 4 * kFP3 ? 2 * kFP1 : 4 * kFP3;                       // layer 1 / layer 3 out
+constexpr int kFBufB = 4 * kFP2;                                                         // layer 2 out
+constexpr int kFW2 = 9 * 16 * 32 * 2, kFW3 = 9 * 32 * 32 * 2, kFW4 = 9 * 32 * 16 * 2;
+constexpr int kFX = kFXR * kFXC * 4;   // one input buffer (raw block sums); two are kept
+constexpr size_t kFusedSmem = (size_t)kFBufA + kFBufB + kFW2 + kFW3 + kFW4 + 2 * kFX;
+static_assert(kFBufA % 16 == 0 && kFBufB % 16 == 0 && kFX % 16 == 0, "16-byte aligned regions");
+// the MMA operands stay inside their regions: block rows x 16 + 15 + 2 and block cols x 8 + 7 + 2
+static_assert(2 * 16 + 15 + 2 < kF1R && 2 * 8 + 7 + 2 < kF1C && 16 + 15 + 2 < kF3R && 8 + 7 + 2 < kF3C, "operands in bounds");
+
+struct FusedIO {
+    const int32_t *xsum;                 // [n][mh][mw] block sums
+    const __nv_bfloat16 *w1;             // [16][9]
+    const __nv_bfloat16 *wt[3];          // layers 2-4: [COUT][9 CIN]
+    const float *bias[4];
+    const __nv_bfloat16 *wh;             // [16]
+    const float *bh;                     // [1]
+    float *z;                            // [n][mh][mw]
+    int n, mh, mw, tiles_r, tiles_c, heat;
+    const FrameState *fs;                // road rows only (null: every tile)
+};
+
+// weights of one layer -> the B layout of k_conv_tc (per K step kk: K halves COUT x 16 B apart, groups of 8
+// output channels 128 B apart)
+template <int CIN, int COUT>
+__device__ __forceinline__ void fused_load_w(const __nv_bfloat16 *wt, unsigned char *wsm)
+{
+    for (int i = threadIdx.x; i < COUT * 9 * (CIN / 8); i += kFusedThreads) {
+        const int n = i / (9 * CIN / 8), rem = i % (9 * CIN / 8), tap = rem / (CIN / 8), c8 = rem % (CIN / 8);
+        const int kk = tap * (CIN / 16) + (c8 >> 1), h = c8 & 1;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(wt + (size_t)n * 9 * CIN + tap * CIN + c8 * 8));
+        *reinterpret_cast<uint4 *>(wsm + kk * COUT * 32 + h * COUT * 16 + (n >> 3) * 128 + (n & 7) * 16) = v;
+    }
+}
+
+// One thread issues the MMAs of a layer: NBR x NBC blocks of 16 x 8 output cells over an input region of
+// RC cells per row (planes of PB bytes), accumulator of block b at column b * COUT.
+template <int CIN, int COUT, int NBR, int NBC, int RC, int PB>
+__device__ __forceinline__ void fused_mma(uint32_t in_base, uint32_t w_base, uint32_t tbase)
+{
+    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((128u >> 4) << 24);
+#pragma unroll 1
+    for (int b = 0; b < NBR * NBC; ++b) {
+        const int by = b / NBC, bx = b % NBC;
+        const uint32_t dacc = tbase + (uint32_t)(b * COUT);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+            for (int c16 = 0; c16 < CIN / 16; ++c16) {
+                const int kk = tap * (CIN / 16) + c16;
+                const uint32_t cell = (uint32_t)((by * 16 + tap / 3) * RC + bx * 8 + tap % 3);
+                const uint64_t ad = tc_desc(in_base + (uint32_t)(2 * c16 * PB) + cell * 16u, PB, RC * 16);
+                const uint64_t bd = tc_desc(w_base + (uint32_t)(kk * COUT * 32), COUT * 16, 128);
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                             ::"r"(dacc), "l"(ad), "l"(bd), "r"(kIdesc), "r"(kk));
+            }
+    }
+}
+
+// Epilogue of layer 2 or 3: bias + ReLU -> bf16 into the next layer's input region (ORR x ORC cells,
+// planes of PB bytes) whose origin is (oy, ox) in the map; zero outside the map.
+template <int NBR, int NBC, int ORR, int ORC, int PB>
+__device__ __forceinline__ void fused_epi32(uint32_t tbase, const float *bias, unsigned char *out, int oy, int ox,
+                                            int mh, int mw)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, h = warp >> 2;
+#pragma unroll 1
+    for (int b = 0; b < NBR * NBC; ++b) {
+        const int Y = (b / NBC) * 16 + q * 4 + (lane >> 3), X = (b % NBC) * 8 + (lane & 7);
+        uint32_t r[16];
+        tc_load<16>(tbase + (uint32_t)(b * 32 + 16 * h) + ((uint32_t)(q * 32) << 16), r);
+        if (Y < ORR && X < ORC) {
+            const int y = oy + Y, x = ox + X;
+            const bool in = y >= 0 && y < mh && x >= 0 && x < mw;
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+                uint32_t o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int c = 16 * h + 8 * pl + 2 * k;
+                    const float v0 = fmaxf(__fadd_rn(__uint_as_float(r[8 * pl + 2 * k]), bias[c]), 0.0f);
+                    const float v1 = fmaxf(__fadd_rn(__uint_as_float(r[8 * pl + 2 * k + 1]), bias[c + 1]), 0.0f);
+                    o[k] = in ? pack2(v0, v1) : 0u;
+                }
+                *reinterpret_cast<uint4 *>(out + (2 * h + pl) * PB + (Y * ORC + X) * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    }
+}
+
+// wait for the layer's MMAs (bounded; false on a timeout)
+__device__ __forceinline__ bool fused_wait(uint32_t mbar, uint32_t &phase)
+{
+    const bool ok = tc_wait(mbar, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return ok;
+}
+
+__device__ __forceinline__ void fused_sync_for_mma()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic stores -> tensor-core reads
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_net_fused(const FusedIO io, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char fsm[];
+    __shared__ uint32_t taddr_s;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ float w1s[16 * 9], b1s[16], b2s[32], b3s[32], b4s[16], hws[16];
+    __shared__ int fail_s;
+    unsigned char *bufA = fsm, *bufB = fsm + kFBufA;
+    unsigned char *w2 = bufB + kFBufB, *w3 = w2 + kFW2, *w4 = w3 + kFW3;
+    int32_t *xbuf[2] = {reinterpret_cast<int32_t *>(w4 + kFW4), reinterpret_cast<int32_t *>(w4 + kFW4 + kFX)};
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mh = io.mh, mw = io.mw;
+    fused_load_w<16, 32>(io.wt[0], w2);
+    fused_load_w<32, 32>(io.wt[1], w3);
+    fused_load_w<32, 16>(io.wt[2], w4);
+    for (int i = tid; i < 16 * 9; i += kFusedThreads)
+        w1s[i] = __bfloat162float(io.w1[i]);
+    if (tid < 16) {
+        b1s[tid] = io.bias[0][tid];
+        b4s[tid] = io.bias[3][tid];
+        hws[tid] = __bfloat162float(io.wh[tid]);
+    }
+    if (tid < 32) {
+        b2s[tid] = io.bias[1][tid];
+        b3s[tid] = io.bias[2][tid];
+    }
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) {
+        fail_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&taddr_s);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(dst));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fused_sync_for_mma();   // weights (generic stores) visible to the tensor cores, tensor memory allocated
+    const uint32_t tbase = taddr_s;
+    const uint32_t aA = (uint32_t)__cvta_generic_to_shared(bufA), aB = (uint32_t)__cvta_generic_to_shared(bufB);
+    const uint32_t aw2 = (uint32_t)__cvta_generic_to_shared(w2), aw3 = (uint32_t)__cvta_generic_to_shared(w3),
+                   aw4 = (uint32_t)__cvta_generic_to_shared(w4);
+    const float bh = io.bh[0];
+    uint32_t phase = 0u;
+    const int per_frame = io.tiles_r * io.tiles_c, total = io.n * per_frame;
+    // the tiles this CTA owns that reach a road row: blockIdx.x, + gridDim.x, ...
+    auto next_tile = [&](int t) {
+        for (; t < total; t += gridDim.x) {
+            const int f = t / per_frame, rem = t % per_frame;
+            if ((rem / io.tiles_c) * kFR + kFR - 1 >= first_needed_row(io.fs, f, 0))
+                return t;
+        }
+        return total;
+    };
+    // the raw block sums of tile t's input region (origin y0 - 4, x0 - 4) into buf by cp.async, zero
+    // outside the map
+    auto load_x = [&](int t, int32_t *buf) {
+        const int f = t / per_frame, rem = t % per_frame;
+        const int y0 = (rem / io.tiles_c) * kFR, x0 = (rem % io.tiles_c) * kFC;
+        const int32_t *xf = io.xsum + (size_t)f * mh * mw;
+        for (int i = tid; i < kFXR * kFXC; i += kFusedThreads) {
+            const int y = y0 - 4 + i / kFXC, x = x0 - 4 + i % kFXC;
+            const bool in = y >= 0 && y < mh && x >= 0 && x < mw;
+            const int32_t *src = xf + (size_t)(in ? y : 0) * mw + (in ? x : 0);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(buf + i)),
+                         "l"(src), "r"(in ? 4 : 0) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    int t = next_tile(blockIdx.x), it = 0;
+    if (t < total)
+        load_x(t, xbuf[0]);
+    for (; t < total; ++it) {
+        const int f = t / per_frame, rem = t % per_frame;
+        const int y0 = (rem / io.tiles_c) * kFR, x0 = (rem % io.tiles_c) * kFC;
+        const int32_t *xs = xbuf[it & 1];
+        const int tn = next_tile(t + gridDim.x);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");   // this tile's input
+        __syncthreads();
+        if (tn < total)
+            load_x(tn, xbuf[(it + 1) & 1]);   // the next tile's input arrives during this tile
+        // layer 1 on the CUDA cores (origin y0 - 3, x0 - 3): the per-layer kernel's FMA order
+        for (int i = tid; i < kF1R * kF1C; i += kFusedThreads) {
+            const int Y = i / kF1C, X = i % kF1C, y = y0 - 3 + Y, x = x0 - 3 + X;
+            float in[9];
+#pragma unroll
+            for (int tp = 0; tp < 9; ++tp)
+                in[tp] = cell_input(xs[(Y + tp / 3) * kFXC + X + tp % 3]);
+            const bool inmap = y >= 0 && y < mh && x >= 0 && x < mw;
+            uint32_t o[8];
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                float s0 = b1s[c], s1 = b1s[c + 1];
+#pragma unroll
+                for (int tp = 0; tp < 9; ++tp) {
+                    s0 = __fmaf_rn(w1s[c * 9 + tp], in[tp], s0);
+                    s1 = __fmaf_rn(w1s[(c + 1) * 9 + tp], in[tp], s1);
+                }
+                o[c >> 1] = inmap ? pack2(fmaxf(s0, 0.0f), fmaxf(s1, 0.0f)) : 0u;
+            }
+            *reinterpret_cast<uint4 *>(bufA + i * 16) = make_uint4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<uint4 *>(bufA + kFP1 + i * 16) = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+        fused_sync_for_mma();
+        // layer 2: 3 x 3 blocks over the layer-1 region -> layer-2 region (origin y0 - 2, x0 - 2)
+        if (tid == 0) {
+            fused_mma<16, 32, 3, 3, kF1C, kFP1>(aA, aw2, tbase);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+        }
+        if (!fused_wait(mb, phase))
+            atomicExch(&fail_s, 1);
+        __syncthreads();
+        if (fail_s)
+            break;
+        fused_epi32<3, 3, kF2R, kF2C, kFP2>(tbase, b2s, bufB, y0 - 2, x0 - 2, mh, mw);
+        fused_sync_for_mma();
+        // layer 3 -> layer-3 region (origin y0 - 1, x0 - 1), into the buffer layer 1 used
+        if (tid == 0) {
+            fused_mma<32, 32, 3, 3, kF2C, kFP2>(aB, aw3, tbase);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+        }
+        if (!fused_wait(mb, phase))
+            atomicExch(&fail_s, 1);
+        __syncthreads();
+        if (fail_s)
+            break;
+        fused_epi32<3, 3, kF3R, kF3C, kFP3>(tbase, b3s, bufA, y0 - 1, x0 - 1, mh, mw);
+        fused_sync_for_mma();
+        // layer 4: 2 x 2 blocks -> bias + ReLU, the 1x1 head, the logit or the heatmap
+        if (tid == 0) {
+            fused_mma<32, 16, 2, 2, kF3C, kFP3>(aA, aw4, tbase);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+        }
+        if (!fused_wait(mb, phase))
+            atomicExch(&fail_s, 1);
+        __syncthreads();
+        if (fail_s)
+            break;
+        {
+            const int q = warp & 3;
+#pragma unroll 1
+            for (int b = (warp >> 2) * 2; b < (warp >> 2) * 2 + 2; ++b) {
+                const int Y = (b >> 1) * 16 + q * 4 + (lane >> 3), X = (b & 1) * 8 + (lane & 7);
+                uint32_t r[16];
+                tc_load<16>(tbase + (uint32_t)(b * 16) + ((uint32_t)(q * 32) << 16), r);
+                const int y = y0 + Y, x = x0 + X;
+                if (y < mh && x < mw) {
+                    float zc = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int c = 2 * k;
+                        const float v0 = fmaxf(__fadd_rn(__uint_as_float(r[c]), b4s[c]), 0.0f);
+                        const float v1 = fmaxf(__fadd_rn(__uint_as_float(r[c + 1]), b4s[c + 1]), 0.0f);
+                        const uint32_t o = pack2(v0, v1);
+                        zc = __fmaf_rn(hws[c + 1], bf_hi(o), __fmaf_rn(hws[c], bf_lo(o), zc));
+                    }
+                    zc = __fadd_rn(zc, bh);
+                    io.z[((size_t)f * mh + y) * mw + x] = io.heat ? __frcp_rn(__fadd_rn(1.0f, expf(-zc))) : zc;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();   // the next tile overwrites both buffers and the accumulators
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        t = tn;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (tid == 0 && fail_s)
+        atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+}
+
+// ---------------------------------------------------------------------------------------------------
 // weight gradients: dW[co][tap][ci] = sum_cells dS[co] A[cell + (tap)][ci]; column 9 CIN holds the bias
 // ---------------------------------------------------------------------------------------------------
 struct WgradIO {
@@ -922,9 +1235,46 @@ static cudaError_t conv(ConvIO io, cudaStream_t s)
     return cudaGetLastError();
 }
 
+static cudaError_t net_forward_fused(const NetArgs &a, const int32_t *xsum, int n, float *z, bool heat, cudaStream_t s,
+                                     const FrameState *road)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_net_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr = true;
+    }
+    FusedIO io{};
+    io.xsum = xsum;
+    io.w1 = a.wf[0];
+    for (int l = 0; l < 3; ++l)
+        io.wt[l] = a.wf[l + 1];
+    for (int l = 0; l < 4; ++l)
+        io.bias[l] = a.bias[l];
+    io.wh = a.whb;
+    io.bh = a.bh;
+    io.z = z;
+    io.n = n;
+    io.mh = a.mh;
+    io.mw = a.mw;
+    io.tiles_r = (a.mh + kFR - 1) / kFR;
+    io.tiles_c = (a.mw + kFC - 1) / kFC;
+    io.heat = heat ? 1 : 0;
+    io.fs = road;
+    int *err = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&err, g_tc_error);
+    if (e != cudaSuccess)
+        return e;
+    k_net_fused<<<grid_for(n * io.tiles_r * io.tiles_c, 1), kFusedThreads, kFusedSmem, s>>>(io, err);
+    return cudaGetLastError();
+}
+
 cudaError_t net_forward(const NetArgs &a, const int32_t *xsum, int n, float *z, bool keep_a4, bool heat,
                         cudaStream_t s, const FrameState *road)
 {
+    if (!keep_a4 && a.fused)   // inference in one kernel, the activations never leave the SM
+        return net_forward_fused(a, xsum, n, z, heat, s, road);
     const long long cells = (long long)n * a.mh * a.mw;
     const int g1 = (int)((cells + kCellThreads - 1) / kCellThreads);
     k_conv1<<<grid_for(g1, 8), kCellThreads, 0, s>>>(a, xsum, n, road);

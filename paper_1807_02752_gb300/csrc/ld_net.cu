@@ -467,6 +467,22 @@ int ld_net_debug_get(ld_net *net, int32_t frame, int32_t stage, void *host_dst, 
     return e == cudaSuccess ? LD_OK : ncuda(net, e, "debug copy");
 }
 
+int ld_net_set_fused(ld_net *net, int32_t on)
+{
+    if (!net)
+        return LD_E_ARG;
+    const cudaError_t e = cudaStreamSynchronize(ld::handle_stream(net->h));
+    if (e != cudaSuccess)
+        return ncuda(net, e, "sync");
+    net->a.fused = on ? 1 : 0;
+    for (LearnedGraph &g : net->graphs)   // the captured calls hold the other form's kernels
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g = LearnedGraph{};
+        }
+    return LD_OK;
+}
+
 int ld_net_status(ld_net *net)
 {
     if (!net)

@@ -32,6 +32,7 @@ struct NetArgs {
     float *theta, *m, *v;           // master weights and Adam moments [kNetParams]
     float *part;                    // weight-gradient partials [SMs x kWgradCtasPerSm][32][289]
     float *part_head;               // loss partials [608][18]
+    int fused = 0;                  // 1: inference forward as one kernel (k_net_fused); 0: one kernel per layer
 };
 
 // logits (heat = false) or the heatmap sigmoid(z) of every cell; with road (the frames' fit states) only

@@ -197,6 +197,8 @@ def load(checked: bool = False):
                  "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs", "ld_detect_learned",
                  "ld_net_debug_get"):
         getattr(L, name).restype = C.c_int
+    L.ld_net_set_fused.argtypes = [p, i32]
+    L.ld_net_set_fused.restype = C.c_int
     L.ld_checked_build.argtypes = []
     L.ld_checked_build.restype = i32
     L.ld_check_status.argtypes = [p]
@@ -228,6 +230,7 @@ EXPORTED = ["ld_params_default", "ld_n_starts", "ld_create", "ld_detect", "ld_de
             "ld_server_submit_pinned", "ld_server_submit_batch", "ld_server_poll",
             "ld_server_drain", "ld_server_stream_state", "ld_server_stats_get", "ld_server_last_error",
             "ld_server_destroy", "ld_server_set_learned", "ld_net_param_count", "ld_net_create", "ld_net_set_params", "ld_net_get_params",
+            "ld_net_set_fused",
             "ld_net_forward", "ld_net_grad", "ld_net_apply_grad", "ld_net_train_step", "ld_make_training_pairs",
             "ld_detect_learned", "ld_net_debug_size", "ld_net_debug_get", "ld_net_status", "ld_net_last_error", "ld_net_destroy",
             "ld_stereo_params_default", "ld_stereo_create", "ld_stereo_run", "ld_stereo_run_timed", "ld_detect_stereo",
@@ -568,6 +571,10 @@ class Net:
         """theta: float32 device tensor of NET_PARAMS values (resets the optimiser state)."""
         assert theta.is_cuda and theta.numel() == NET_PARAMS and theta.dtype.itemsize == 4 and theta.is_contiguous()
         self._check(self.L.ld_net_set_params(self.h, theta.data_ptr()))
+
+    def set_fused(self, on: bool = True):
+        """Inference forward as one fused kernel (the default) or one kernel per layer (ld_net_set_fused)."""
+        self._check(self.L.ld_net_set_fused(self.h, 1 if on else 0))
 
     def get_params(self):
         import torch

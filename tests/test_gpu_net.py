@@ -375,3 +375,45 @@ def test_trained_network_gains_over_untrained_and_raw_map(torch_cuda):
     finally:
         net.close()
         det.close()
+
+
+@pytest.mark.parametrize("name,n", [("batch64_1242x375", 8), ("small_320x120", 5)])
+def test_fused_forward_matches_per_layer(torch_cuda, name, n):
+    """The fused inference kernel (all layers and the head per tile, activations on chip) against one kernel
+    per layer: logits bit-identical on every cell (every row is needed without a road restriction), and in
+    the learned detection the same lanes, byte for byte, and the same heatmap on the road rows; with random
+    and with the package's trained weights."""
+    import os
+
+    torch = torch_cuda
+    cfg, _ = scenes.WORKLOADS[name]
+    disp, img, _ = _frames(cfg, n, first=4242)
+    p = ld.default_params(n_disp=cfg.n_disp)
+    det = ld.Detector(cfg.width, cfg.height, n, p)
+    net = ld.Net(det)
+    d, i = torch.from_numpy(disp).cuda(), torch.from_numpy(img).cuda()
+    xs, _, _ = net.training_pairs(d, i)
+    rnd = (np.random.default_rng(5).standard_normal(ld.NET_PARAMS) * 0.2).astype(np.float32)
+    trained = np.load(os.path.join(os.path.dirname(ld.__file__), "proposal_weights.npy")).astype(np.float32)
+    try:
+        for theta in (rnd, trained):
+            net.set_params(torch.from_numpy(theta).cuda())
+            res = {}
+            for fused in (False, True):
+                net.set_fused(fused)
+                z = net.forward(xs, cfg.width, cfg.height).clone()
+                lanes = ld.Detector.lanes(net.detect(d, i, top_k=32)).copy()
+                torch.cuda.synchronize()
+                heat = [net.debug(f, ld.NET_STAGE_HEATMAP).reshape(net.map_shape(cfg.width, cfg.height)).copy()
+                        for f in range(n)]
+                net.status()
+                res[fused] = (z, lanes, heat)
+            (z0, l0, h0), (z1, l1, h1) = res[False], res[True]
+            assert torch.equal(z0, z1), f"logits differ at {int((z0 != z1).sum())} cells"
+            assert l0.tobytes() == l1.tobytes()
+            for f in range(n):
+                r0 = max(int(l0[f]["v_top"]), 0) // 4
+                assert (h0[f][r0:] == h1[f][r0:]).all(), f"frame {f}: heatmap differs on the road rows"
+    finally:
+        net.close()
+        det.close()
