@@ -3,13 +3,15 @@ that a profiler attached to the process sees every kernel of every call as a sep
 
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 4 learned 64
+    python -m paper_1807_02752_gb300.run_workload batch64_1242x375 3 learned 96 fused
     python -m paper_1807_02752_gb300.run_workload batch64_1242x375 3 stereo
     python -m paper_1807_02752_gb300.run_workload mixed 20
 
 Each call launches the nine kernels of the path once, in order, on the handle's stream, and times each
 with CUDA events; the per-kernel times of the last call are printed.  With `learned [top_k]` each call is
 the learned form instead (the network with the package's trained weights ranks the starts; exact
-energies for the top_k coarse starts), timed as a whole.  With `stereo` each call is the stereo stage on
+energies for the top_k coarse starts), timed as a whole; `fused` after top_k runs the network as the one
+fused kernel instead of one kernel per layer.  With `stereo` each call is the stereo stage on
 the workload's stereo pairs (search range propagation for both maps, then the consistency check).
 `mixed` times frames of three camera sizes (16 x 1242x375, 8 x 1280x720, 8 x 1920x1080, D = 256) as one
 ld_detect_groups call, as one ld_detect_mixed call (one launch per stage) and as three ld_detect calls in
@@ -77,6 +79,7 @@ def main(argv=None):
     learned = len(argv) > 2 and argv[2] == "learned"
     stereo = len(argv) > 2 and argv[2] == "stereo"
     top_k = int(argv[3]) if len(argv) > 3 else 64
+    fused = len(argv) > 4 and argv[4] == "fused"
     if name not in scenes.WORKLOADS:
         raise SystemExit(f"unknown workload {name!r}; known: {', '.join(scenes.WORKLOADS)}")
     cfg, n = scenes.WORKLOADS[name]
@@ -101,6 +104,7 @@ def main(argv=None):
         net = ld.Net(det)
         w = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "proposal_weights.npy"))
         net.set_params(torch.from_numpy(w.astype(np.float32)).cuda())
+        net.set_fused(fused)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ms = []
         for _ in range(calls):
@@ -109,7 +113,8 @@ def main(argv=None):
             e1.record()
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
-        print(name, n, "frames, learned form, top_k", top_k, "ms per call:", [round(x, 4) for x in ms])
+        print(name, n, "frames, learned form, top_k", top_k, "fused network" if fused else "network per layer",
+              "ms per call:", [round(x, 4) for x in ms])
         net.close()
     else:
         ms = None
