@@ -383,6 +383,7 @@ struct VpxMem {
     uint8_t *sup;          // [H]
     int *sh;
     int16_t *pid;          // [H]
+    int4 *rinfo;           // [H] per DP row v: first staged vote and count of row v - chi (entering), of row v + chi + 1 (leaving)
     unsigned char *dyn;    // backtrack rows [seg_rows][row bytes], later the column bitmaps of the votes
 };
 
@@ -434,6 +435,19 @@ __device__ __forceinline__ void scatter_delta(const KParams &kp, const Work &w, 
         for (int q = t0; q < vr.n; q += stride)
             if (LD_IN(vr.p[q], kp.W, CK_VPX_VOTE))
                 atoms_add(delta + 4u * (uint32_t)vr.p[q], -1);
+    }
+}
+
+// The band change of DP row v from its staged descriptor: thread q takes vote q of the entering row, then
+// of the leaving row (one round for up to blockDim.x votes).
+__device__ __forceinline__ void scatter_staged(const VpxMem &S, int v, uint32_t delta, int W)
+{
+    const int4 ri = S.rinfo[v];
+    for (int q = threadIdx.x; q < ri.y + ri.w; q += blockDim.x) {
+        const bool enter = q < ri.y;
+        const int c = S.vb[enter ? ri.x + q : ri.z + (q - ri.y)];
+        if (LD_IN(c, W, CK_VPX_VOTE))
+            atoms_add(delta + 4u * (uint32_t)c, enter ? 1 : -1);
     }
 }
 
@@ -625,8 +639,12 @@ __device__ void vpx_dp_body(const KParams &kp, const Work &w, const VpxMem &S, i
         __syncthreads();
     }
     for (int v = vmax - 1; v >= vtop; --v) {
-        if (v - 1 >= vtop)
-            scatter_delta(kp, w, S, f, v - 1, vtop, staged, ((v - 1) & 1) ? d1 : d0, tid, nt);
+        if (v - 1 >= vtop) {
+            if (staged && !kp.band_literal)
+                scatter_staged(S, v - 1, ((v - 1) & 1) ? d1 : d0, W);
+            else
+                scatter_delta(kp, w, S, f, v - 1, vtop, staged, ((v - 1) & 1) ? d1 : d0, tid, nt);
+        }
         const uint32_t dv = (v & 1) ? d1 : d0;
         const int r = v - vtop;
 #pragma unroll
@@ -712,6 +730,7 @@ __device__ __forceinline__ void vpx_dp_kernel_body(const KParams &kp, const Work
     S.sup = carve<uint8_t>(p, H);
     S.sh = carve<int>(p, kMaxChunks + 64);
     S.pid = carve<int16_t>(p, H);
+    S.rinfo = carve<int4>(p, H);
     S.dyn = carve<unsigned char>(p, 0);
 
     // ---- vote rows [vtop, vmax]: offsets by a block scan, staged in shared memory when they fit ----
@@ -763,6 +782,20 @@ __device__ __forceinline__ void vpx_dp_kernel_body(const KParams &kp, const Work
             }
         }
     }
+    // per DP row v the staged votes entering (row v - chi) and leaving (row v + chi + 1) the band
+    if (staged && !kp.band_literal)
+        for (int v = tid; v < H; v += nt) {
+            int4 ri = make_int4(0, 0, 0, 0);
+            if (v - chi >= vtop && v - chi <= vmax) {
+                ri.x = S.voff[v - chi];
+                ri.y = S.voff[v - chi + 1] - ri.x;
+            }
+            if (v + chi + 1 <= vmax && v + chi + 1 >= vtop) {
+                ri.z = S.voff[v + chi + 1];
+                ri.w = S.voff[v + chi + 2] - ri.z;
+            }
+            S.rinfo[v] = ri;
+        }
     __syncthreads();
     // each vote enters at most 2 chi + 1 band rows, so |E| <= varrho (2 chi + 1) votes + lambda_x tau_x rows
     const bool packed = ((double)kp.vote_rho * (2.0 * chi + 1.0) * votes + (double)kp.lambda_x * kp.tau_x * H) * 16.0 <
@@ -868,6 +901,7 @@ size_t vpx_fixed_bytes(const KParams &kp)
     add(H);
     add(4 * (kMaxChunks + 64));
     add(2 * H);
+    add(16 * H);
     (void)W;
     return ((s + 15) & ~(size_t)15) + 64;
 }
