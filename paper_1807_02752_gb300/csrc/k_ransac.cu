@@ -367,34 +367,85 @@ __device__ __forceinline__ void fit_body(const KParams &kp, const Work &w, const
         if ((long long)kp.eps_den * bc >= (long long)kp.eps_num * ns)
             break;
     }
-    // final least squares over the remaining set: exact sums, one warp per sum (sum t^k for k <= 2M-2, then
+    // final least squares over the remaining set: exact sums (sum t^k for k <= 2M-2, then
     // sum y t^k for k < M), then the normal equations solved on one warp
     if (!(fl & 2)) {
         constexpr int NS = 3 * M - 1;
-        for (int sidx = warp; sidx < NS; sidx += kNW) {
-            const int pk = sidx < 2 * M - 1 ? sidx : sidx - (2 * M - 1);
-            __int128 acc = 0;
+        if constexpr (M == 5) {
+            // each thread's points: the powers of t built once per point, all NS sums at a time
+            __int128 acc[NS];
+#pragma unroll
+            for (int k = 0; k < NS; ++k)
+                acc[k] = 0;
             int cnt = 0;
-            for (int j = lane; j < n; j += 32)
+            for (int j = tid; j < n; j += kFitThreads)
                 if (member[j]) {
-                    const __int128 t = (__int128)(xs[j] - centre);
-                    __int128 pw = sidx < 2 * M - 1 ? (__int128)1 : (__int128)ys[j];
-                    for (int k = 0; k < pk; ++k)
+                    const __int128 t = (__int128)(xs[j] - centre), y = (__int128)ys[j];
+                    __int128 pw = 1;
+#pragma unroll
+                    for (int k = 0; k < 2 * M - 1; ++k) {
+                        acc[k] += pw;
+                        if (k < M)
+                            acc[2 * M - 1 + k] += y * pw;
                         pw *= t;
-                    acc += pw;
+                    }
                     ++cnt;
                 }
+            // warp sums, then the warps' partial sums added by one warp (integer: the order does not matter)
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1)
-                acc += shfl_down_i128(acc, d);
+            for (int k = 0; k < NS; ++k)
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1)
+                    acc[k] += shfl_down_i128(acc[k], d);
             cnt = __reduce_add_sync(0xffffffffu, cnt);
             if (lane == 0) {
-                red[sidx] = acc;
-                if (sidx == 0)
-                    redc[0] = cnt;
+#pragma unroll
+                for (int k = 0; k < NS; ++k)
+                    red[warp * NS + k] = acc[k];
+                redc[warp] = cnt;
             }
+            __syncthreads();
+            if (warp == 0) {
+                __int128 s = 0;
+                int c = 0;
+                if (lane < NS)
+                    for (int wv = 0; wv < kNW; ++wv)
+                        s += red[wv * NS + lane];
+                for (int wv = 0; wv < kNW; ++wv)
+                    c += redc[wv];
+                __syncwarp();
+                if (lane < NS)
+                    red[lane] = s;
+                if (lane == 0)
+                    redc[0] = c;
+            }
+            __syncthreads();
+        } else {   // M = 3: one warp per sum measured faster (8 sums: one round of the 8 warps)
+            for (int sidx = warp; sidx < NS; sidx += kNW) {
+                const int pk = sidx < 2 * M - 1 ? sidx : sidx - (2 * M - 1);
+                __int128 acc = 0;
+                int cnt = 0;
+                for (int j = lane; j < n; j += 32)
+                    if (member[j]) {
+                        const __int128 t = (__int128)(xs[j] - centre);
+                        __int128 pw = sidx < 2 * M - 1 ? (__int128)1 : (__int128)ys[j];
+                        for (int k = 0; k < pk; ++k)
+                            pw *= t;
+                        acc += pw;
+                        ++cnt;
+                    }
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1)
+                    acc += shfl_down_i128(acc, d);
+                cnt = __reduce_add_sync(0xffffffffu, cnt);
+                if (lane == 0) {
+                    red[sidx] = acc;
+                    if (sidx == 0)
+                        redc[0] = cnt;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
         if (warp == 0) {
             double cd[M];
             int ok = redc[0] >= M ? solve_normal_warp<M>(red, kp.e, cd) == 0 : 0;
