@@ -389,7 +389,8 @@ int ld_server_create(const ld_params *p, const ld_server_config *cfg, ld_server 
 /* Submit one frame (HOST pointers, [h][w]; copied into the slot's page-locked staging before the call
  * returns, so the caller may reuse them; the copy to the device is enqueued at once on the slot's stream).
  * Errors: LD_E_ARG (unknown size or stream id, null pointer), LD_E_BUSY (every slot of the class is full
- * or in flight and the HBM budget admits no further slot: poll and retry), LD_E_CUDA. */
+ * or in flight and the HBM budget admits no further slot: poll and retry), LD_E_NOMEM or LD_E_CUDA (a slot
+ * the budget admitted could not be allocated, or a copy failed; ld_server_last_error says which). */
 int ld_server_submit(ld_server *s, int32_t stream_id, const float *disp, const uint8_t *img, int32_t w, int32_t h,
                      uint64_t tag);
 

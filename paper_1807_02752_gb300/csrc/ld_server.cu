@@ -426,9 +426,11 @@ namespace {
 
 // A slot of class cls that can take one more frame (lock held).  With an HBM budget, when every slot of the
 // class is full or in flight a new one is allocated, outside the lock, if the budget and the device's free
-// memory allow it; the lock is held again on return.
-Slot *admit(ld_server *s, int cls, std::unique_lock<std::mutex> &lk)
+// memory allow it; the lock is held again on return.  Null when no slot can take the frame; *alloc_error is
+// then set when allocating a slot failed (s->err says why) rather than every slot being busy.
+Slot *admit(ld_server *s, int cls, std::unique_lock<std::mutex> &lk, bool *alloc_error)
 {
+    *alloc_error = false;
     reap(s);
     for (Slot &sl : s->slots)
         if (sl.cls == cls && sl.state == SlotState::Filling && sl.n < s->cfg.max_batch)
@@ -455,6 +457,7 @@ Slot *admit(ld_server *s, int cls, std::unique_lock<std::mutex> &lk)
     s->growing = false;
     if (bytes < 0) {
         s->err = why;
+        *alloc_error = true;
         return nullptr;
     }
     s->slots.push_back(std::move(fresh));
@@ -489,9 +492,12 @@ int submit_frames(ld_server *s, int32_t n, const int32_t *stream_ids, const floa
     int done = 0;
     while (done < n) {
         std::unique_lock<std::mutex> lk(s->mu);
-        Slot *sl = admit(s, cls, lk);
+        bool alloc_error = false;
+        Slot *sl = admit(s, cls, lk, &alloc_error);
         if (!sl) {
             s->rejected += n - done;
+            if (alloc_error)   // s->err holds the allocation's error
+                return done > 0 ? done : (s->err.find("out of memory") != std::string::npos ? LD_E_NOMEM : LD_E_CUDA);
             if (done == 0)
                 return sfail(s, LD_E_BUSY, "every slot of the size class is full or in flight and the HBM budget "
                                            "admits no further slot");
