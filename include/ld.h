@@ -275,9 +275,10 @@ int32_t ld_flat_range(const ld_params *p);
  * counted; the first failure's site, index and bound are kept.  Nothing traps.  In the regular library
  * the tests compile away and the calls below report a clean state.
  *   ld_checked_build   1 in the checked library, 0 otherwise.
- *   ld_check_status    waits for the device, then out[0] = failures since the last reset,
- *                      out[1..3] = site, index and bound of the first one (0 when none).  LD_E_CUDA on
- *                      a device error.
+ *   ld_check_status    waits for the device, then out[0] = failures since the last reset (all kernels),
+ *                      out[1..3] = site, index and bound of a first one: the first failure recorded by the
+ *                      first translation unit, in link order, that recorded any (0 when none).  LD_E_CUDA
+ *                      on a device error.
  *   ld_check_reset     clears the counts (waits for the device first).
  *   ld_check_site_name the name of a site ("?" for an unknown one).
  *   ld_check_selftest  checked library only: one thread evaluates a test with index = bound (no access
