@@ -434,8 +434,8 @@ class Server:
     """Continuous batching of frames of several sizes from several camera streams (ld_server_* of ld.h)."""
 
     def __init__(self, sizes, params: Params | None = None, slots_per_size: int = 2, max_batch: int = 16,
-                 max_wait_us: int = 500, n_streams: int = 8, hbm_budget_bytes: int = 0):
-        self.L = load()
+                 max_wait_us: int = 500, n_streams: int = 8, hbm_budget_bytes: int = 0, lib=None):
+        self.L = lib if lib is not None else load()
         self.params = params or default_params()
         cfg = ServerConfig()
         cfg.n_sizes = len(sizes)

@@ -121,3 +121,51 @@ def test_maximum_frame_size_checked(checked):
     cfg = scenes.with_size(scenes.HD_1920x1080, width=ld.MAX_W, height=ld.MAX_H, n_disp=ld.MAX_D)
     frames = [scenes.make_frame(cfg, 1400)[:2]]
     _run(torch, L, frames, ld.default_params(n_disp=cfg.n_disp))
+
+
+def test_serving_checked(checked):
+    """The serving runtime through the checked library: frames of two sizes from three streams, pinned and
+    batched submits with slots added under a budget; a clean status and every result the frame's result
+    alone (regular library)."""
+    torch, L = checked
+    sizes = [(70, 33), (130, 50)]
+    p = ld.default_params(n_disp=16)
+    frames = []
+    for k in range(8):
+        for sid in range(3):
+            wh = sizes[(sid + k) % 2]
+            frames.append((sid, wh) + scenes.make_tiny_frame(wh[0], wh[1], 16, 1500 + 10 * sid + k))
+    alone = []
+    dets = {wh: ld.Detector(wh[0], wh[1], 1, p) for wh in sizes}
+    for sid, wh, d, i in frames:
+        alone.append(dets[wh].detect_host(d[None], i[None])[0].tobytes())
+    for det in dets.values():
+        det.close()
+    assert L.ld_check_reset() == ld.OK
+    srv = ld.Server(sizes, p, n_streams=3, slots_per_size=1, max_batch=2, max_wait_us=200,
+                    hbm_budget_bytes=1 << 30, lib=L)
+    got = []
+    keep = []
+    try:
+        for wh in sizes:   # runs of one size, pinned, several slots' worth per call
+            run = [t for t, f in enumerate(frames) if f[1] == wh]
+            d = torch.from_numpy(np.stack([frames[t][2] for t in run])).pin_memory()
+            i = torch.from_numpy(np.stack([frames[t][3] for t in run])).pin_memory()
+            keep.append((d, i))
+            tags = np.array(run, np.uint64)
+            sids = np.array([frames[t][0] for t in run], np.int32)
+            at = 0
+            while at < len(run):
+                at += srv.submit_batch(sids[at:], d[at:], i[at:], tags[at:], pinned=True)
+                if at < len(run):
+                    got.extend(srv.poll(timeout_ms=50))
+        srv.drain()
+        while len(r := srv.poll()):
+            got.extend(r)
+        torch.cuda.synchronize()
+        _clean(L)
+        assert sorted(int(r["tag"]) for r in got) == list(range(len(frames)))
+        for r in got:
+            assert r["lanes"].tobytes() == alone[int(r["tag"])], f"frame {int(r['tag'])}"
+    finally:
+        srv.close()
