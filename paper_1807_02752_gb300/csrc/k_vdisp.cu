@@ -12,7 +12,7 @@
 // atomic when the key changes: fewer atomics than pixels, and few 32-way conflicts on the dominant bin.
 // The run update is branch-free (the flush is a predicated add; invalid pixels keep the run going), so
 // warps do not diverge on the data.  The bin takes two float adds instead of a float-to-integer
-// conversion: for 0 <= x < 2^23, x + 2^23 rounded toward -infinity is 2^23 + floor(x) exactly (the
+// conversion (packed: one instruction adds two pixels): for 0 <= x < 2^23, x + 2^23 rounded toward -infinity is 2^23 + floor(x) exactly (the
 // float spacing there is 1), so its bit pattern minus that of 2^23 is floor(x); any other x leaves a
 // difference >= D (as unsigned), which the bin test rejects.  The shared histogram rows are D + 1 words
 // apart, so the transposed write-out ([D][H] per frame, so that each step of the road DP (Eq. 12) reads
@@ -32,6 +32,15 @@ __device__ __forceinline__ void red_add_if(bool p, uint32_t a, int v)
 {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(a), "r"(v),
                  "r"((int)p));
+}
+
+// One pixel of a run, as one predicated block: when key differs from run_key, add the run's count cnt at
+// address a; cnt becomes 1 (a new key comes from a counted pixel) or else inc (cnt plus the pixel's count).
+__device__ __forceinline__ void flush_step(int key, int run_key, uint32_t a, int &cnt, int inc)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, %2;\n\t@q red.shared.add.s32 [%3], %4;\n\t"
+                 "selp.s32 %0, 1, %5, q;\n\t}"
+                 : "=r"(cnt) : "r"(key), "r"(run_key), "r"(a), "r"(cnt), "r"(inc));
 }
 
 // Rows [tile * kRows, ..) of frame f.
@@ -87,15 +96,24 @@ __device__ __forceinline__ void vdisp_body(const KParams &kp, int32_t *__restric
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             const float l[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
+            // both adds of the bin for two pixels at a time (packed FP32, each element rounded as the scalar add)
+            const float2 h2 = make_float2(0.5f, 0.5f), t2 = make_float2(8388608.0f, 8388608.0f);
+            const float2 p01 = __fadd2_rd(__fadd2_rn(make_float2(l[0], l[1]), h2), t2);
+            const float2 p23 = __fadd2_rd(__fadd2_rn(make_float2(l[2], l[3]), h2), t2);
+            const float pb[4] = {p01.x, p01.y, p23.x, p23.y};
             const int rb = row * Dp, rw = W - col;  // pixels e >= rw of this chunk are on the next row
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const uint32_t b = __float_as_uint(__fadd_rd(__fadd_rn(l[e], 0.5f), 8388608.0f)) - kTwo23Bits;
+                const uint32_t b = __float_as_uint(pb[e]) - kTwo23Bits;
                 const bool ok = l[e] > 0.0f && b < (uint32_t)D;
                 const int key = ok ? (e < rw ? rb : rb + Dp) + (int)b : run_key;
+#ifdef LD_CHECKED
                 const bool nk = key != run_key;
                 red_add_if(nk && LD_IN(run_key, nr * Dp, CK_VDISP_RUN), hbase + 4u * (uint32_t)run_key, run_cnt);
                 run_cnt = (nk ? 0 : run_cnt) + (int)ok;
+#else
+                flush_step(key, run_key, hbase + 4u * (uint32_t)run_key, run_cnt, run_cnt + (int)ok);
+#endif
                 run_key = key;
             }
             col += 128;
