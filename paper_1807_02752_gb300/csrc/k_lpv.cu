@@ -166,20 +166,25 @@ __device__ __forceinline__ void m1_body(const KParams &kp, const Work &w, int R,
                 atomicAdd(drow + (W - 1 - c0), -g);
         }
         __syncthreads();
-        for (int u = c0 + tid; u < c1; u += kM1Threads) {
-            const int32_t *col = dd + (u - c0);
-            int box = 0;  // sum of D over the rows of M_0 row r0 - 1 (D rows 0 .. 2 varsigma)
-            for (int i = 0; i <= 2 * vs; ++i)
-                box += col[(size_t)i * cw];
-            int xp = r0 - 1 >= 0 ? box : 0;
-            box += col[(size_t)(2 * vs + 1) * cw] - col[0];
-            int xc = box;  // M_0 row r0 (inside the frame)
-            for (int r = 0; r < nr; ++r) {
-                const int g = r0 + r;
-                box += col[(size_t)(r + 2 + 2 * vs) * cw] - col[(size_t)(r + 1) * cw];  // M_0 row g + 1
+        // column pass, one thread per column: pointers walk the D rows and the M_1 rows (no index products)
+        const int span = 2 * vs + 1;
+        for (int uc = tid; uc < cw; uc += kM1Threads) {
+            const int32_t *lo = dd + uc;                     // D rows 0 .. 2 varsigma: M_0 row r0 - 1
+            const int32_t *hi = lo + span * cw;
+            int box = 0;
+            for (const int32_t *p = lo; p < hi; p += cw)
+                box += *p;
+            int xp = r0 - 1 >= 0 ? box : 0;                  // 0 above the frame
+            box += *hi - *lo;                                 // M_0 row r0 (inside the frame)
+            hi += cw;
+            lo += cw;
+            int xc = box;
+            int32_t *out = M1 + (size_t)r0 * W + c0 + uc;
+            for (int g = r0; g < r0 + nr; ++g, hi += cw, lo += cw, out += W) {
+                box += *hi - *lo;                             // M_0 row g + 1
                 const int xn = g + 1 <= vmax ? box : 0;
                 if (g >= rs)
-                    M1[(size_t)g * W + u] = xp + 2 * xc + xn;
+                    *out = xp + 2 * xc + xn;
                 xp = xc;
                 xc = xn;
             }
