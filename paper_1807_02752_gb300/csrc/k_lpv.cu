@@ -211,12 +211,12 @@ __global__ void __launch_bounds__(kM1Threads, 2) k_m1_fd(const FrameDesc *__rest
 // the frames flagged LD_F_FALLBACK (the proposal selected no lane there).
 // A short list (MODE 1) is latency-bound: each start is a serial chain of divisions and gathers, so the
 // list form issues the M_1 loads of 32 rows at a time instead of 8 (fewer dependent round trips).
-template <int MODE>
+template <int MODE, bool LAM>
 __device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, const int32_t *elist, const int32_t *ecnt,
                                             int ecap, const int f, const int tile)
 {
     constexpr int kEnBatch = MODE == 1 ? 32 : kEnBatchDefault;
-    extern __shared__ float vrow[];   // [2][H]: V_px, V_py
+    extern __shared__ float vrow[];   // [3][H]: V_px, V_py, and the divisor of Eq. 25 for each row
     const int W = kp.W, H = kp.H;
     const FrameState &fs = w.fs[f];
     if (fs.flags & LD_F_NO_LANES)
@@ -230,6 +230,8 @@ __device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, co
     for (int v = threadIdx.x; v < H; v += kEnThreads) {
         vrow[v] = rows[2 * H + v];
         vrow[H + v] = rows[H + v];
+        // the step into row v divides by (v + 1) - V_py(v + 1), the same for every start
+        vrow[2 * H + v] = v < H - 1 ? __fsub_rn(__fadd_rn((float)v, 1.0f), rows[H + v + 1]) : 1.0f;
     }
     __syncthreads();
     int i = tile * kEnThreads + threadIdx.x;
@@ -242,7 +244,6 @@ __device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, co
         return;
     const int32_t *M1 = w.M1 + (size_t)f * H * W;
     const float fW = (float)W;
-    const bool lam = kp.lambda_g != 0;  // lambda_g is 0 or 1
     // The track recursion does not depend on M_1.  Each batch of kEnBatch rows first computes the track
     // columns (no load in flight while the divisions run), then issues the batch's M_1 loads back to back,
     // then adds them in row order.
@@ -259,8 +260,7 @@ __device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, co
                 if (v < vmax) {
                     const float vx = vrow[v + 1], vy = vrow[H + v + 1];
                     const float num = __fsub_rn(__fadd_rn(vx, __fmul_rn(fv, u)), __fmul_rn(vy, u));
-                    const float den = __fsub_rn(__fadd_rn(fv, 1.0f), vy);
-                    u = __fdiv_rn(num, den);
+                    u = __fdiv_rn(num, vrow[2 * H + v]);
                 }
                 const float c = floorf(__fadd_rn(u, 0.5f));
                 if (c >= 0.0f && c < fW)
@@ -269,14 +269,15 @@ __device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, co
             fv = __fsub_rn(fv, 1.0f);
         }
         int32_t m[kEnBatch];
+        const int rowoff = v0 * W;   // H W < 2^31
 #pragma unroll
         for (int b = 0; b < kEnBatch; ++b)
             m[b] = col[b] >= 0 && LD_IN(col[b], W, CK_EN_COL) && LD_IN(v0 - b, H, CK_EN_ROW)
-                       ? __ldg(M1 + (size_t)(v0 - b) * W + col[b]) : 0;
+                       ? __ldg(M1 + (rowoff - b * W + col[b])) : 0;
 #pragma unroll
         for (int b = 0; b < kEnBatch; ++b)
             if (decltype(full)::value || b < nb)
-                E = (long long)m[b] + (lam ? E : 0ll);
+                E = LAM ? E + (long long)m[b] : (long long)m[b];
     };
     int v0 = vmax;
     for (; v0 - kEnBatch + 1 >= vtop; v0 -= kEnBatch)
@@ -287,20 +288,26 @@ __device__ __forceinline__ void energy_body(const KParams &kp, const Work &w, co
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kEnThreads, MODE == 1 ? 2 : 8) k_energy(const KParams kp, const Work w,
+__global__ void __launch_bounds__(kEnThreads, MODE == 1 ? 2 : 12) k_energy(const KParams kp, const Work w,
                                                                          const int32_t *elist, const int32_t *ecnt,
                                                                          int ecap)
 {
-    energy_body<MODE>(kp, w, elist, ecnt, ecap, blockIdx.y, blockIdx.x);
+    if (kp.lambda_g != 0)   // lambda_g is 0 or 1
+        energy_body<MODE, true>(kp, w, elist, ecnt, ecap, blockIdx.y, blockIdx.x);
+    else
+        energy_body<MODE, false>(kp, w, elist, ecnt, ecap, blockIdx.y, blockIdx.x);
 }
-__global__ void __launch_bounds__(kEnThreads, 8) k_energy_fd(const FrameDesc *__restrict__ fd)
+__global__ void __launch_bounds__(kEnThreads, 12) k_energy_fd(const FrameDesc *__restrict__ fd)
 {
     const FrameDesc &d = fd[blockIdx.y];
     const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
     const Work w = d.w;
     if ((int)blockIdx.x * kEnThreads >= kp.n_starts)
         return;
-    energy_body<0>(kp, w, nullptr, nullptr, 0, 0, blockIdx.x);
+    if (kp.lambda_g != 0)
+        energy_body<0, true>(kp, w, nullptr, nullptr, 0, 0, blockIdx.x);
+    else
+        energy_body<0, false>(kp, w, nullptr, nullptr, 0, 0, blockIdx.x);
 }
 
 // mode 0: every start; 1: minima only at candidate starts (cflag bit 0), minimum over the evaluated ones
@@ -503,7 +510,7 @@ cudaError_t launch_m1_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaSt
 cudaError_t launch_energy_fd(const KParams &kmax, const FrameDesc *fd, int n, cudaStream_t s)
 {
     dim3 grid((kmax.n_starts + kEnThreads - 1) / kEnThreads, n);
-    k_energy_fd<<<grid, kEnThreads, sizeof(float) * 2 * kmax.H, s>>>(fd);
+    k_energy_fd<<<grid, kEnThreads, sizeof(float) * 3 * kmax.H, s>>>(fd);
     return cudaGetLastError();
 }
 
@@ -516,7 +523,7 @@ cudaError_t launch_select_fd(const KParams &kmax, const FrameDesc *fd, int n, cu
 cudaError_t launch_energy(const KParams &kp, const Work &w, cudaStream_t s)
 {
     dim3 grid((kp.n_starts + kEnThreads - 1) / kEnThreads, kp.n_frames);
-    k_energy<0><<<grid, kEnThreads, sizeof(float) * 2 * kp.H, s>>>(kp, w, nullptr, nullptr, 0);
+    k_energy<0><<<grid, kEnThreads, sizeof(float) * 3 * kp.H, s>>>(kp, w, nullptr, nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -524,14 +531,14 @@ cudaError_t launch_energy_list(const KParams &kp, const Work &w, const int32_t *
                                cudaStream_t s)
 {
     dim3 grid((ecap + kEnThreads - 1) / kEnThreads, kp.n_frames);
-    k_energy<1><<<grid, kEnThreads, sizeof(float) * 2 * kp.H, s>>>(kp, w, elist, ecnt, ecap);
+    k_energy<1><<<grid, kEnThreads, sizeof(float) * 3 * kp.H, s>>>(kp, w, elist, ecnt, ecap);
     return cudaGetLastError();
 }
 
 cudaError_t launch_energy_fallback(const KParams &kp, const Work &w, cudaStream_t s)
 {
     dim3 grid((kp.n_starts + kEnThreads - 1) / kEnThreads, kp.n_frames);
-    k_energy<2><<<grid, kEnThreads, sizeof(float) * 2 * kp.H, s>>>(kp, w, nullptr, nullptr, 0);
+    k_energy<2><<<grid, kEnThreads, sizeof(float) * 3 * kp.H, s>>>(kp, w, nullptr, nullptr, 0);
     return cudaGetLastError();
 }
 
