@@ -43,6 +43,16 @@ __device__ __forceinline__ void flush_step(int key, int run_key, uint32_t a, int
                  : "=r"(cnt) : "r"(key), "r"(run_key), "r"(a), "r"(cnt), "r"(inc));
 }
 
+// 16-byte load of the disparity, which this kernel reads once, under an L2 evict_first policy: its lines
+// go first when the L2 needs room, ahead of the lines (often dirty) that earlier kernels left there.
+__device__ __forceinline__ float4 ld_stream(const float4 *p, uint64_t pol)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+    return v;
+}
+
 // Rows [tile * kRows, ..) of frame f.
 __device__ __forceinline__ void vdisp_body(const KParams &kp, int32_t *__restrict__ myT, const float *__restrict__ disp,
                                            int kRows, int f, int tile)
@@ -84,13 +94,15 @@ __device__ __forceinline__ void vdisp_body(const KParams &kp, int32_t *__restric
     // one run per lane, updated without branches: an invalid pixel takes the run's key (it neither breaks nor
     // extends the count); a new key flushes the run with a predicated shared-memory add (an empty run adds 0)
     const uint32_t hbase = (uint32_t)__cvta_generic_to_shared(hist);
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     int run_key = 0, run_cnt = 0;
     for (int base = w0; base < w1; base += 32 * kUnroll) {
         float4 x[kUnroll];
 #pragma unroll
         for (int k = 0; k < kUnroll; ++k) {
             const int i = base + 32 * k + lane;
-            x[k] = i < w1 && LD_IN(head + 4 * i + 3, n, CK_VDISP_LOAD) ? __ldg(body + i)
+            x[k] = i < w1 && LD_IN(head + 4 * i + 3, n, CK_VDISP_LOAD) ? ld_stream(body + i, pol)
                                                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // 0 does not count
         }
 #pragma unroll
