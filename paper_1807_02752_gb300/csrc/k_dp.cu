@@ -153,7 +153,7 @@ __device__ __forceinline__ void road_dp_body(const KParams &kp, const Work &w, c
             dst[c] = (own && d >= 1 && v < H) ? __ldg(my + (size_t)d * H + v) : 0;
         }
     };
-    constexpr int kSets = 4;  // steps of load latency hidden: kSets - 1
+    constexpr int kSets = 16;  // steps of load latency hidden: kSets - 1
     int reg[kSets][2];
 #pragma unroll
     for (int k = 0; k < kSets; ++k)
@@ -243,10 +243,16 @@ __device__ __forceinline__ void road_dp_body(const KParams &kp, const Work &w, c
         w.npts[f * 2] = k;
 }
 
+// One thread per pair of rows: the tallest frame (LD_MAX_H rows) needs (LD_MAX_H + 1) / 2 threads, rounded
+// up to whole warps.  The bound is kept tight so that the 16 register sets of the load pipeline fit without
+// spilling.
+constexpr int kRoadMaxThreads = 640;
+static_assert(((LD_MAX_H + 1) / 2 + 31) / 32 * 32 <= kRoadMaxThreads, "road DP: one thread per pair of rows");
+
 template <int TMAX>
-__global__ void __launch_bounds__(1024) k_road_dp(const KParams kp, const Work w) { road_dp_body<TMAX>(kp, w, blockIdx.x); }
+__global__ void __launch_bounds__(kRoadMaxThreads) k_road_dp(const KParams kp, const Work w) { road_dp_body<TMAX>(kp, w, blockIdx.x); }
 template <int TMAX>
-__global__ void __launch_bounds__(1024) k_road_dp_fd(const FrameDesc *__restrict__ fd)
+__global__ void __launch_bounds__(kRoadMaxThreads) k_road_dp_fd(const FrameDesc *__restrict__ fd)
 {
     const FrameDesc &d = fd[blockIdx.x];
     const KParams kp = d.kp;   // the frame's parameters, loaded once into registers
