@@ -166,27 +166,65 @@ __device__ __forceinline__ void m1_body(const KParams &kp, const Work &w, int R,
                 atomicAdd(drow + (W - 1 - c0), -g);
         }
         __syncthreads();
-        // column pass, one thread per column: pointers walk the D rows and the M_1 rows (no index products)
+        // column pass: pointers walk the D rows and the M_1 rows (no index products).  With an even width
+        // and chunk every row starts on 8 bytes, so a thread takes two adjacent columns per 8-byte load and
+        // store; otherwise one column.  Each column's sums are the same integer adds in the same order.
         const int span = 2 * vs + 1;
-        for (int uc = tid; uc < cw; uc += kM1Threads) {
-            const int32_t *lo = dd + uc;                     // D rows 0 .. 2 varsigma: M_0 row r0 - 1
-            const int32_t *hi = lo + span * cw;
-            int box = 0;
-            for (const int32_t *p = lo; p < hi; p += cw)
-                box += *p;
-            int xp = r0 - 1 >= 0 ? box : 0;                  // 0 above the frame
-            box += *hi - *lo;                                 // M_0 row r0 (inside the frame)
-            hi += cw;
-            lo += cw;
-            int xc = box;
-            int32_t *out = M1 + (size_t)r0 * W + c0 + uc;
-            for (int g = r0; g < r0 + nr; ++g, hi += cw, lo += cw, out += W) {
-                box += *hi - *lo;                             // M_0 row g + 1
-                const int xn = g + 1 <= vmax ? box : 0;
-                if (g >= rs)
-                    *out = xp + 2 * xc + xn;
-                xp = xc;
-                xc = xn;
+        if (((W | cw | c0) & 1) == 0) {
+            const int cw2 = cw >> 1, W2 = W >> 1;
+            for (int pc = tid; pc < cw2; pc += kM1Threads) {
+                const int2 *lo = reinterpret_cast<const int2 *>(dd) + pc;   // D rows 0 .. 2 varsigma: M_0 row r0 - 1
+                const int2 *hi = lo + span * cw2;
+                int bx = 0, by = 0;
+                for (const int2 *p = lo; p < hi; p += cw2) {
+                    const int2 t = *p;
+                    bx += t.x;
+                    by += t.y;
+                }
+                int xpx = r0 - 1 >= 0 ? bx : 0, xpy = r0 - 1 >= 0 ? by : 0;   // 0 above the frame
+                {
+                    const int2 a = *hi, b = *lo;                               // M_0 row r0 (inside the frame)
+                    bx += a.x - b.x;
+                    by += a.y - b.y;
+                }
+                hi += cw2;
+                lo += cw2;
+                int xcx = bx, xcy = by;
+                int2 *out = reinterpret_cast<int2 *>(M1 + (size_t)r0 * W + c0) + pc;
+                for (int g = r0; g < r0 + nr; ++g, hi += cw2, lo += cw2, out += W2) {
+                    const int2 a = *hi, b = *lo;                               // M_0 row g + 1
+                    bx += a.x - b.x;
+                    by += a.y - b.y;
+                    const int xnx = g + 1 <= vmax ? bx : 0, xny = g + 1 <= vmax ? by : 0;
+                    if (g >= rs)
+                        *out = make_int2(xpx + 2 * xcx + xnx, xpy + 2 * xcy + xny);
+                    xpx = xcx;
+                    xcx = xnx;
+                    xpy = xcy;
+                    xcy = xny;
+                }
+            }
+        } else {
+            for (int uc = tid; uc < cw; uc += kM1Threads) {
+                const int32_t *lo = dd + uc;                     // D rows 0 .. 2 varsigma: M_0 row r0 - 1
+                const int32_t *hi = lo + span * cw;
+                int box = 0;
+                for (const int32_t *p = lo; p < hi; p += cw)
+                    box += *p;
+                int xp = r0 - 1 >= 0 ? box : 0;                  // 0 above the frame
+                box += *hi - *lo;                                 // M_0 row r0 (inside the frame)
+                hi += cw;
+                lo += cw;
+                int xc = box;
+                int32_t *out = M1 + (size_t)r0 * W + c0 + uc;
+                for (int g = r0; g < r0 + nr; ++g, hi += cw, lo += cw, out += W) {
+                    box += *hi - *lo;                             // M_0 row g + 1
+                    const int xn = g + 1 <= vmax ? box : 0;
+                    if (g >= rs)
+                        *out = xp + 2 * xc + xn;
+                    xp = xc;
+                    xc = xn;
+                }
             }
         }
         __syncthreads();
